@@ -1,0 +1,293 @@
+"""Benchmark of the IB-LBM step on B300: MLUPS and fraction of the HBM roofline.
+
+Workload (default): the fixed-cylinder case matrix on a 2048x1024 lattice
+(D = 64 at (0.4 Lx, 0.5 Ly), 201 markers, U = 0.1, Re = 100 and 200) with every
+scheme {DF, MDF (5 iterations), DFC} x kernel {hat, Peskin 4-point} x collision
+{BGK, TRT (Lambda = 3/16), CM-MRT}: 36 lattices, FP32 shifted populations,
+advanced together with one batched launch sequence per step.  A bench step is
+one IB-LBM step of every lattice.  The populations (2 x 75.5 MB per lattice,
+5.4 GB in all) exceed the 126 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS & % of HBM peak per IB-LBM step; batched cases/s with p50/p99 latency"
+UNIT = "MLUPS"
+BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
+DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
+
+
+def matrix_specs(storage=W.F32, res=(100.0, 200.0), nx=2048, ny=1024):
+    specs = []
+    for re in res:
+        for scheme in (W.DF, W.MDF, W.DFC):
+            for kernel in (W.HAT, W.PESKIN4):
+                for col in (W.BGK, W.TRT, W.CMMRT):
+                    specs.append(W.fixed_cylinder_2048(re=re, storage=storage, collision=col, kernel=kernel,
+                                                       scheme=scheme, nx=nx, ny=ny, mdf_iters=5))
+    return specs
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(spec, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, single thread, on a bounded number of steps
+    of one lattice of the workload; returns (MLUPS, steps, seconds)."""
+    import oracle
+    from tests.harness import oracle_case
+    c = oracle_case(spec)
+    t0 = time.perf_counter()
+    c.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    c.step(n)
+    dt = time.perf_counter() - t0
+    return spec.nodes * n / dt / 1e6, n, dt
+
+
+def run_reference(args, specs):
+    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = specs[0] if not args.small else specs[0]
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline(spec, budget_s=0.5)
+    tot_nodes, tot_time = 0, 0.0
+    for _ in range(args.steps):
+        mlups, n, dt = cpu_baseline(spec, budget_s=args.ref_budget)
+        per_step.append(dt)
+        tot_nodes += spec.nodes * n
+        tot_time += dt
+    value = tot_nodes / tot_time / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_time / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": spec.name + " (one lattice of the 2048x1024 matrix)", "lattices": 1,
+                       "scheme": "DF", "kernel": "hat", "collision": "BGK", "storage": "f64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step = %.0f s of oracle steps on one 2048x1024 lattice" % args.ref_budget},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--small", action="store_true", help="256x128 lattices (quick check, not a bench number)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=5.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    nx, ny = (256, 128) if args.small else (2048, 1024)
+    specs = matrix_specs(nx=nx, ny=ny) if not args.small else [
+        W.fixed_cylinder_2048(re=re, storage=W.F32, collision=c, kernel=k, scheme=s, nx=nx, ny=ny,
+                              diameter=16.0, nmark=50, mdf_iters=5)
+        for re in (100.0, 200.0) for s in (W.DF, W.MDF, W.DFC) for k in (W.HAT, W.PESKIN4)
+        for c in (W.BGK, W.TRT, W.CMMRT)]
+    if args.impl == "reference":
+        run_reference(args, specs)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2609_02298_b300 as L
+    L.use_torch_allocator()
+    lats = [L.Lattice.from_spec(s) for s in specs]
+    nodes = sum(s.nodes for s in specs)
+    storage = specs[0].storage
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (graph capture happens here)
+    L.step_batch(lats, args.warmup)
+    for l in lats:
+        l.sync()
+    # timed region: CUDA events on the launching stream, kernel events on
+    lead = lats[0]
+    lead.set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clocks:
+        e0.record(stream)
+        L.step_batch(lats, args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sc_ms, sc_n = lead.kernel_timing()
+    lead.set_timing(False)
+    for l in lats:
+        rc = l.sync()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = nodes * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (stream-collide over all lattices)
+    peak, peak_kind = read_peaks()
+    sc_avg_s = sc_ms / max(1, sc_n) / 1e3
+    alg_bytes = BYTES_PER_LU[storage] * nodes
+    achieved = alg_bytes / sc_avg_s / 1e9 if sc_n else None
+
+    # end to end through the public API from host buffers: restore every lattice
+    # from a host checkpoint, run the steps, read back force histories and fields
+    blobs = [l.snapshot() for l in lats]
+    h2d = sum(len(b) for b in blobs)
+    barrier()
+    t0 = time.perf_counter()
+    for l, b in zip(lats, blobs):
+        l.restore(b)
+    L.step_batch(lats, args.steps)
+    d2h = 0
+    for l in lats:
+        hist = l.force_history(0, cap=args.steps)
+        r, ux, uy = l.macro()
+        d2h += hist.nbytes + r.nbytes + ux.nbytes + uy.nbytes
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nodes * args.steps * world / e2e_s / 1e6
+
+    if rank == 0:
+        cpu = None
+        if not args.small:
+            mlups_cpu, n_cpu, dt_cpu = cpu_baseline(W.fixed_cylinder_2048(re=100.0, storage=W.F64,
+                                                                          collision=W.BGK, kernel=W.HAT,
+                                                                          scheme=W.DF), args.cpu_budget)
+            cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "%d steps of one 2048x1024 lattice (DF, hat, BGK, FP64), %.1f s" % (n_cpu, dt_cpu)}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
+            "config": {"workload": ("fixed-cylinder matrix %dx%d, D=%g, %d markers: Re {100,200} x "
+                                    "{DF, MDF(5), DFC} x {hat, P4} x {BGK, TRT, CM-MRT}" %
+                                    (nx, ny, specs[0].bodies[0].radius * 2, len(specs[0].bodies[0].xy))),
+                       "lattices": len(specs), "nodes_per_step": nodes, "storage": "f32 shifted",
+                       "l2": "working set %.1f GB > 126 MB L2, no flush" % (2 * alg_bytes / 2 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "hbm_fraction": (value * 1e6 * BYTES_PER_LU[storage] / (peak * 1e9)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_kind": peak_kind, "kernel": "sc_kernel<float>",
+                         "bytes_per_launch": alg_bytes, "launches": sc_n,
+                         "avg_launch_ms": sc_avg_s * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks.summary(),
+            "device_status": rc,
+        }
+        print(json.dumps(line), flush=True)
+    for l in lats:
+        l.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * iblbm.h -- C ABI of the B300 (sm_103a) immersed-boundary lattice Boltzmann
+ * library (libiblbm.so).
+ *
+ * The library advances D2Q9 lattice Boltzmann flows coupled to rigid bodies
+ * given as Lagrangian marker sets, following H. Jo, "Mechanism-Resolved
+ * Interface Momentum Transfer in Immersed-Boundary Lattice Boltzmann
+ * Simulations":
+ *   - stream + collide with BGK (Eq. 1-3), TRT or central-moment MRT (Eq. 5,
+ *     Sec. 2.2) and Guo forcing with the half-force velocity of Eq. 4;
+ *   - marker interpolation (Eq. 7) and spreading (Eq. 8) with the hat (Eq. 9)
+ *     or Peskin 4-point (Eq. 10) kernel;
+ *   - direct forcing (Eq. 11), multi-direct forcing (Eq. 12-14) and
+ *     distribution-function correction (Eq. 15-20);
+ *   - FP64 rigid-body Velocity-Verlet (Eq. 21-23) with the internal-mass
+ *     correction of Eq. A3.
+ *
+ * Conventions shared by every call:
+ *   Units      lattice units, dx = dt = 1, rho_f = 1 (Sec. 2.1, App. A.1).
+ *   Layout     host population arrays are double, unshifted, one plane per
+ *              direction: f[(i*ny + y)*nx + x], i in 0..8 with
+ *              e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1)
+ *              e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1).
+ *              The state between steps is the post-collision field.
+ *   Ownership  inputs are copied in; the caller keeps its arrays.  Outputs go
+ *              to caller-allocated host buffers of the documented size.
+ *              Device memory belongs to the context; it comes from the
+ *              allocator installed with iblbm_set_allocator (else cudaMalloc).
+ *   Streams    all device work of a context is ordered on the stream given in
+ *              its lattice descriptor (NULL = legacy default stream).
+ *              Calls documented as "syncs" wait for that stream.
+ *   Errors     every int-returning call returns IBLBM_OK (0) on success, a
+ *              negative IBLBM_ERR_* on error (the context stays usable unless
+ *              stated), or a positive IBLBM_WARN_* for a completed call with a
+ *              warning.  iblbm_strerror() names each code.
+ *   Threads    a context is not thread-safe; use one host thread per context.
+ */
+#ifndef IBLBM_H
+#define IBLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------- */
+#define IBLBM_OK 0
+#define IBLBM_WARN_MDF_NOT_CONVERGED 1   /* an MDF loop hit N_max or its divergence guard */
+#define IBLBM_ERR_INVALID_ARG (-1)
+#define IBLBM_ERR_OOM (-2)
+#define IBLBM_ERR_UNSTABLE (-3)           /* non-finite or non-positive density seen */
+#define IBLBM_ERR_MARKER_OUT_OF_DOMAIN (-4)
+#define IBLBM_ERR_BODY_OVERLAP (-5)
+#define IBLBM_ERR_TIMEOUT (-6)
+#define IBLBM_ERR_NOT_ADMITTED (-7)
+#define IBLBM_ERR_BUSY (-8)
+#define IBLBM_ERR_CUDA (-9)
+#define IBLBM_ERR_NOT_FOUND (-10)
+#define IBLBM_ERR_CAPACITY (-11)          /* a buffer given by the caller is too small */
+
+typedef struct iblbm_ctx iblbm_ctx;
+
+/* Collision operator, Sec. 2.2.  IBLBM_STREAM_ONLY is the identity collision
+ * (pure streaming), a verification mode with no counterpart in the paper. */
+typedef enum { IBLBM_BGK = 0, IBLBM_TRT = 1, IBLBM_CMMRT = 2, IBLBM_STREAM_ONLY = 3 } iblbm_collision;
+/* Regularised delta kernel, Sec. 2.4 (Eq. 9, Eq. 10). */
+typedef enum { IBLBM_HAT = 0, IBLBM_PESKIN4 = 1 } iblbm_kernel;
+/* Boundary-enforcement scheme, Sec. 2.5. */
+typedef enum { IBLBM_DF = 0, IBLBM_MDF = 1, IBLBM_DFC = 2 } iblbm_scheme;
+/* Population storage: FP64, FP32 shifted (f - w), FP16 shifted with FP32 compute. */
+typedef enum { IBLBM_F64 = 0, IBLBM_F32 = 1, IBLBM_F16S = 2 } iblbm_storage;
+/* Domain side condition.  VELOCITY is the Zou-He closure at the prescribed
+ * velocity (inflow, far-field and no-slip walls of Sec. 2.9); NEUMANN copies
+ * the nine post-streaming populations of the adjacent interior node (zero
+ * gradient).  PERIODIC must be set on both sides of an axis or on neither. */
+typedef enum { IBLBM_BC_PERIODIC = 0, IBLBM_BC_VELOCITY = 1, IBLBM_BC_NEUMANN = 2 } iblbm_bc;
+/* Body motion: fixed (or moved by the caller with iblbm_move_body), prescribed
+ * in-line oscillation x_c(t) = x_c0 - A sin(2 pi t / T) (Sec. 2.9.2), or free
+ * rigid-body dynamics (Sec. 2.7). */
+typedef enum { IBLBM_FIXED = 0, IBLBM_PRESCRIBED = 1, IBLBM_FREE = 2 } iblbm_motion;
+
+typedef struct {
+    int nx, ny;                 /* lattice nodes, each >= 3 */
+    int storage;                /* iblbm_storage */
+    int bc[4];                  /* iblbm_bc for the west, east, south, north sides */
+    double u_bc[4][2];          /* velocity of each VELOCITY side */
+    double trt_lambda;          /* TRT magic parameter Lambda_eo (e.g. 3/16 or 1/4) */
+    double cm_sq, cm_se;        /* CM-MRT third/fourth-order rates (paper: 1.2, 1.4) */
+    double force[2];            /* uniform body-force density on the fluid (usually 0) */
+    double init_rho, init_u[2]; /* initial state: equilibrium at this density/velocity */
+    void* cuda_stream;          /* cudaStream_t, NULL = legacy default stream */
+} iblbm_lattice_desc;
+
+typedef struct {
+    double xc, yc;              /* body centre (lattice units) */
+    double radius;              /* for the masses m_s = rho_s pi r^2, I_s = m_s r^2 / 2 */
+    double rho_ratio;           /* rho_s / rho_f */
+    int motion;                 /* iblbm_motion */
+    double gx, gy;              /* gravity (lattice units), Eq. 22 */
+    int internal_mass;          /* 1: scheme (B-2), Eq. A3; 0: scheme (A) */
+    int mdf_nmin, mdf_nmax;     /* MDF iteration bounds (paper: 5, 20) */
+    double mdf_tol;             /* MDF L_inf slip tolerance (paper: 1e-4) */
+    double mdf_omega;           /* MDF relaxation; <= 0 selects 1/||A||_inf */
+    double osc_amp, osc_period; /* PRESCRIBED: A and T of x_c(t) */
+    int history_cap;            /* force-history ring capacity in steps (<= 0: 65536) */
+} iblbm_body_desc;
+
+/* ---- memory --------------------------------------------------------------------- */
+/* Installs the device allocator used by every later context (process-wide).
+ * alloc(bytes, stream, user) returns a device pointer or NULL; free(ptr, stream,
+ * user) releases it.  Passing NULL functions restores cudaMalloc/cudaFree. */
+typedef void* (*iblbm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*iblbm_free_fn)(void* ptr, void* stream, void* user);
+int iblbm_set_allocator(iblbm_alloc_fn alloc, iblbm_free_fn free_fn, void* user);
+
+/* ---- lattice ---------------------------------------------------------------------- */
+/* Creates a lattice context on the current CUDA device (Sec. 2.1-2.2).
+ * tau > 1/2 is the relaxation time (nu = (tau - 1/2)/3); BGK/TRT/CM-MRT share it
+ * as the viscous rate.  Initialises every node to the equilibrium at
+ * (init_rho, init_u).  *out receives the context.  Errors: INVALID_ARG, OOM, CUDA. */
+int iblbm_create(const iblbm_lattice_desc* desc, int collision, double tau, iblbm_ctx** out);
+/* Frees the context and all its device memory (syncs).  NULL is ignored. */
+void iblbm_destroy(iblbm_ctx* ctx);
+
+/* Adds a rigid body given by n markers xy[2*n] (x0,y0,x1,y1,...) with arc
+ * length ds (Eq. 8), delta kernel and scheme (Sec. 2.3-2.5).  The markers are
+ * rigidly attached to the centre (xc, yc).  For MDF with mdf_omega <= 0 the
+ * relaxation 1/||A||_inf is computed here once (Sec. 2.5.2); for DFC the
+ * factors lambda_k of Eq. 17 are computed on the device.  Every kernel
+ * footprint must lie inside the lattice.  *body_id receives the index (0, 1,
+ * ...).  Errors: INVALID_ARG, MARKER_OUT_OF_DOMAIN, BODY_OVERLAP (two MDF
+ * bodies whose footprints could overlap), OOM. */
+int iblbm_add_body(iblbm_ctx* ctx, const double* xy, int n, double ds, int kernel, int scheme,
+                   const iblbm_body_desc* body, int* body_id);
+
+/* Advances nsteps IB-LBM steps, asynchronously on the context stream (replays
+ * a captured CUDA graph).  One step: stream with domain conditions, IB stage of
+ * every body, collide, body forces and motion update.  Device-side errors
+ * (instability, markers leaving the lattice) are reported by the next syncing
+ * call.  Errors: INVALID_ARG, CUDA. */
+int iblbm_step(iblbm_ctx* ctx, int nsteps);
+
+/* Waits for the context stream and returns the first device-side error seen,
+ * IBLBM_WARN_MDF_NOT_CONVERGED if an MDF loop stopped early, else IBLBM_OK. */
+int iblbm_sync(iblbm_ctx* ctx);
+
+/* Steps seen so far. */
+long long iblbm_steps_done(const iblbm_ctx* ctx);
+
+/* Force (x, y) and torque on body body_id from the last step, FP64, following
+ * the sign rules of Sec. 2.7 (DF/MDF: -sum F_L ds; DFC: sum F_s).  Syncs. */
+int iblbm_body_forces(iblbm_ctx* ctx, int body_id, double out[3]);
+/* Body centre, velocity and rotation after the last step: xc, yc, vx, vy,
+ * omega, theta.  Syncs. */
+int iblbm_body_state(iblbm_ctx* ctx, int body_id, double out[6]);
+/* Copies the last min(cap, steps) entries of the force history (3 doubles per
+ * step, oldest first) into out[3*cap]; *n receives the count.  Syncs. */
+int iblbm_force_history(iblbm_ctx* ctx, int body_id, double* out, int cap, int* n);
+/* FIXED bodies only: replaces the marker positions (xy[2*n], or NULL to keep
+ * them) and sets the rigid velocity uvw = (vx, vy, omega) used for
+ * U_d = v + omega x (X - X_c).  Errors: INVALID_ARG (not FIXED), MARKER_OUT_OF_DOMAIN. */
+int iblbm_move_body(iblbm_ctx* ctx, int body_id, const double* xy, const double uvw[3]);
+
+/* Per-marker data of the last step into out[7*n]: X, Y, U_d,x, U_d,y, force x,
+ * force y (DF: F_L, MDF: F_total, DFC: F_s), lambda_k (DFC, else 0).  Syncs. */
+int iblbm_marker_data(iblbm_ctx* ctx, int body_id, double* out);
+/* Stencil origin (i0, j0) of each marker for the last step into ij[2*n]: the
+ * footprint is i0..i0+S-1 x j0..j0+S-1, S = 2 (hat) or 4 (Peskin).  Syncs. */
+int iblbm_marker_stencils(iblbm_ctx* ctx, int body_id, int* ij);
+/* MDF diagnostics of the last step: increments applied, last L_inf residual
+ * (FP64) and omega_MDF.  Syncs. */
+int iblbm_mdf_info(iblbm_ctx* ctx, int body_id, int* iterations, double* residual, double* omega);
+
+/* Post-collision populations into f[9*nx*ny] (layout above).  shifted = 0
+ * returns f; shifted = 1 returns the stored values f - w_i exactly as held in
+ * device memory, widened to double.  Syncs. */
+int iblbm_get_populations(iblbm_ctx* ctx, double* f, int shifted);
+/* Replaces the post-collision state with f[9*nx*ny] (unshifted, layout above);
+ * values are rounded to the storage precision after the shift.  Syncs. */
+int iblbm_set_populations(iblbm_ctx* ctx, const double* f);
+/* Density and Eq. 4 velocity of the last collision into rho/ux/uy[nx*ny]
+ * (row-major y, x), computed from the post-collision state.  Syncs. */
+int iblbm_get_macro(iblbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Whole-state checkpoint (populations, body state, markers) into host memory.
+ * host may be NULL to query the size into *n.  Errors: CAPACITY.  Syncs. */
+int iblbm_snapshot(iblbm_ctx* ctx, void* host, size_t cap, size_t* n);
+/* Restores a checkpoint written by iblbm_snapshot of a context with the same
+ * lattice and bodies.  Errors: INVALID_ARG.  Syncs. */
+int iblbm_restore(iblbm_ctx* ctx, const void* host, size_t n);
+
+/* Device bytes held by the context. */
+size_t iblbm_device_bytes(const iblbm_ctx* ctx);
+
+const char* iblbm_strerror(int status);
+
+/* ---- batched stepping (one launch sequence for many cases) ------------------------- */
+/* Advances every context in ctxs[0..n) by nsteps steps with one launch per kernel
+ * per storage type per step, over a case/tile table (uneven lattices allowed).
+ * All contexts must live on the current device; the work is ordered on
+ * ctxs[0]'s stream after the other contexts' streams.  Results are identical to
+ * stepping each context alone.  Errors: INVALID_ARG, CUDA. */
+int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
+
+/* ---- timing of the stream-collide kernel ------------------------------------------ */
+/* While enabled, steps launch their kernels one by one (no graph) and bracket
+ * each stream-collide launch with CUDA events on the launching stream.
+ * iblbm_kernel_timing returns the summed event time (ms) and the launch count
+ * since the last reset, then resets.  Syncs. */
+int iblbm_set_timing(iblbm_ctx* ctx, int enable);
+int iblbm_kernel_timing(iblbm_ctx* ctx, double* stream_collide_ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,969 @@
+// C ABI of libiblbm.so (declared in include/iblbm.h): context management,
+// device memory, CUDA-graph stepping, batched stepping over many lattices,
+// checkpoints and exports.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "iblbm.h"
+#include "kernels.cuh"
+
+using namespace iblbm;
+
+// ------------------------------------------------------------------------------------------
+static void forget_plans(iblbm_ctx* c);
+
+namespace {
+
+struct AllocHooks {
+    iblbm_alloc_fn alloc = nullptr;
+    iblbm_free_fn free_fn = nullptr;
+    void* user = nullptr;
+};
+AllocHooks g_hooks;
+std::mutex g_mu;
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+    bytes = std::max<size_t>(256, (bytes + 255) & ~size_t(255));
+    if (g_hooks.alloc) return g_hooks.alloc(bytes, st, g_hooks.user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (!p) return;
+    if (g_hooks.free_fn) g_hooks.free_fn(p, st, g_hooks.user);
+    else cudaFree(p);
+}
+
+int status_from_bits(unsigned bits) {
+    if (bits & STAT_MARKER_OUT) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
+    if (bits & STAT_UNSTABLE) return IBLBM_ERR_UNSTABLE;
+    if (bits & STAT_CAPACITY) return IBLBM_ERR_CAPACITY;
+    if (bits & STAT_MDF_WARN) return IBLBM_WARN_MDF_NOT_CONVERGED;
+    return IBLBM_OK;
+}
+
+size_t storage_bytes(int st) { return st == ST_F64 ? 8 : (st == ST_F32 ? 4 : 2); }
+size_t real_bytes(int st) { return st == ST_F64 ? 8 : 4; }
+int storage_vec(int st) { return st == ST_F64 ? 2 : (st == ST_F32 ? 4 : 8); }
+
+struct BodyHost {
+    int n = 0;
+    int kernel = 0, scheme = 0, motion = 0;
+    double xc = 0, yc = 0, reach = 0;   // centre and marker reach for overlap checks
+};
+
+struct GraphSet {
+    cudaGraphExec_t one = nullptr, many = nullptr;
+    int many_steps = 0;
+    void reset() {
+        if (one) cudaGraphExecDestroy(one);
+        if (many) cudaGraphExecDestroy(many);
+        one = many = nullptr;
+    }
+};
+
+}  // namespace
+
+struct iblbm_ctx {
+    int device = 0;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    iblbm_lattice_desc desc{};
+    int collision = 0;
+    double tau = 0;
+    CaseDev hc{};                 // host copy of the static case fields
+    CaseDev* dc = nullptr;        // device case
+    BodyDev* dbodies = nullptr;   // device array [kMaxBodies]
+    BodyRef* drefs = nullptr;     // device [kMaxBodies]
+    CaseDev** dcases = nullptr;   // device [1]
+    long long* djob = nullptr;    // device [2]
+    std::vector<BodyHost> bodies;
+    std::vector<std::pair<void*, size_t>> allocs;
+    std::vector<BodyDev> hbodies; // host copies of the static body records (device pointers inside)
+    size_t bytes = 0;
+    long long steps = 0;
+    long long jobs = 0;
+    int sc_grid = 1;
+    GraphSet graphs;
+    bool dirty = true;
+    int version = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double sc_ms = 0;
+    int sc_count = 0;
+
+    void* alloc(size_t b) {
+        void* p = dev_alloc(b, work);
+        if (p) {
+            allocs.push_back({p, b});
+            bytes += b;
+        }
+        return p;
+    }
+};
+
+namespace {
+
+int check(cudaError_t e) {
+    if (e == cudaSuccess) return IBLBM_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? IBLBM_ERR_OOM : IBLBM_ERR_CUDA;
+}
+
+cudaEvent_t pool_event(iblbm_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void drain_timing(iblbm_ctx* c) {
+    for (auto& pr : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+            c->sc_ms += ms;
+            c->sc_count += 1;
+        }
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    c->ev_pending.clear();
+}
+
+// One step of one lattice: prepare bodies, IB stage, stream-collide, finish.
+cudaError_t launch_step(iblbm_ctx* c, cudaStream_t st, bool timed) {
+    const int nb = (int)c->bodies.size();
+    FinLaunch fl{c->drefs, nb, 1, c->dcases};
+    cudaError_t e = cudaSuccess;
+    if (nb > 0) {
+        if ((e = launch_body(fl, 0, st)) != cudaSuccess) return e;
+        IbLaunch il{c->drefs, nb, 0};
+        if ((e = launch_ib(c->hc.storage, il, st)) != cudaSuccess) return e;
+    }
+    ScLaunch sl{c->dcases, c->djob, 1, 0};
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+        a = pool_event(c);
+        b = pool_event(c);
+        cudaEventRecord(a, st);
+    }
+    if ((e = launch_stream_collide(c->hc.storage, sl, c->jobs, c->sc_grid, st)) != cudaSuccess) return e;
+    if (timed) {
+        cudaEventRecord(b, st);
+        c->ev_pending.push_back({a, b});
+    }
+    return launch_body(fl, 1, st);
+}
+
+int capture(iblbm_ctx* c, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return check(e);
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_step(c, c->work, false);
+    cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return check(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return check(e);
+}
+
+int ensure_graphs(iblbm_ctx* c) {
+    if (!c->dirty && c->graphs.one) return IBLBM_OK;
+    c->graphs.reset();
+    int rc = capture(c, 1, &c->graphs.one);
+    if (rc) return rc;
+    c->graphs.many_steps = 16;
+    rc = capture(c, c->graphs.many_steps, &c->graphs.many);
+    if (rc) return rc;
+    c->dirty = false;
+    return IBLBM_OK;
+}
+
+int sync_status(iblbm_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return check(e);
+    unsigned bits = 0;
+    e = cudaMemcpy(&bits, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return check(e);
+    return status_from_bits(bits);
+}
+
+void begin_user(iblbm_ctx* c) {
+    cudaEventRecord(c->ev_in, c->user_stream);
+    cudaStreamWaitEvent(c->work, c->ev_in, 0);
+}
+void end_user(iblbm_ctx* c) {
+    cudaEventRecord(c->ev_out, c->work);
+    cudaStreamWaitEvent(c->user_stream, c->ev_out, 0);
+}
+
+bool valid_bc(const int* bc) {
+    for (int s = 0; s < 4; ++s)
+        if (bc[s] < 0 || bc[s] > 2) return false;
+    return (bc[0] == BC_PER) == (bc[1] == BC_PER) && (bc[2] == BC_PER) == (bc[3] == BC_PER);
+}
+
+int stencil_ok(int S, int nx, int ny, double X, double Y) {
+    if (!std::isfinite(X) || !std::isfinite(Y)) return 0;
+    const int i0 = (int)std::floor(X) - (S == 4 ? 1 : 0), j0 = (int)std::floor(Y) - (S == 4 ? 1 : 0);
+    return i0 >= 0 && j0 >= 0 && i0 + S <= nx && j0 + S <= ny;
+}
+
+int body_index_ok(iblbm_ctx* c, int id) { return c && id >= 0 && id < (int)c->bodies.size(); }
+
+BodyDev fetch_body(iblbm_ctx* c, int id) {
+    BodyDev b;
+    cudaMemcpy(&b, &c->dbodies[id], sizeof(BodyDev), cudaMemcpyDeviceToHost);
+    return b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+int iblbm_set_allocator(iblbm_alloc_fn alloc, iblbm_free_fn free_fn, void* user) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((alloc == nullptr) != (free_fn == nullptr)) return IBLBM_ERR_INVALID_ARG;
+    g_hooks.alloc = alloc;
+    g_hooks.free_fn = free_fn;
+    g_hooks.user = user;
+    return IBLBM_OK;
+}
+
+const char* iblbm_strerror(int status) {
+    switch (status) {
+    case IBLBM_OK: return "ok";
+    case IBLBM_WARN_MDF_NOT_CONVERGED: return "MDF iteration stopped at N_max or by its divergence guard";
+    case IBLBM_ERR_INVALID_ARG: return "invalid argument";
+    case IBLBM_ERR_OOM: return "out of device memory";
+    case IBLBM_ERR_UNSTABLE: return "non-finite or non-positive density";
+    case IBLBM_ERR_MARKER_OUT_OF_DOMAIN: return "a marker footprint left the lattice";
+    case IBLBM_ERR_BODY_OVERLAP: return "MDF bodies with overlapping footprints";
+    case IBLBM_ERR_TIMEOUT: return "timeout";
+    case IBLBM_ERR_NOT_ADMITTED: return "request not admitted";
+    case IBLBM_ERR_BUSY: return "busy";
+    case IBLBM_ERR_CUDA: return "CUDA runtime error";
+    case IBLBM_ERR_NOT_FOUND: return "not found";
+    case IBLBM_ERR_CAPACITY: return "buffer too small";
+    default: return "unknown status";
+    }
+}
+
+int iblbm_create(const iblbm_lattice_desc* d, int collision, double tau, iblbm_ctx** out) {
+    if (!d || !out) return IBLBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d->nx < 3 || d->ny < 3 || d->storage < 0 || d->storage > 2 || !valid_bc(d->bc)) return IBLBM_ERR_INVALID_ARG;
+    if (collision < 0 || collision > 3 || !(tau > 0.5) || !std::isfinite(tau)) return IBLBM_ERR_INVALID_ARG;
+    if (collision == COL_TRT && !(d->trt_lambda > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    if (!(d->init_rho > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    iblbm_ctx* c = new iblbm_ctx();
+    cudaGetDevice(&c->device);
+    c->desc = *d;
+    c->collision = collision;
+    c->tau = tau;
+    c->user_stream = static_cast<cudaStream_t>(d->cuda_stream);
+    if (cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        iblbm_destroy(c);
+        return IBLBM_ERR_CUDA;
+    }
+    CaseDev& h = c->hc;
+    h.nx = d->nx;
+    h.ny = d->ny;
+    h.pitch = ((d->nx + 1 + 31) / 32) * 32;   // room for one padding column, 16-byte rows
+    h.storage = d->storage;
+    h.plane = (long long)h.pitch * d->ny;
+    h.collision = collision;
+    for (int s = 0; s < 4; ++s) {
+        h.bc[s] = d->bc[s];
+        h.ubc[s][0] = d->u_bc[s][0];
+        h.ubc[s][1] = d->u_bc[s][1];
+    }
+    h.tau = tau;
+    h.omega = 1.0 / tau;
+    h.s_e = 1.0 / tau;
+    h.s_o = collision == COL_TRT ? 1.0 / (0.5 + d->trt_lambda / (tau - 0.5)) : 1.0 / tau;
+    h.cm_sq = d->cm_sq;
+    h.cm_se = d->cm_se;
+    h.gfx = d->force[0];
+    h.gfy = d->force[1];
+    h.nbodies = 0;
+    h.dfc_all_fixed = 1;
+    h.step = 0;
+    h.status = 0;
+    const size_t fbytes = 9 * (size_t)h.plane * storage_bytes(d->storage);
+    h.f[0] = c->alloc(fbytes);
+    h.f[1] = c->alloc(fbytes);
+    c->dc = static_cast<CaseDev*>(c->alloc(sizeof(CaseDev)));
+    c->dbodies = static_cast<BodyDev*>(c->alloc(sizeof(BodyDev) * kMaxBodies));
+    c->drefs = static_cast<BodyRef*>(c->alloc(sizeof(BodyRef) * kMaxBodies));
+    c->dcases = static_cast<CaseDev**>(c->alloc(sizeof(CaseDev*)));
+    c->djob = static_cast<long long*>(c->alloc(2 * sizeof(long long)));
+    if (!h.f[0] || !h.f[1] || !c->dc || !c->dbodies || !c->drefs || !c->dcases || !c->djob) {
+        iblbm_destroy(c);
+        return IBLBM_ERR_OOM;
+    }
+    h.bodies = c->dbodies;
+    const int V = storage_vec(d->storage);
+    c->jobs = (long long)d->ny * ((d->nx + 32 * V - 1) / (32 * V));
+    long long job_off[2] = {0, c->jobs};
+    int bps = sc_blocks_per_sm(d->storage);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const long long want = (c->jobs + 7) / 8;
+    c->sc_grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * bps));
+    cudaMemsetAsync(h.f[0], 0, fbytes, c->work);
+    cudaMemsetAsync(h.f[1], 0, fbytes, c->work);
+    cudaMemcpyAsync(c->dc, &h, sizeof(CaseDev), cudaMemcpyHostToDevice, c->work);
+    cudaMemcpyAsync(c->dcases, &c->dc, sizeof(CaseDev*), cudaMemcpyHostToDevice, c->work);
+    cudaMemcpyAsync(c->djob, job_off, sizeof(job_off), cudaMemcpyHostToDevice, c->work);
+    launch_fill_equilibrium(&h, c->dc, d->init_rho, d->init_u[0], d->init_u[1], c->work);
+    int rc = check(cudaStreamSynchronize(c->work));
+    if (rc) {
+        iblbm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return IBLBM_OK;
+}
+
+void iblbm_destroy(iblbm_ctx* c) {
+    if (!c) return;
+    forget_plans(c);
+    if (c->work) cudaStreamSynchronize(c->work);
+    c->graphs.reset();
+    drain_timing(c);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& a : c->allocs) dev_free(a.first, c->work);
+    if (c->work) cudaStreamSynchronize(c->work);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->work) cudaStreamDestroy(c->work);
+    cudaGetLastError();
+    delete c;
+}
+
+int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel, int scheme,
+                   const iblbm_body_desc* bd, int* body_id) {
+    if (!c || !xy || n <= 0 || !(ds > 0.0) || !bd || kernel < 0 || kernel > 1 || scheme < 0 || scheme > 2)
+        return IBLBM_ERR_INVALID_ARG;
+    if ((int)c->bodies.size() >= kMaxBodies) return IBLBM_ERR_INVALID_ARG;
+    if (bd->motion < 0 || bd->motion > 2 || !(bd->radius > 0.0) || !(bd->rho_ratio > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    if (bd->motion == MOT_PRESC && !(bd->osc_period > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    if (scheme == SCH_MDF && (bd->mdf_nmin < 0 || bd->mdf_nmax < 1 || bd->mdf_nmin > bd->mdf_nmax)) return IBLBM_ERR_INVALID_ARG;
+    const int S = kernel == K_HAT ? 2 : 4;
+    double reach = 0.0;
+    for (int k = 0; k < n; ++k) {
+        if (!stencil_ok(S, c->hc.nx, c->hc.ny, xy[2 * k], xy[2 * k + 1])) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
+        reach = std::max(reach, std::hypot(xy[2 * k] - bd->xc, xy[2 * k + 1] - bd->yc));
+    }
+    if (scheme == SCH_MDF) {
+        for (auto& o : c->bodies)
+            if (o.scheme == SCH_MDF && std::hypot(o.xc - bd->xc, o.yc - bd->yc) < o.reach + reach + 5.0)
+                return IBLBM_ERR_BODY_OVERLAP;
+    }
+    const size_t rb = real_bytes(c->hc.storage);
+    const int side = 2 * (int)std::ceil(reach) + S + 4;
+    const int box_cap = side * side;
+    const int nent = n * S * S;
+    const int hist_cap = bd->history_cap > 0 ? bd->history_cap : 65536;
+    BodyDev B;
+    std::memset(&B, 0, sizeof(B));
+    B.n = n; B.kernel = kernel; B.scheme = scheme; B.motion = bd->motion;
+    B.internal_mass = bd->internal_mass ? 1 : 0;
+    B.mdf_nmin = bd->mdf_nmin; B.mdf_nmax = bd->mdf_nmax; B.S = S;
+    B.ds = ds; B.radius = bd->radius; B.rho_ratio = bd->rho_ratio; B.gx = bd->gx; B.gy = bd->gy;
+    B.mdf_tol = bd->mdf_tol; B.osc_amp = bd->osc_amp; B.osc_period = bd->osc_period > 0 ? bd->osc_period : 1.0;
+    B.xc0 = bd->xc; B.yc0 = bd->yc; B.t0 = c->steps;
+    B.st.xc = bd->xc; B.st.yc = bd->yc;
+    B.st.mdf_omega = bd->mdf_omega;
+    B.st.omega_valid = 0;
+    B.box_cap = box_cap; B.nent = nent; B.hist_cap = hist_cap;
+    B.X = (double*)c->alloc(8 * n); B.Y = (double*)c->alloc(8 * n);
+    B.r0x = (double*)c->alloc(8 * n); B.r0y = (double*)c->alloc(8 * n);
+    B.Udx = (double*)c->alloc(8 * n); B.Udy = (double*)c->alloc(8 * n);
+    B.Fx = (double*)c->alloc(8 * n); B.Fy = (double*)c->alloc(8 * n);
+    B.lam = (double*)c->alloc(8 * n);
+    B.node_map = (int*)c->alloc(4 * (size_t)box_cap);
+    B.fp_node = (int*)c->alloc(4 * (size_t)nent);
+    B.csr_off = (int*)c->alloc(4 * (size_t)(nent + 1));
+    B.csr_ent = (int*)c->alloc(4 * (size_t)nent);
+    B.fill = (int*)c->alloc(4 * (size_t)nent);
+    B.ij = (int*)c->alloc(8 * (size_t)n);
+    B.wts = c->alloc(rb * 8 * (size_t)n);
+    B.fpdata = c->alloc(rb * 9 * (size_t)nent);
+    B.patch = c->alloc(rb * 9 * (size_t)nent);
+    B.mk = c->alloc(rb * 16 * (size_t)n);
+    B.hist = (double*)c->alloc(24 * (size_t)hist_cap);
+    if (!B.X || !B.Y || !B.r0x || !B.r0y || !B.Udx || !B.Udy || !B.Fx || !B.Fy || !B.lam || !B.node_map ||
+        !B.fp_node || !B.csr_off || !B.csr_ent || !B.fill || !B.ij || !B.wts || !B.fpdata || !B.patch || !B.mk ||
+        !B.hist)
+        return IBLBM_ERR_OOM;
+    std::vector<double> X(n), Y(n), rx(n), ry(n);
+    for (int k = 0; k < n; ++k) {
+        X[k] = xy[2 * k];
+        Y[k] = xy[2 * k + 1];
+        rx[k] = X[k] - bd->xc;
+        ry[k] = Y[k] - bd->yc;
+    }
+    cudaStream_t w = c->work;
+    cudaMemcpyAsync(B.X, X.data(), 8 * n, cudaMemcpyHostToDevice, w);
+    cudaMemcpyAsync(B.Y, Y.data(), 8 * n, cudaMemcpyHostToDevice, w);
+    cudaMemcpyAsync(B.r0x, rx.data(), 8 * n, cudaMemcpyHostToDevice, w);
+    cudaMemcpyAsync(B.r0y, ry.data(), 8 * n, cudaMemcpyHostToDevice, w);
+    cudaMemsetAsync(B.Udx, 0, 8 * n, w);
+    cudaMemsetAsync(B.Udy, 0, 8 * n, w);
+    cudaMemsetAsync(B.Fx, 0, 8 * n, w);
+    cudaMemsetAsync(B.Fy, 0, 8 * n, w);
+    cudaMemsetAsync(B.lam, 0, 8 * n, w);
+    cudaMemsetAsync(B.hist, 0, 24 * (size_t)hist_cap, w);
+    const int id = (int)c->bodies.size();
+    cudaMemcpyAsync(&c->dbodies[id], &B, sizeof(BodyDev), cudaMemcpyHostToDevice, w);
+    BodyRef ref{c->dc, &c->dbodies[id], id, 0};
+    cudaMemcpyAsync(&c->drefs[id], &ref, sizeof(BodyRef), cudaMemcpyHostToDevice, w);
+    BodyHost bh;
+    bh.n = n; bh.kernel = kernel; bh.scheme = scheme; bh.motion = bd->motion;
+    bh.xc = bd->xc; bh.yc = bd->yc; bh.reach = reach;
+    c->bodies.push_back(bh);
+    c->hbodies.push_back(B);
+    c->hc.nbodies = (int)c->bodies.size();
+    int all_fixed = 1;
+    for (auto& o : c->bodies)
+        if (o.scheme == SCH_DFC && o.motion != MOT_FIXED) all_fixed = 0;
+    c->hc.dfc_all_fixed = all_fixed;
+    cudaMemcpyAsync(&c->dc->nbodies, &c->hc.nbodies, sizeof(int), cudaMemcpyHostToDevice, w);
+    cudaMemcpyAsync(&c->dc->dfc_all_fixed, &c->hc.dfc_all_fixed, sizeof(int), cudaMemcpyHostToDevice, w);
+    // every DFC body re-derives lambda_k now that W_total may include new markers
+    for (int b = 0; b < id; ++b) {
+        int zero = 0;
+        cudaMemcpyAsync(&c->dbodies[b].lam_valid, &zero, sizeof(int), cudaMemcpyHostToDevice, w);
+    }
+    c->dirty = true;
+    c->version++;
+    if (body_id) *body_id = id;
+    return check(cudaStreamSynchronize(w));
+}
+
+int iblbm_step(iblbm_ctx* c, int nsteps) {
+    if (!c || nsteps < 0) return IBLBM_ERR_INVALID_ARG;
+    if (nsteps == 0) return IBLBM_OK;
+    begin_user(c);
+    int rc = IBLBM_OK;
+    if (c->timing) {
+        for (int s = 0; s < nsteps && !rc; ++s) rc = check(launch_step(c, c->work, true));
+    } else {
+        rc = ensure_graphs(c);
+        int left = nsteps;
+        while (!rc && left >= c->graphs.many_steps) {
+            rc = check(cudaGraphLaunch(c->graphs.many, c->work));
+            left -= c->graphs.many_steps;
+        }
+        while (!rc && left > 0) {
+            rc = check(cudaGraphLaunch(c->graphs.one, c->work));
+            --left;
+        }
+    }
+    end_user(c);
+    if (!rc) c->steps += nsteps;
+    return rc;
+}
+
+int iblbm_sync(iblbm_ctx* c) {
+    if (!c) return IBLBM_ERR_INVALID_ARG;
+    return sync_status(c);
+}
+
+long long iblbm_steps_done(const iblbm_ctx* c) { return c ? c->steps : -1; }
+
+size_t iblbm_device_bytes(const iblbm_ctx* c) { return c ? c->bytes : 0; }
+
+int iblbm_body_forces(iblbm_ctx* c, int id, double out[3]) {
+    if (!body_index_ok(c, id) || !out) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    out[0] = b.st.Fhx; out[1] = b.st.Fhy; out[2] = b.st.Th;
+    return rc;
+}
+
+int iblbm_body_state(iblbm_ctx* c, int id, double out[6]) {
+    if (!body_index_ok(c, id) || !out) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    out[0] = b.st.xc; out[1] = b.st.yc; out[2] = b.st.vx; out[3] = b.st.vy; out[4] = b.st.om; out[5] = b.st.theta;
+    return rc;
+}
+
+int iblbm_force_history(iblbm_ctx* c, int id, double* out, int cap, int* n) {
+    if (!body_index_ok(c, id) || (!out && cap > 0) || cap < 0 || !n) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    const long long have = std::min<long long>(b.st.hist_n, b.hist_cap);
+    const long long m = std::min<long long>(have, cap);
+    std::vector<double> ring(3 * (size_t)b.hist_cap);
+    if (m > 0) cudaMemcpy(ring.data(), b.hist, 24 * (size_t)b.hist_cap, cudaMemcpyDeviceToHost);
+    for (long long j = 0; j < m; ++j) {
+        const long long step = b.st.hist_n - m + j;
+        const long long slot = step % b.hist_cap;
+        std::memcpy(out + 3 * j, ring.data() + 3 * slot, 24);
+    }
+    *n = (int)m;
+    return rc;
+}
+
+int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3]) {
+    if (!body_index_ok(c, id)) return IBLBM_ERR_INVALID_ARG;
+    if (c->bodies[id].motion != MOT_FIXED) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    const int n = b.n;
+    if (xy) {
+        for (int k = 0; k < n; ++k)
+            if (!stencil_ok(b.S, c->hc.nx, c->hc.ny, xy[2 * k], xy[2 * k + 1])) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
+        std::vector<double> X(n), Y(n);
+        for (int k = 0; k < n; ++k) { X[k] = xy[2 * k]; Y[k] = xy[2 * k + 1]; }
+        cudaMemcpy(b.X, X.data(), 8 * n, cudaMemcpyHostToDevice);
+        cudaMemcpy(b.Y, Y.data(), 8 * n, cudaMemcpyHostToDevice);
+        b.cache_valid = 0;
+        b.lam_valid = 0;
+    }
+    if (uvw) {
+        b.st.vx = uvw[0];
+        b.st.vy = uvw[1];
+        b.st.om = uvw[2];
+    }
+    cudaMemcpy(&c->dbodies[id], &b, sizeof(BodyDev), cudaMemcpyHostToDevice);
+    if (xy)
+        for (int o = 0; o < (int)c->bodies.size(); ++o) {
+            int zero = 0;
+            cudaMemcpy(&c->dbodies[o].lam_valid, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        }
+    return check(cudaGetLastError());
+}
+
+int iblbm_marker_data(iblbm_ctx* c, int id, double* out) {
+    if (!body_index_ok(c, id) || !out) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    const int n = b.n;
+    std::vector<double> col(n);
+    double* src[7] = {b.X, b.Y, b.Udx, b.Udy, b.Fx, b.Fy, b.lam};
+    for (int j = 0; j < 7; ++j) {
+        cudaMemcpy(col.data(), src[j], 8 * n, cudaMemcpyDeviceToHost);
+        for (int k = 0; k < n; ++k) out[7 * k + j] = (j == 6 && b.scheme != SCH_DFC) ? 0.0 : col[k];
+    }
+    return check(cudaGetLastError()) ? IBLBM_ERR_CUDA : rc;
+}
+
+int iblbm_marker_stencils(iblbm_ctx* c, int id, int* ij) {
+    if (!body_index_ok(c, id) || !ij) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    cudaMemcpy(ij, b.ij, 8 * (size_t)b.n, cudaMemcpyDeviceToHost);
+    return check(cudaGetLastError()) ? IBLBM_ERR_CUDA : rc;
+}
+
+int iblbm_mdf_info(iblbm_ctx* c, int id, int* iters, double* res, double* omega) {
+    if (!body_index_ok(c, id)) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    if (iters) *iters = b.st.mdf_iters;
+    if (res) *res = b.st.mdf_res;
+    if (omega) *omega = b.st.mdf_omega;
+    return rc;
+}
+
+int iblbm_get_populations(iblbm_ctx* c, double* f, int shifted) {
+    if (!c || !f) return IBLBM_ERR_INVALID_ARG;
+    const size_t N = 9 * (size_t)c->hc.nx * c->hc.ny;
+    double* d = static_cast<double*>(dev_alloc(N * 8, c->work));
+    if (!d) return IBLBM_ERR_OOM;
+    int rc = check(launch_export(&c->hc, c->dc, d, shifted ? 1 : 0, c->work));
+    if (!rc) rc = check(cudaMemcpyAsync(f, d, N * 8, cudaMemcpyDeviceToHost, c->work));
+    if (!rc) rc = check(cudaStreamSynchronize(c->work));
+    dev_free(d, c->work);
+    return rc;
+}
+
+int iblbm_set_populations(iblbm_ctx* c, const double* f) {
+    if (!c || !f) return IBLBM_ERR_INVALID_ARG;
+    const size_t N = 9 * (size_t)c->hc.nx * c->hc.ny;
+    cudaStreamSynchronize(c->work);
+    double* d = static_cast<double*>(dev_alloc(N * 8, c->work));
+    if (!d) return IBLBM_ERR_OOM;
+    int rc = check(cudaMemcpyAsync(d, f, N * 8, cudaMemcpyHostToDevice, c->work));
+    if (!rc) rc = check(launch_import(&c->hc, c->dc, d, c->work));
+    if (!rc) rc = check(cudaStreamSynchronize(c->work));
+    dev_free(d, c->work);
+    return rc;
+}
+
+int iblbm_get_macro(iblbm_ctx* c, double* rho, double* ux, double* uy) {
+    if (!c || !rho || !ux || !uy) return IBLBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)c->hc.nx * c->hc.ny;
+    double* d = static_cast<double*>(dev_alloc(3 * N * 8, c->work));
+    if (!d) return IBLBM_ERR_OOM;
+    int rc = check(launch_macro(&c->hc, c->dc, d, d + N, d + 2 * N, c->work));
+    if (!rc) rc = check(cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, c->work));
+    if (!rc) rc = check(cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, c->work));
+    if (!rc) rc = check(cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, c->work));
+    if (!rc) rc = check(cudaStreamSynchronize(c->work));
+    dev_free(d, c->work);
+    return rc;
+}
+
+// Checkpoint layout: header, the current population buffer (raw storage), then
+// per body: BodyState and the marker arrays X, Y, Udx, Udy, Fx, Fy, lam and the
+// force-history ring.
+struct SnapHeader {
+    unsigned magic;
+    int nx, ny, storage, nbodies, pad;
+    long long steps;
+    unsigned long long dev_step;
+};
+
+int iblbm_snapshot(iblbm_ctx* c, void* host, size_t cap, size_t* n) {
+    if (!c || !n) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    const size_t fb = 9 * (size_t)c->hc.plane * storage_bytes(c->hc.storage);
+    size_t total = sizeof(SnapHeader) + fb;
+    std::vector<BodyDev> bs;
+    for (int b = 0; b < (int)c->bodies.size(); ++b) {
+        bs.push_back(fetch_body(c, b));
+        total += sizeof(BodyState) + 7 * 8 * (size_t)bs.back().n + 24 * (size_t)bs.back().hist_cap;
+    }
+    *n = total;
+    if (!host) return IBLBM_OK;
+    if (cap < total) return IBLBM_ERR_CAPACITY;
+    CaseDev dcase;
+    cudaMemcpy(&dcase, c->dc, sizeof(CaseDev), cudaMemcpyDeviceToHost);
+    char* p = static_cast<char*>(host);
+    SnapHeader h{0x49424c4du, c->hc.nx, c->hc.ny, c->hc.storage, (int)c->bodies.size(), 0, c->steps, dcase.step};
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    cudaMemcpy(p, c->hc.f[(int)(dcase.step & 1ull)], fb, cudaMemcpyDeviceToHost);
+    p += fb;
+    for (auto& b : bs) {
+        std::memcpy(p, &b.st, sizeof(BodyState));
+        p += sizeof(BodyState);
+        double* arr[7] = {b.X, b.Y, b.Udx, b.Udy, b.Fx, b.Fy, b.lam};
+        for (int j = 0; j < 7; ++j) {
+            cudaMemcpy(p, arr[j], 8 * (size_t)b.n, cudaMemcpyDeviceToHost);
+            p += 8 * (size_t)b.n;
+        }
+        cudaMemcpy(p, b.hist, 24 * (size_t)b.hist_cap, cudaMemcpyDeviceToHost);
+        p += 24 * (size_t)b.hist_cap;
+    }
+    return check(cudaGetLastError()) ? IBLBM_ERR_CUDA : rc;
+}
+
+int iblbm_restore(iblbm_ctx* c, const void* host, size_t n) {
+    if (!c || !host || n < sizeof(SnapHeader)) return IBLBM_ERR_INVALID_ARG;
+    SnapHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != 0x49424c4du || h.nx != c->hc.nx || h.ny != c->hc.ny || h.storage != c->hc.storage ||
+        h.nbodies != (int)c->bodies.size())
+        return IBLBM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->work);
+    const size_t fb = 9 * (size_t)c->hc.plane * storage_bytes(c->hc.storage);
+    const char* p = static_cast<const char*>(host) + sizeof(h);
+    size_t need = sizeof(h) + fb;
+    std::vector<BodyDev> bs;
+    for (int b = 0; b < h.nbodies; ++b) {
+        bs.push_back(fetch_body(c, b));
+        need += sizeof(BodyState) + 7 * 8 * (size_t)bs.back().n + 24 * (size_t)bs.back().hist_cap;
+    }
+    if (n < need) return IBLBM_ERR_INVALID_ARG;
+    cudaMemcpy(c->hc.f[(int)(h.dev_step & 1ull)], p, fb, cudaMemcpyHostToDevice);
+    p += fb;
+    cudaMemcpy(&c->dc->step, &h.dev_step, sizeof(unsigned long long), cudaMemcpyHostToDevice);
+    unsigned zero = 0;
+    cudaMemcpy(&c->dc->status, &zero, sizeof(unsigned), cudaMemcpyHostToDevice);
+    for (int b = 0; b < h.nbodies; ++b) {
+        BodyDev& B = bs[b];
+        std::memcpy(&B.st, p, sizeof(BodyState));
+        p += sizeof(BodyState);
+        double* arr[7] = {B.X, B.Y, B.Udx, B.Udy, B.Fx, B.Fy, B.lam};
+        for (int j = 0; j < 7; ++j) {
+            cudaMemcpy(arr[j], p, 8 * (size_t)B.n, cudaMemcpyHostToDevice);
+            p += 8 * (size_t)B.n;
+        }
+        cudaMemcpy(B.hist, p, 24 * (size_t)B.hist_cap, cudaMemcpyHostToDevice);
+        p += 24 * (size_t)B.hist_cap;
+        B.cache_valid = 0;
+        B.lam_valid = 0;
+        B.status = 0;
+        B.t0 = h.steps - B.st.nstep;   // step at which the body joined the checkpointed run
+        cudaMemcpy(&c->dbodies[b], &B, sizeof(BodyDev), cudaMemcpyHostToDevice);
+    }
+    c->steps = h.steps;
+    for (int b = 0; b < h.nbodies; ++b) c->hbodies[b].t0 = bs[b].t0;
+    return check(cudaDeviceSynchronize());
+}
+
+int iblbm_set_timing(iblbm_ctx* c, int enable) {
+    if (!c) return IBLBM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->work);
+    drain_timing(c);
+    c->timing = enable != 0;
+    c->sc_ms = 0;
+    c->sc_count = 0;
+    return IBLBM_OK;
+}
+
+int iblbm_kernel_timing(iblbm_ctx* c, double* ms, int* launches) {
+    if (!c) return IBLBM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->work);
+    drain_timing(c);
+    if (ms) *ms = c->sc_ms;
+    if (launches) *launches = c->sc_count;
+    c->sc_ms = 0;
+    c->sc_count = 0;
+    return IBLBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batched stepping: one launch per kernel per storage type per step over a
+// case/tile table spanning every lattice of the batch.
+namespace {
+
+struct BatchGroup {
+    int storage = 0;
+    int ncases = 0;
+    long long jobs = 0;
+    int grid = 1;
+    CaseDev** dcases = nullptr;
+    long long* djob = nullptr;
+    BodyRef* drefs = nullptr;
+    int nrefs = 0;
+};
+
+struct BatchPlan {
+    std::vector<iblbm_ctx*> ctxs;
+    std::vector<int> versions;
+    std::vector<BatchGroup> groups;
+    BodyRef* drefs_all = nullptr;
+    CaseDev** dcases_all = nullptr;
+    int nrefs_all = 0;
+    std::vector<void*> mem;
+    GraphSet graphs;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> joins;
+    ~BatchPlan() {
+        graphs.reset();
+        for (auto p : mem) dev_free(p, st);
+        for (auto e : joins) cudaEventDestroy(e);
+    }
+};
+
+std::map<std::vector<iblbm_ctx*>, BatchPlan*> g_plans;
+
+void* plan_alloc(BatchPlan* P, size_t b) {
+    void* p = dev_alloc(b, P->st);
+    if (p) P->mem.push_back(p);
+    return p;
+}
+
+cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
+    cudaError_t e = cudaSuccess;
+    FinLaunch all{P->drefs_all, P->nrefs_all, (int)P->ctxs.size(), P->dcases_all};
+    if (P->nrefs_all > 0) {
+        if ((e = launch_body(all, 0, st)) != cudaSuccess) return e;
+        for (auto& g : P->groups) {
+            IbLaunch il{g.drefs, g.nrefs, 0};
+            if ((e = launch_ib(g.storage, il, st)) != cudaSuccess) return e;
+        }
+    }
+    for (auto& g : P->groups) {
+        ScLaunch sl{g.dcases, g.djob, g.ncases, 0};
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timer) {
+            a = pool_event(timer);
+            b = pool_event(timer);
+            cudaEventRecord(a, st);
+        }
+        if ((e = launch_stream_collide(g.storage, sl, g.jobs, g.grid, st)) != cudaSuccess) return e;
+        if (timer) {
+            cudaEventRecord(b, st);
+            timer->ev_pending.push_back({a, b});
+        }
+    }
+    return launch_body(all, 1, st);
+}
+
+BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
+    std::vector<iblbm_ctx*> key(ctxs, ctxs + n);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        bool ok = true;
+        for (int i = 0; i < n; ++i) ok &= it->second->versions[i] == ctxs[i]->version;
+        if (ok) return it->second;
+        delete it->second;
+        g_plans.erase(it);
+    }
+    BatchPlan* P = new BatchPlan();
+    P->ctxs = key;
+    P->st = ctxs[0]->work;
+    for (int i = 0; i < n; ++i) P->versions.push_back(ctxs[i]->version);
+    std::vector<BodyRef> all_refs;
+    std::vector<CaseDev*> all_cases;
+    for (int st = 0; st < 3; ++st) {
+        BatchGroup g;
+        g.storage = st;
+        std::vector<CaseDev*> cs;
+        std::vector<long long> off{0};
+        std::vector<BodyRef> refs;
+        const int V = storage_vec(st);
+        for (int i = 0; i < n; ++i) {
+            iblbm_ctx* c = ctxs[i];
+            if (c->hc.storage != st) continue;
+            cs.push_back(c->dc);
+            off.push_back(off.back() + (long long)c->hc.ny * ((c->hc.nx + 32 * V - 1) / (32 * V)));
+            for (int b = 0; b < (int)c->bodies.size(); ++b) refs.push_back(BodyRef{c->dc, &c->dbodies[b], b, 0});
+        }
+        if (cs.empty()) continue;
+        g.ncases = (int)cs.size();
+        g.jobs = off.back();
+        g.nrefs = (int)refs.size();
+        g.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
+        g.djob = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
+        g.drefs = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, refs.size())));
+        if (!g.dcases || !g.djob || !g.drefs) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+        cudaMemcpyAsync(g.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
+        cudaMemcpyAsync(g.djob, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
+        if (!refs.empty())
+            cudaMemcpyAsync(g.drefs, refs.data(), sizeof(BodyRef) * refs.size(), cudaMemcpyHostToDevice, P->st);
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
+        g.grid = (int)std::max<long long>(1, std::min<long long>((g.jobs + 7) / 8, (long long)sms * sc_blocks_per_sm(st)));
+        P->groups.push_back(g);
+        all_refs.insert(all_refs.end(), refs.begin(), refs.end());
+        all_cases.insert(all_cases.end(), cs.begin(), cs.end());
+    }
+    P->nrefs_all = (int)all_refs.size();
+    P->drefs_all = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, all_refs.size())));
+    P->dcases_all = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * all_cases.size()));
+    if (!P->drefs_all || !P->dcases_all) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+    if (!all_refs.empty())
+        cudaMemcpyAsync(P->drefs_all, all_refs.data(), sizeof(BodyRef) * all_refs.size(), cudaMemcpyHostToDevice, P->st);
+    cudaMemcpyAsync(P->dcases_all, all_cases.data(), sizeof(CaseDev*) * all_cases.size(), cudaMemcpyHostToDevice, P->st);
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        P->joins.push_back(e);
+    }
+    *rc = check(cudaStreamSynchronize(P->st));
+    if (*rc) { delete P; return nullptr; }
+    g_plans[key] = P;
+    return P;
+}
+
+int batch_capture(BatchPlan* P, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return check(e);
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_batch_step(P, P->st, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(P->st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return check(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return check(e);
+}
+
+}  // namespace
+
+extern "C" int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps) {
+    if (!ctxs || n <= 0 || nsteps < 0) return IBLBM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device) return IBLBM_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return IBLBM_ERR_INVALID_ARG;
+    }
+    if (nsteps == 0) return IBLBM_OK;
+    int rc = IBLBM_OK;
+    BatchPlan* P = get_plan(ctxs, n, &rc);
+    if (!P) return rc;
+    iblbm_ctx* lead = ctxs[0];
+    // order after every context's own stream and previous work
+    for (int i = 0; i < n; ++i) {
+        begin_user(ctxs[i]);
+        if (i > 0) {
+            cudaEventRecord(P->joins[i], ctxs[i]->work);
+            cudaStreamWaitEvent(P->st, P->joins[i], 0);
+        }
+    }
+    if (lead->timing) {
+        for (int s = 0; s < nsteps && !rc; ++s) rc = check(launch_batch_step(P, P->st, lead));
+    } else {
+        if (!P->graphs.one) {
+            rc = batch_capture(P, 1, &P->graphs.one);
+            if (!rc) {
+                P->graphs.many_steps = 8;
+                rc = batch_capture(P, P->graphs.many_steps, &P->graphs.many);
+            }
+        }
+        int left = nsteps;
+        while (!rc && left >= P->graphs.many_steps) {
+            rc = check(cudaGraphLaunch(P->graphs.many, P->st));
+            left -= P->graphs.many_steps;
+        }
+        while (!rc && left > 0) {
+            rc = check(cudaGraphLaunch(P->graphs.one, P->st));
+            --left;
+        }
+    }
+    cudaEventRecord(P->joins[0], P->st);
+    for (int i = 0; i < n; ++i) {
+        if (i > 0) cudaStreamWaitEvent(ctxs[i]->work, P->joins[0], 0);
+        end_user(ctxs[i]);
+        if (!rc) ctxs[i]->steps += nsteps;
+    }
+    return rc;
+}
+
+// Drops cached batch plans that contain a context about to be destroyed.
+static void forget_plans(iblbm_ctx* c) {
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        if (std::find(it->first.begin(), it->first.end(), c) != it->first.end()) {
+            cudaStreamSynchronize(it->second->st);
+            delete it->second;
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}

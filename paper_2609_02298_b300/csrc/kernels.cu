@@ -1,0 +1,910 @@
+// Kernels of one IB-LBM step (Sec. 2.1-2.7):
+//   ib_kernel      one CTA per body: footprint, post-streaming gather, DF / MDF /
+//                  DFC, deterministic spread to a per-body patch, FP64 force and
+//                  torque reduction.
+//   sc_kernel      fused pull-stream + domain conditions + IB patch + collide,
+//                  one warp per row segment of 32 x 16-byte vectors.
+//   body_kernel    FP64 rigid-body motion: first half of Eq. 23 and marker motion
+//                  before the IB stage, second half with Eq. A3 after it; advances
+//                  the step counters.
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace iblbm {
+
+// ------------------------------------------------------------------------------------------
+// IB patch lookup shared by stream-collide and the macro export.
+template <class R>
+__device__ __forceinline__ void add_ib(const CaseDev& C, int x, int y, R (&s)[9], R& Fx, R& Fy) {
+    for (int b = 0; b < C.nbodies; ++b) {
+        const BodyDev& B = C.bodies[b];
+        const int lx = x - B.bx0, ly = y - B.by0;
+        if (B.nfp <= 0 || lx < 0 || ly < 0 || lx >= B.bw || ly >= B.bh) continue;
+        const int slot = B.node_map[ly * B.bw + lx];
+        if (slot < 0) continue;
+        const R* p = static_cast<const R*>(B.patch) + (size_t)slot * 9;
+        if (B.scheme == SCH_DFC) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s[i] += p[i];
+        } else {
+            Fx += p[0];
+            Fy += p[1];
+        }
+    }
+}
+
+__device__ __forceinline__ bool row_has_ib(const CaseDev& C, int y, int xa, int xb) {
+    bool ib = false;
+    for (int b = 0; b < C.nbodies; ++b) {
+        const BodyDev& B = C.bodies[b];
+        if (B.nfp > 0 && y >= B.by0 && y < B.by0 + B.bh && B.bx0 < xb && B.bx0 + B.bw > xa) ib = true;
+    }
+    return ib;
+}
+
+template <class R>
+__device__ __forceinline__ bool bad_density(R rho) {
+    return !(rho > R(0) && rho < R(1e30));
+}
+
+// ------------------------------------------------------------------------------------------
+// Stream-collide of one row segment [xseg, xseg + 32V) of row y, one warp.
+template <class S>
+__device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int lane) {
+    using R = typename Traits<S>::R;
+    constexpr int V = Traits<S>::V;
+    const unsigned FULL = 0xffffffffu;
+    const int parity = (int)(C.step & 1ull);
+    const S* __restrict__ src = static_cast<const S*>(C.f[parity]);
+    S* __restrict__ dst = static_cast<S*>(C.f[parity ^ 1]);
+    const int nx = C.nx, ny = C.ny, pitch = C.pitch;
+    const long long plane = C.plane;
+    const bool xper = C.bc[SIDE_W] == BC_PER, yper = C.bc[SIDE_S] == BC_PER;
+    CollParams<R> P;
+    P.load(C);
+    const R gfx = R(C.gfx), gfy = R(C.gfy);
+    const int x0 = xseg + lane * V;
+    const bool ib = row_has_ib(C, y, xseg, xseg + 32 * V);
+    bool unstable = false;
+
+    if (!yper && (y == 0 || y == ny - 1)) {
+        // boundary row: node by node with the general domain conditions
+#pragma unroll 1
+        for (int k = 0; k < V; ++k) {
+            const int x = x0 + k;
+            if (x >= nx) break;
+            R s[9];
+            post_stream_node<S, R>(C, src, x, y, s);
+            R Fx = gfx, Fy = gfy;
+            if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+            unstable |= bad_density(collide<R>(P, s, Fx, Fy));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st1(dst + i * plane + (long long)y * pitch + x, s[i]);
+        }
+    } else {
+        int ym = y - 1, yp = y + 1;
+        if (yper) {
+            if (ym < 0) ym += ny;
+            if (yp >= ny) yp -= ny;
+        }
+        const bool active = x0 < nx;
+        R s[9][V];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sy = ey(i) == 1 ? ym : (ey(i) == -1 ? yp : y);
+            const S* row = src + i * plane + (long long)sy * pitch;
+            R v[V];
+            if (active) {
+                ld16(row + x0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) v[k] = R(0);
+            }
+            if (ex(i) == 0) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) s[i][k] = v[k];
+            } else if (ex(i) == 1) {
+                R left = __shfl_up_sync(FULL, v[V - 1], 1);
+                if (lane == 0) left = x0 > 0 ? ld1(row + x0 - 1) : (xper ? ld1(row + nx - 1) : R(0));
+                s[i][0] = left;
+#pragma unroll
+                for (int k = 1; k < V; ++k) s[i][k] = v[k - 1];
+            } else {
+                R right = __shfl_down_sync(FULL, v[0], 1);
+                if (lane == 31) right = x0 + V < pitch ? ld1(row + x0 + V) : R(0);
+#pragma unroll
+                for (int k = 0; k < V - 1; ++k) s[i][k] = v[k + 1];
+                s[i][V - 1] = right;
+            }
+        }
+        // east / west sides
+        const int ke = nx - 1 - x0;                       // position of the east node in this lane
+        const bool east_here = ke >= 0 && ke < V;
+        const bool east_in_seg = (nx - 1 >= xseg) && (nx - 1 < xseg + 32 * V);
+        if (xper) {
+            if (east_here) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (ex(i) == -1) {
+                        const int sy = ey(i) == 1 ? ym : (ey(i) == -1 ? yp : y);
+#pragma unroll
+                        for (int k = 0; k < V; ++k)
+                            if (k == ke) s[i][k] = ld1(src + i * plane + (long long)sy * pitch);
+                    }
+            }
+        } else {
+            // zero-gradient east copies node nx-2: same lane, or the previous lane's last node
+            R nb[9];
+            if (east_in_seg && C.bc[SIDE_E] == BC_NEU && ((nx - 1) % V) == 0) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) nb[i] = __shfl_up_sync(FULL, s[i][V - 1], 1);
+                // node nx-2 opens the previous segment: pull it directly
+                if (east_here && lane == 0) pull_node<S, R>(C, src, nx - 2, y, nb);
+            }
+            if (east_here) {
+                if (C.bc[SIDE_E] == BC_NEU) {
+                    if (ke == 0) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) s[i][0] = nb[i];
+                    } else {
+#pragma unroll
+                        for (int k = 1; k < V; ++k)
+                            if (k == ke) {
+#pragma unroll
+                                for (int i = 0; i < 9; ++i) s[i][k] = s[i][k - 1];
+                            }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k)
+                        if (k == ke) {
+                            R t[9];
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) t[i] = s[i][k];
+                            zou_he<R>(SIDE_E, t, R(C.ubc[SIDE_E][0]), R(C.ubc[SIDE_E][1]));
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) s[i][k] = t[i];
+                        }
+                }
+            }
+            if (x0 == 0) {
+                if (C.bc[SIDE_W] == BC_NEU) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) s[i][0] = s[i][1];
+                } else {
+                    R t[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) t[i] = s[i][0];
+                    zou_he<R>(SIDE_W, t, R(C.ubc[SIDE_W][0]), R(C.ubc[SIDE_W][1]));
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) s[i][0] = t[i];
+                }
+            }
+        }
+        // IB patch, collision
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            R t[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) t[i] = s[i][k];
+            R Fx = gfx, Fy = gfy;
+            if (ib && x0 + k < nx) add_ib<R>(C, x0 + k, y, t, Fx, Fy);
+            const R rho = collide<R>(P, t, Fx, Fy);
+            if (x0 + k < nx) unstable |= bad_density(rho);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s[i][k] = t[i];
+        }
+        if (active) {
+            if (x0 + V <= nx) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) st16(dst + i * plane + (long long)y * pitch + x0, s[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+#pragma unroll
+                    for (int k = 0; k < V; ++k)
+                        if (x0 + k < nx) st1(dst + i * plane + (long long)y * pitch + x0 + k, s[i][k]);
+            }
+        }
+    }
+    if (__any_sync(FULL, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads) sc_kernel(ScLaunch L, long long jobs) {
+    constexpr int V = Traits<S>::V;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+    for (long long job = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5; job < jobs; job += nwarps) {
+        int lo = 0, hi = L.ncases - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+        }
+        const CaseDev& C = *L.cases[lo];
+        const long long local = job - L.job_off[lo];
+        const int nseg = (C.nx + 32 * V - 1) / (32 * V);
+        const int y = (int)(local / nseg), seg = (int)(local % nseg);
+        sc_row<S>(C, y, seg * 32 * V, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Block helpers (fixed-order reductions so results do not depend on timing).
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    const int t = threadIdx.x;
+    __syncthreads();
+    sh[t] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] = fmax(sh[t], sh[t + s]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int t = threadIdx.x;
+    __syncthreads();
+    sh[t] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] = sh[t] + sh[t + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ int block_min_i(int v, int* sh) {
+    const int t = threadIdx.x;
+    __syncthreads();
+    sh[t] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] = min(sh[t], sh[t + s]);
+        __syncthreads();
+    }
+    const int r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Footprint of a body: stencil origins and weights, bounding box, box-local
+// node -> slot map and a node -> marker CSR whose lists are sorted by marker
+// index (so every spread sums in ascending marker order, like Eq. 8 written out).
+template <class R>
+__device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
+    const int tid = threadIdx.x, n = B.n, Sx = B.S, SS = Sx * Sx, kern = B.kernel;
+    R* wts = static_cast<R*>(B.wts);
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, err = 0;
+    for (int k = tid; k < n; k += kThreads) {
+        const double X = B.X[k], Y = B.Y[k];
+        const int i0 = (int)floor(X) - (Sx == 4 ? 1 : 0), j0 = (int)floor(Y) - (Sx == 4 ? 1 : 0);
+        if (!(X == X) || !(Y == Y) || i0 < 0 || j0 < 0 || i0 + Sx > C.nx || j0 + Sx > C.ny) err = 1;
+        B.ij[2 * k] = i0;
+        B.ij[2 * k + 1] = j0;
+        for (int a = 0; a < Sx; ++a) {
+            wts[k * 8 + a] = phi<R>(kern, R((double)(i0 + a) - X));
+            wts[k * 8 + 4 + a] = phi<R>(kern, R((double)(j0 + a) - Y));
+        }
+        mnx = min(mnx, i0); mny = min(mny, j0); mxx = max(mxx, i0); mxy = max(mxy, j0);
+    }
+    const int e = -block_min_i(-err, shi);
+    const int bx0 = block_min_i(mnx, shi), by0 = block_min_i(mny, shi);
+    const int bx1 = -block_min_i(-mxx, shi) + Sx, by1 = -block_min_i(-mxy, shi) + Sx;
+    const int bw = bx1 - bx0, bh = by1 - by0;
+    if (e || (long long)bw * bh > B.box_cap) {
+        if (tid == 0) {
+            B.nfp = 0;
+            B.status |= e ? STAT_MARKER_OUT : STAT_CAPACITY;
+            atomicOr(const_cast<unsigned*>(&C.status), e ? STAT_MARKER_OUT : STAT_CAPACITY);
+        }
+        __syncthreads();
+        return false;
+    }
+    const int area = bw * bh;
+    for (int q = tid; q < area; q += kThreads) B.node_map[q] = 0;
+    __syncthreads();
+    for (int en = tid; en < n * SS; en += kThreads) {
+        const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
+        const int node = (B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0);
+        atomicAdd(&B.node_map[node], 1);
+    }
+    __syncthreads();
+    // chunked exclusive scans: slot index and CSR offset
+    const int chunk = (area + kThreads - 1) / kThreads;
+    const int beg = min(area, tid * chunk), end = min(area, beg + chunk);
+    int nz = 0, cnt = 0;
+    for (int q = beg; q < end; ++q) {
+        const int c = B.node_map[q];
+        nz += c > 0;
+        cnt += c;
+    }
+    int* sa = shi;
+    int* sb = shi + kThreads + 1;
+    sa[tid] = nz;
+    sb[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int a = 0, b = 0;
+        for (int t = 0; t < kThreads; ++t) {
+            const int ta = sa[t], tb = sb[t];
+            sa[t] = a; sb[t] = b;
+            a += ta; b += tb;
+        }
+        sa[kThreads] = a;
+        sb[kThreads] = b;
+    }
+    __syncthreads();
+    int slot = sa[tid], off = sb[tid];
+    for (int q = beg; q < end; ++q) {
+        const int c = B.node_map[q];
+        if (c > 0) {
+            B.fp_node[slot] = q;
+            B.csr_off[slot] = off;
+            B.node_map[q] = slot;
+            ++slot;
+            off += c;
+        } else {
+            B.node_map[q] = -1;
+        }
+    }
+    const int nfp = sa[kThreads];
+    if (tid == 0) {
+        B.csr_off[nfp] = sb[kThreads];
+        B.bx0 = bx0; B.by0 = by0; B.bw = bw; B.bh = bh; B.nfp = nfp;
+    }
+    for (int q = tid; q < nfp; q += kThreads) B.fill[q] = 0;
+    __syncthreads();
+    for (int en = tid; en < n * SS; en += kThreads) {
+        const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
+        const int node = (B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0);
+        const int sl = B.node_map[node];
+        B.csr_ent[B.csr_off[sl] + atomicAdd(&B.fill[sl], 1)] = en;
+    }
+    __syncthreads();
+    for (int q = tid; q < nfp; q += kThreads) {   // insertion sort of each short list
+        const int o0 = B.csr_off[q], o1 = B.csr_off[q + 1];
+        for (int i = o0 + 1; i < o1; ++i) {
+            const int v = B.csr_ent[i];
+            int j = i - 1;
+            while (j >= o0 && B.csr_ent[j] > v) {
+                B.csr_ent[j + 1] = B.csr_ent[j];
+                --j;
+            }
+            B.csr_ent[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Slot of stencil node (a, b) of marker k.
+__device__ __forceinline__ int slot_of(const BodyDev& B, int k, int a, int b, int bx0, int by0, int bw) {
+    return B.node_map[(B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0)];
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
+    using R = typename Traits<S>::R;
+    const BodyRef ref = L.refs[blockIdx.x];
+    const CaseDev& C = *ref.c;
+    BodyDev& B = *ref.b;
+    __shared__ int shi[2 * kThreads + 4];
+    __shared__ double shd[kThreads];
+    const int tid = threadIdx.x;
+    if (B.nfp < 0) return;
+    const int n = B.n, Sx = B.S, scheme = B.scheme;
+    if (!B.cache_valid) {
+        if (!build_footprint<R>(C, B, shi)) return;
+        if (tid == 0) B.cache_valid = (B.motion == MOT_FIXED) ? 1 : 0;
+    }
+    __syncthreads();
+    const int bx0 = B.bx0, by0 = B.by0, bw = B.bw, nfp = B.nfp;
+    const R* wts = static_cast<const R*>(B.wts);
+    R* fp = static_cast<R*>(B.fpdata);
+    R* patch = static_cast<R*>(B.patch);
+    R* mk = static_cast<R*>(B.mk);
+    const R ds = R(B.ds);
+
+    // MDF relaxation 1/||A||_inf (Sec. 2.5.2): sum_m A_lm = ds sum_x D_l(x) W(x),
+    // W(x) = sum_m D_m(x); computed once on the first step.
+    if (scheme == SCH_MDF && !B.st.omega_valid) {
+        for (int q = tid; q < nfp; q += kThreads) {
+            R w = R(0);
+            for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
+                const int en = B.csr_ent[o], k = en / (Sx * Sx), r = en % (Sx * Sx);
+                w += wts[k * 8 + (r % Sx)] * wts[k * 8 + 4 + (r / Sx)];
+            }
+            patch[(size_t)q * 9] = w;
+        }
+        __syncthreads();
+        double best = 0.0;
+        for (int k = tid; k < n; k += kThreads) {
+            double row = 0.0;
+            for (int b = 0; b < Sx; ++b)
+                for (int a = 0; a < Sx; ++a)
+                    row += (double)(wts[k * 8 + a] * wts[k * 8 + 4 + b]) *
+                           (double)patch[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9];
+            best = fmax(best, row * B.ds);
+        }
+        best = block_max(best, shd);
+        if (tid == 0) {
+            if (B.st.mdf_omega <= 0.0) B.st.mdf_omega = 1.0 / best;
+            B.st.omega_valid = 1;
+        }
+        __syncthreads();
+    }
+
+    // DFC lambda_k of Eq. 17; W_total sums the markers of every DFC body of the case.
+    if (scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
+        for (int q = tid; q < nfp; q += kThreads) {
+            const int node = B.fp_node[q];
+            const int x = bx0 + node % bw, y = by0 + node / bw;
+            R w = R(0);
+            for (int ob = 0; ob < C.nbodies; ++ob) {
+                const BodyDev& O = C.bodies[ob];
+                if (O.scheme != SCH_DFC) continue;
+                if (ob == ref.index) {
+                    for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
+                        const int en = B.csr_ent[o], k = en / (Sx * Sx), r = en % (Sx * Sx);
+                        w += wts[k * 8 + (r % Sx)] * wts[k * 8 + 4 + (r / Sx)];
+                    }
+                } else {
+                    for (int k = 0; k < O.n; ++k) {
+                        const double dx = (double)x - O.X[k], dy = (double)y - O.Y[k];
+                        if (fabs(dx) >= 2.5 || fabs(dy) >= 2.5) continue;
+                        w += phi<R>(O.kernel, R(dx)) * phi<R>(O.kernel, R(dy));
+                    }
+                }
+            }
+            patch[(size_t)q * 9] = w;
+        }
+        __syncthreads();
+        for (int k = tid; k < n; k += kThreads) {
+            R ws = R(0);
+            for (int b = 0; b < Sx; ++b)
+                for (int a = 0; a < Sx; ++a)
+                    ws += patch[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9] *
+                          (wts[k * 8 + a] * wts[k * 8 + 4 + b]);
+            const double lam = 1.0 / (2.0 * 1.0 * B.ds * (double)ws);
+            B.lam[k] = lam;
+        }
+        __syncthreads();
+        if (tid == 0) B.lam_valid = 1;
+    }
+
+    // gather the post-streaming state at every footprint node
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    for (int q = tid; q < nfp; q += kThreads) {
+        const int node = B.fp_node[q];
+        const int x = bx0 + node % bw, y = by0 + node / bw;
+        R s[9];
+        post_stream_node<S, R>(C, src, x, y, s);
+        R* o = fp + (size_t)q * 9;
+        if (scheme == SCH_DFC) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[i] = s[i];
+        } else {
+            R drho = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                drho += s[i];
+                jx += R(ex(i)) * s[i];
+                jy += R(ey(i)) * s[i];
+            }
+            const R rho = R(1) + drho;
+            o[0] = rho;
+            o[1] = jx / rho;
+            o[2] = jy / rho;
+            o[3] = o[1];
+            o[4] = o[2];
+        }
+    }
+    __syncthreads();
+
+    if (scheme == SCH_DF) {
+        // Eq. 7 on rho and u_raw, Eq. 11
+        for (int k = tid; k < n; k += kThreads) {
+            R rk = R(0), Ux = R(0), Uy = R(0);
+            for (int b = 0; b < Sx; ++b)
+                for (int a = 0; a < Sx; ++a) {
+                    const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
+                    const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
+                    rk += g[0] * D;
+                    Ux += g[1] * D;
+                    Uy += g[2] * D;
+                }
+            const R Fx = R(2) * rk * (R(B.Udx[k]) - Ux), Fy = R(2) * rk * (R(B.Udy[k]) - Uy);
+            mk[k * 16 + 0] = Fx;
+            mk[k * 16 + 1] = Fy;
+            B.Fx[k] = (double)Fx;
+            B.Fy[k] = (double)Fy;
+        }
+    } else if (scheme == SCH_MDF) {
+        // Eqs. 12-14: at least N_min increments; tolerance and 1.5x guard are
+        // tested on U^(n) before increment n; a diverging iterate is not applied.
+        const R om = R(B.st.mdf_omega);
+        for (int k = tid; k < n; k += kThreads) {
+            R rk = R(0);
+            for (int b = 0; b < Sx; ++b)
+                for (int a = 0; a < Sx; ++a)
+                    rk += fp[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9] * (wts[k * 8 + a] * wts[k * 8 + 4 + b]);
+            mk[k * 16 + 2] = rk;
+            mk[k * 16 + 3] = R(0);
+            mk[k * 16 + 4] = R(0);
+        }
+        __syncthreads();
+        int applied = 0;
+        double rprev = 0.0, r = 0.0;
+        bool guard = false, tol_met = false;
+        for (int it = 1; it <= B.mdf_nmax; ++it) {
+            double e = 0.0;
+            for (int k = tid; k < n; k += kThreads) {
+                R Ux = R(0), Uy = R(0);
+                for (int b = 0; b < Sx; ++b)
+                    for (int a = 0; a < Sx; ++a) {
+                        const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
+                        const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
+                        Ux += g[3] * D;
+                        Uy += g[4] * D;
+                    }
+                const double dx = B.Udx[k] - (double)Ux, dy = B.Udy[k] - (double)Uy;
+                e = fmax(e, sqrt(dx * dx + dy * dy));
+                mk[k * 16 + 5] = R(2) * mk[k * 16 + 2] * (R(B.Udx[k]) - Ux);   // Eq. 13
+                mk[k * 16 + 6] = R(2) * mk[k * 16 + 2] * (R(B.Udy[k]) - Uy);
+            }
+            r = block_max(e, shd);
+            if (applied >= B.mdf_nmin && r < B.mdf_tol) { tol_met = true; break; }
+            if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
+            for (int q = tid; q < nfp; q += kThreads) {
+                R sx = R(0), sy = R(0);
+                for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
+                    const int en = B.csr_ent[o], k = en / (Sx * Sx), rr = en % (Sx * Sx);
+                    const R D = wts[k * 8 + (rr % Sx)] * wts[k * 8 + 4 + (rr / Sx)];
+                    sx += mk[k * 16 + 5] * D * ds;
+                    sy += mk[k * 16 + 6] * D * ds;
+                }
+                R* g = fp + (size_t)q * 9;
+                g[3] += om / (R(2) * g[0]) * sx;   // Eq. 14 with the node density
+                g[4] += om / (R(2) * g[0]) * sy;
+            }
+            for (int k = tid; k < n; k += kThreads) {
+                mk[k * 16 + 3] += om * mk[k * 16 + 5];
+                mk[k * 16 + 4] += om * mk[k * 16 + 6];
+            }
+            __syncthreads();
+            rprev = r;
+            ++applied;
+        }
+        for (int k = tid; k < n; k += kThreads) {
+            mk[k * 16 + 0] = mk[k * 16 + 3];
+            mk[k * 16 + 1] = mk[k * 16 + 4];
+            B.Fx[k] = (double)mk[k * 16 + 3];
+            B.Fy[k] = (double)mk[k * 16 + 4];
+        }
+        if (tid == 0) {
+            B.st.mdf_iters = applied;
+            B.st.mdf_res = r;
+            if (guard || (!tol_met && B.mdf_nmax > B.mdf_nmin)) {
+                B.status |= STAT_MDF_WARN;
+                atomicOr(const_cast<unsigned*>(&C.status), STAT_MDF_WARN);
+            }
+        }
+    } else {
+        // DFC, Eqs. 15, 16, 18, 20 on shifted populations: the w_i parts of
+        // f*_opp - f*_i cancel, leaving s*_opp - s*_i + 6 w_i e_i.U_d (rho_f = 1).
+        for (int k = tid; k < n; k += kThreads) {
+            R st[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st[i] = R(0);
+            for (int b = 0; b < Sx; ++b)
+                for (int a = 0; a < Sx; ++a) {
+                    const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
+                    const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) st[i] += g[i] * D;
+                }
+            const R lam = R(B.lam[k]);
+            const R udx = R(B.Udx[k]), udy = R(B.Udy[k]);
+            R fsx = R(0), fsy = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R d = lam * (st[opp(i)] - st[i] + R(6) * wgt<R>(i) * (R(ex(i)) * udx + R(ey(i)) * udy));
+                mk[k * 16 + 2 + i] = d;
+                fsx += R(ex(i)) * d;
+                fsy += R(ey(i)) * d;
+            }
+            mk[k * 16 + 0] = -ds * fsx;
+            mk[k * 16 + 1] = -ds * fsy;
+            B.Fx[k] = (double)(-ds * fsx);
+            B.Fy[k] = (double)(-ds * fsy);
+        }
+    }
+    __syncthreads();
+
+    // spread (Eq. 8 / Eq. 19) as a gather over each node's marker list in ascending order
+    for (int q = tid; q < nfp; q += kThreads) {
+        R p[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p[i] = R(0);
+        for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
+            const int en = B.csr_ent[o], k = en / (Sx * Sx), rr = en % (Sx * Sx);
+            const R D = wts[k * 8 + (rr % Sx)] * wts[k * 8 + 4 + (rr / Sx)];
+            if (scheme == SCH_DFC) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) p[i] += mk[k * 16 + 2 + i] * D * ds;
+            } else {
+                p[0] += mk[k * 16 + 0] * D * ds;
+                p[1] += mk[k * 16 + 1] * D * ds;
+            }
+        }
+        R* o = patch + (size_t)q * 9;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i] = p[i];
+    }
+
+    // force and torque on the body (Sec. 2.7), FP64, fixed-order tree
+    double gxs = 0.0, gys = 0.0, ts = 0.0;
+    for (int k = tid; k < n; k += kThreads) {
+        double gx, gy;
+        if (scheme == SCH_DFC) { gx = B.Fx[k]; gy = B.Fy[k]; }
+        else { gx = -B.Fx[k] * B.ds; gy = -B.Fy[k] * B.ds; }
+        const double rx = B.X[k] - B.st.xc, ry = B.Y[k] - B.st.yc;
+        gxs += gx;
+        gys += gy;
+        ts += rx * gy - ry * gx;
+    }
+    const double Fhx = block_sum(gxs, shd), Fhy = block_sum(gys, shd), Th = block_sum(ts, shd);
+    if (tid == 0) {
+        B.st.Fhx = Fhx;
+        B.st.Fhy = Fhy;
+        B.st.Th = Th;
+        const long long h = B.st.hist_n % B.hist_cap;
+        B.hist[3 * h + 0] = Fhx;
+        B.hist[3 * h + 1] = Fhy;
+        B.hist[3 * h + 2] = Th;
+        B.st.hist_n = B.st.hist_n + 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Body motion at the start of a step (mode PREPARE): first half of Eq. 23 with
+// F_total^n = F_h^n + F_g + dF_IM^n and the torque-only rotation (FREE), x_c(t)
+// at t = n + 1 (PRESCRIBED), then marker positions and U_d = v + omega x (X - X_c).
+// At the end of a step (mode FINISH): second half of Eq. 23 and Eq. A3 (FREE),
+// the body and case step counters.
+__global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
+    const double PI = 3.14159265358979323846;
+    if ((int)blockIdx.x >= L.nrefs) {
+        if (mode == 1 && threadIdx.x == 0) L.cases[blockIdx.x - L.nrefs]->step += 1ull;
+        return;
+    }
+    BodyDev& B = *L.refs[blockIdx.x].b;
+    BodyState& S = B.st;
+    const double r2 = B.radius * B.radius;
+    const double ms = B.rho_ratio * PI * r2, Is = 0.5 * ms * r2;
+    const double dm = (B.rho_ratio - 1.0) * PI * r2, mf = PI * r2;
+    if (mode == 1) {
+        if (threadIdx.x == 0) {
+            if (B.motion == MOT_FREE) {
+                const double vnx = S.vhx + (S.Fhx + dm * B.gx + S.dFimx) / (2.0 * ms);
+                const double vny = S.vhy + (S.Fhy + dm * B.gy + S.dFimy) / (2.0 * ms);
+                const double omn = S.omh + S.Th / (2.0 * Is);
+                if (B.internal_mass) {
+                    S.dFimx = mf * (vnx - S.vx);
+                    S.dFimy = mf * (vny - S.vy);
+                } else {
+                    S.dFimx = 0.0;
+                    S.dFimy = 0.0;
+                }
+                S.vx = vnx; S.vy = vny; S.om = omn;
+            }
+            S.nstep = S.nstep + 1;
+        }
+        return;
+    }
+    __shared__ double sh[8];
+    if (threadIdx.x == 0) {
+        double vx = S.vx, vy = S.vy, om = S.om;
+        if (B.motion == MOT_FREE) {
+            const double Ftx = S.Fhx + dm * B.gx + S.dFimx, Fty = S.Fhy + dm * B.gy + S.dFimy;
+            S.vhx = S.vx + Ftx / (2.0 * ms);
+            S.vhy = S.vy + Fty / (2.0 * ms);
+            S.omh = S.om + S.Th / (2.0 * Is);
+            S.xc += S.vhx;
+            S.yc += S.vhy;
+            S.theta += S.omh;
+            vx = S.vhx; vy = S.vhy; om = S.omh;
+        } else if (B.motion == MOT_PRESC) {
+            const double t = (double)(B.t0 + S.nstep + 1);
+            const double w = 2.0 * PI / B.osc_period;
+            S.xc = B.xc0 - B.osc_amp * sin(w * t);
+            S.vx = -B.osc_amp * w * cos(w * t);
+            vx = S.vx; vy = 0.0; om = 0.0;
+        }
+        sh[0] = S.xc; sh[1] = S.yc; sh[2] = vx; sh[3] = vy; sh[4] = om;
+        sh[5] = cos(S.theta); sh[6] = sin(S.theta);
+        if (B.motion != MOT_FIXED) B.cache_valid = 0;
+    }
+    __syncthreads();
+    const double xc = sh[0], yc = sh[1], vx = sh[2], vy = sh[3], om = sh[4], ct = sh[5], st = sh[6];
+    for (int k = threadIdx.x; k < B.n; k += kThreads) {
+        double rx, ry;
+        if (B.motion == MOT_FREE) {
+            rx = ct * B.r0x[k] - st * B.r0y[k];
+            ry = st * B.r0x[k] + ct * B.r0y[k];
+            B.X[k] = xc + rx;
+            B.Y[k] = yc + ry;
+        } else if (B.motion == MOT_PRESC) {
+            rx = B.r0x[k];
+            ry = B.r0y[k];
+            B.X[k] = xc + rx;
+            B.Y[k] = B.yc0 + ry;
+        } else {
+            rx = B.X[k] - xc;
+            ry = B.Y[k] - yc;
+        }
+        B.Udx[k] = vx - om * ry;
+        B.Udy[k] = vy + om * rx;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Export / import / initial state / macro fields.
+template <class S>
+__global__ void export_kernel(const CaseDev* __restrict__ Cp, double* out, int shifted) {
+    using R = typename Traits<S>::R;
+    const CaseDev& C = *Cp;
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    const long long N = (long long)C.nx * C.ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 9 * N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / N);
+        const long long r = q % N;
+        const int y = (int)(r / C.nx), x = (int)(r % C.nx);
+        const double v = (double)ld1(src + i * C.plane + (long long)y * C.pitch + x);
+        out[q] = shifted ? v : v + wgt<double>(i);
+    }
+}
+
+template <class S>
+__global__ void import_kernel(const CaseDev* __restrict__ Cp, const double* in) {
+    const CaseDev& C = *Cp;
+    S* dst = static_cast<S*>(C.f[(int)(C.step & 1ull)]);
+    const long long N = (long long)C.nx * C.ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 9 * N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / N);
+        const long long r = q % N;
+        const int y = (int)(r / C.nx), x = (int)(r % C.nx);
+        st1(dst + i * C.plane + (long long)y * C.pitch + x, (typename Traits<S>::R)(in[q] - wgt<double>(i)));
+    }
+}
+
+template <class S>
+__global__ void fill_eq_kernel(const CaseDev* __restrict__ Cp, double rho, double ux, double uy) {
+    const CaseDev& C = *Cp;
+    const long long N = (long long)C.plane;
+    const double uu = ux * ux + uy * uy;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 9 * N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / N);
+        const double v = seq_i<double>(i, rho - 1.0, rho, ux, uy, uu);
+        st1(static_cast<S*>(C.f[0]) + q, (typename Traits<S>::R)v);
+        st1(static_cast<S*>(C.f[1]) + q, (typename Traits<S>::R)v);
+    }
+}
+
+template <class S>
+__global__ void macro_kernel(const CaseDev* __restrict__ Cp, double* rho, double* ux, double* uy) {
+    using R = typename Traits<S>::R;
+    const CaseDev& C = *Cp;
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    const long long N = (long long)C.nx * C.ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(q / C.nx), x = (int)(q % C.nx);
+        double drho = 0.0, jx = 0.0, jy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            const double v = (double)ld1(src + i * C.plane + (long long)y * C.pitch + x);
+            drho += v;
+            jx += ex(i) * v;
+            jy += ey(i) * v;
+        }
+        R s[9];
+        for (int i = 0; i < 9; ++i) s[i] = R(0);
+        R Fx = R(C.gfx), Fy = R(C.gfy);
+        add_ib<R>(C, x, y, s, Fx, Fy);
+        const double r = 1.0 + drho;
+        rho[q] = r;
+        ux[q] = (jx - 0.5 * (double)Fx) / r;
+        uy[q] = (jy - 0.5 * (double)Fy) / r;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+static int grid_for(long long work) {
+    long long g = (work + 255) / 256;
+    if (g > 148 * 32) g = 148 * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_stream_collide(int storage, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
+    if (jobs <= 0) return cudaSuccess;
+    switch (storage) {
+    case ST_F64: sc_kernel<double><<<grid, kThreads, 0, st>>>(L, jobs); break;
+    case ST_F32: sc_kernel<float><<<grid, kThreads, 0, st>>>(L, jobs); break;
+    default: sc_kernel<__half><<<grid, kThreads, 0, st>>>(L, jobs); break;
+    }
+    return cudaGetLastError();
+}
+
+int sc_blocks_per_sm(int storage) {
+    int nb = 1;
+    switch (storage) {
+    case ST_F64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<double>, kThreads, 0); break;
+    case ST_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<float>, kThreads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<__half>, kThreads, 0); break;
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
+    if (L.nrefs <= 0) return cudaSuccess;
+    switch (storage) {
+    case ST_F64: ib_kernel<double><<<L.nrefs, kThreads, 0, st>>>(L); break;
+    case ST_F32: ib_kernel<float><<<L.nrefs, kThreads, 0, st>>>(L); break;
+    default: ib_kernel<__half><<<L.nrefs, kThreads, 0, st>>>(L); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st) {
+    const int g = L.nrefs + (mode == 1 ? L.ncases : 0);
+    if (g <= 0) return cudaSuccess;
+    body_kernel<<<g, kThreads, 0, st>>>(L, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st) {
+    const int g = grid_for(9LL * hc->nx * hc->ny);
+    switch (hc->storage) {
+    case ST_F64: export_kernel<double><<<g, 256, 0, st>>>(dc, out, shifted); break;
+    case ST_F32: export_kernel<float><<<g, 256, 0, st>>>(dc, out, shifted); break;
+    default: export_kernel<__half><<<g, 256, 0, st>>>(dc, out, shifted); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st) {
+    const int g = grid_for(9LL * hc->nx * hc->ny);
+    switch (hc->storage) {
+    case ST_F64: import_kernel<double><<<g, 256, 0, st>>>(dc, in); break;
+    case ST_F32: import_kernel<float><<<g, 256, 0, st>>>(dc, in); break;
+    default: import_kernel<__half><<<g, 256, 0, st>>>(dc, in); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st) {
+    const int g = grid_for(9LL * hc->plane);
+    switch (hc->storage) {
+    case ST_F64: fill_eq_kernel<double><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    case ST_F32: fill_eq_kernel<float><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    default: fill_eq_kernel<__half><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux, double* uy, cudaStream_t st) {
+    const int g = grid_for((long long)hc->nx * hc->ny);
+    switch (hc->storage) {
+    case ST_F64: macro_kernel<double><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    case ST_F32: macro_kernel<float><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    default: macro_kernel<__half><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace iblbm

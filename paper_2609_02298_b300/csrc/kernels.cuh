@@ -1,0 +1,49 @@
+// Launch descriptors shared by the kernels and the host runtime.
+#pragma once
+
+#include "iblbm_dev.cuh"
+
+namespace iblbm {
+
+// A body seen from a launch: its case and its slot in that case.
+struct BodyRef {
+    CaseDev* c;
+    BodyDev* b;
+    int index;      // body index within its case
+    int pad_;
+};
+
+// One stream-collide launch over many cases of one storage type.  Work unit:
+// one warp handles one row segment of 32*V nodes of one case; job_off[c] is
+// the first job of case c (prefix sum, ncases + 1 entries).
+struct ScLaunch {
+    CaseDev** cases;
+    long long* job_off;
+    int ncases;
+    int pad_;
+};
+
+struct IbLaunch {
+    BodyRef* refs;
+    int nrefs;
+    int pad_;
+};
+
+struct FinLaunch {
+    BodyRef* refs;
+    int nrefs;
+    int ncases;
+    CaseDev** cases;
+};
+
+// host-side launchers (kernels.cu)
+cudaError_t launch_stream_collide(int storage, const ScLaunch& L, long long jobs, int grid, cudaStream_t st);
+cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
+cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st);   // 0 prepare, 1 finish
+cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st);
+cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st);
+cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st);
+cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux, double* uy, cudaStream_t st);
+int sc_blocks_per_sm(int storage);
+
+}  // namespace iblbm

@@ -143,10 +143,11 @@ def sedimentation(two_particles=False, storage=F64, internal_mass=1, kernel=PESK
                   nx=400, ny=1600, diameter=20.0, tau=0.65, g=8.33e-5, steps=60000) -> CaseSpec:
     """Walled channel, gravity along -y, disk(s) released at rest (Sec. 2.9.3 shape)."""
     nmark = int(round(math.pi * diameter))
+    # released 8 D below the top wall; the second (heavy) particle 2 D below the light one
     if two_particles:
-        placements = [(0.5 * nx, ny - 200.0, 1.5), (0.5 * nx, ny - 160.0, 1.01)]
+        placements = [(0.5 * nx, ny - 10.0 * diameter, 1.5), (0.5 * nx, ny - 8.0 * diameter, 1.01)]
     else:
-        placements = [(0.5 * nx, ny - 160.0, 1.5)]
+        placements = [(0.5 * nx, ny - 8.0 * diameter, 1.5)]
     bodies = []
     for xc, yc, rr in placements:
         xy, ds = circle_markers(xc, yc, diameter, nmark)
