@@ -161,8 +161,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="256x128 lattices (quick check, not a bench number)")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle time for the CPU baseline (0: not reported)")
     ap.add_argument("--ref-budget", type=float, default=5.0)
+    ap.add_argument("--lattices", type=int, default=0,
+                    help="use only the first K lattices of the matrix (profiling a smaller case)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     nx, ny = (256, 128) if args.small else (2048, 1024)
@@ -171,6 +174,8 @@ def main():
                               diameter=16.0, nmark=50, mdf_iters=5)
         for re in (100.0, 200.0) for s in (W.DF, W.MDF, W.DFC) for k in (W.HAT, W.PESKIN4)
         for c in (W.BGK, W.TRT, W.CMMRT)]
+    if args.lattices > 0:
+        specs = specs[:args.lattices]
     if args.impl == "reference":
         run_reference(args, specs)
         return
@@ -253,7 +258,7 @@ def main():
 
     if rank == 0:
         cpu = None
-        if not args.small:
+        if not args.small and args.cpu_budget > 0:
             mlups_cpu, n_cpu, dt_cpu = cpu_baseline(W.fixed_cylinder_2048(re=100.0, storage=W.F64,
                                                                           collision=W.BGK, kernel=W.HAT,
                                                                           scheme=W.DF), args.cpu_budget)

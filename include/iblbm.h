@@ -203,6 +203,39 @@ const char* iblbm_strerror(int status);
  * stepping each context alone.  Errors: INVALID_ARG, CUDA. */
 int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
 
+/* ---- serving loop ---------------------------------------------------------------------- */
+/* Continuous batching of simulation requests (no counterpart in the paper; it
+ * serves the method of Sec. 2 to many callers).  A request is a lattice with
+ * at most one body run for nsteps steps; its result is the body's force
+ * history.  Requests are admitted in arrival order while a slot is free and
+ * the estimated device bytes fit the budget; admitted cases stay resident and
+ * every tick advances all of them with one batched launch sequence per step,
+ * so a case's result is identical to running it alone.  Not thread-safe. */
+typedef struct iblbm_server iblbm_server;
+/* hbm_budget: device bytes the resident cases may hold; max_slots: resident
+ * cases at most; stream: cudaStream_t the cases order their work after. */
+int iblbm_server_create(size_t hbm_budget, int max_slots, void* stream, iblbm_server** out);
+void iblbm_server_destroy(iblbm_server* srv);
+/* Queues a request (copies every input).  body/xy may be NULL when n = 0.
+ * *req_id receives its id.  Errors: INVALID_ARG. */
+int iblbm_server_submit(iblbm_server* srv, const iblbm_lattice_desc* desc, int collision, double tau,
+                        const iblbm_body_desc* body, const double* xy, int n, double ds, int kernel,
+                        int scheme, int nsteps, long long* req_id);
+/* One tick: advances every resident case by min(max_steps, fewest steps left)
+ * steps, admits queued requests while the device works, retires finished
+ * cases (their memory is freed at once).  Returns the number of requests
+ * completed in this tick (>= 0) or an error; *resident / *queued receive the
+ * counts after the tick (either may be NULL). */
+int iblbm_server_tick(iblbm_server* srv, int max_steps, int* resident, int* queued);
+/* Result of a request: 1 when done (force history into forces_out[3*cap],
+ * *n entries, *latency_s seconds from submission to completion), 0 while
+ * pending, IBLBM_ERR_NOT_ADMITTED if it can never fit the budget, another
+ * negative code if its case failed, IBLBM_ERR_NOT_FOUND for an unknown id. */
+int iblbm_server_poll(iblbm_server* srv, long long req_id, double* forces_out, int cap, int* n,
+                      double* latency_s);
+/* Device bytes held by resident cases and the resident / queued counts. */
+int iblbm_server_stats(const iblbm_server* srv, size_t* used_bytes, int* resident, int* queued);
+
 /* ---- timing of the stream-collide kernel ------------------------------------------ */
 /* While enabled, steps launch their kernels one by one (no graph) and bracket
  * each stream-collide launch with CUDA events on the launching stream.

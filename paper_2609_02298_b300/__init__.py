@@ -83,6 +83,13 @@ SIGNATURES = [
     ("iblbm_step_batch", _i, [_P(_vp), _i, _i]),
     ("iblbm_set_timing", _i, [_vp, _i]),
     ("iblbm_kernel_timing", _i, [_vp, _pd, _pi]),
+    ("iblbm_server_create", _i, [_sz, _i, _vp, _P(_vp)]),
+    ("iblbm_server_destroy", None, [_vp]),
+    ("iblbm_server_submit", _i, [_vp, _P(LatticeDesc), _i, _d, _P(BodyDesc), _pd, _i, _d, _i, _i, _i,
+                                 _P(_ll)]),
+    ("iblbm_server_tick", _i, [_vp, _i, _pi, _pi]),
+    ("iblbm_server_poll", _i, [_vp, _ll, _pd, _i, _pi, _pd]),
+    ("iblbm_server_stats", _i, [_vp, _P(_sz), _pi, _pi]),
 ]
 
 _lib = None
@@ -336,3 +343,89 @@ def step_batch(lattices: Iterable[Lattice], nsteps: int) -> None:
     lats = list(lattices)
     arr = (C.c_void_p * len(lats))(*[l.handle.value for l in lats])
     _check(load_library().iblbm_step_batch(arr, len(lats), nsteps), "iblbm_step_batch")
+
+
+def _lattice_desc(spec, storage=None, stream=0) -> LatticeDesc:
+    d = LatticeDesc()
+    d.nx, d.ny = spec.nx, spec.ny
+    d.storage = spec.storage if storage is None else storage
+    for s in range(4):
+        d.bc[s] = spec.bc[s]
+        d.u_bc[s][0], d.u_bc[s][1] = spec.ubc[s]
+    d.trt_lambda, d.cm_sq, d.cm_se = spec.trt_lambda, spec.cm_sq, spec.cm_se
+    d.force[0], d.force[1] = spec.force
+    d.init_rho = 1.0
+    d.init_u[0], d.init_u[1] = spec.init_u
+    d.cuda_stream = stream
+    return d
+
+
+class Server:
+    """Continuous-batching serving loop (``iblbm_server_*``)."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 64, stream: Optional[int] = None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        self._stream = stream
+        h = C.c_void_p()
+        _check(load_library().iblbm_server_create(int(hbm_budget), max_slots, stream, C.byref(h)),
+               "iblbm_server_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().iblbm_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, spec, nsteps: int, storage=None) -> int:
+        """Queues a case described like ``Lattice.from_spec`` (at most one body)."""
+        d = _lattice_desc(spec, storage, self._stream)
+        rid = C.c_longlong(0)
+        if spec.bodies:
+            b0 = spec.bodies[0]
+            b = BodyDesc()
+            b.xc, b.yc, b.radius, b.rho_ratio, b.motion = b0.xc, b0.yc, b0.radius, b0.rho_ratio, b0.motion
+            b.gx, b.gy, b.internal_mass = b0.gx, b0.gy, b0.internal_mass
+            b.mdf_nmin, b.mdf_nmax, b.mdf_tol, b.mdf_omega = b0.mdf_nmin, b0.mdf_nmax, b0.mdf_tol, b0.mdf_omega
+            b.osc_amp, b.osc_period, b.history_cap = b0.osc_amp, b0.osc_period, max(nsteps, 1)
+            xy = np.ascontiguousarray(b0.xy, dtype=np.float64).reshape(-1, 2)
+            rc = load_library().iblbm_server_submit(self._h, C.byref(d), spec.collision, spec.tau, C.byref(b),
+                                                    _dp(xy), len(xy), b0.ds, b0.kernel, b0.scheme, nsteps,
+                                                    C.byref(rid))
+        else:
+            rc = load_library().iblbm_server_submit(self._h, C.byref(d), spec.collision, spec.tau, None, None,
+                                                    0, 0.0, 0, 0, nsteps, C.byref(rid))
+        _check(rc, "iblbm_server_submit")
+        return rid.value
+
+    def tick(self, max_steps: int):
+        res, que = C.c_int(0), C.c_int(0)
+        done = _check(load_library().iblbm_server_tick(self._h, max_steps, C.byref(res), C.byref(que)),
+                      "iblbm_server_tick")
+        return done, res.value, que.value
+
+    def poll(self, req_id: int, cap: int = 1 << 20):
+        """Returns None while pending, else (force history (n, 3), latency seconds)."""
+        out = np.zeros((cap, 3))
+        n, lat = C.c_int(0), C.c_double(0)
+        rc = load_library().iblbm_server_poll(self._h, req_id, _dp(out), cap, C.byref(n), C.byref(lat))
+        if rc == 0:
+            return None
+        _check(rc, "iblbm_server_poll")
+        return out[:n.value].copy(), lat.value
+
+    def stats(self):
+        used, res, que = C.c_size_t(0), C.c_int(0), C.c_int(0)
+        _check(load_library().iblbm_server_stats(self._h, C.byref(used), C.byref(res), C.byref(que)),
+               "iblbm_server_stats")
+        return used.value, res.value, que.value

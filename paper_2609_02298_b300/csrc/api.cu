@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "iblbm.h"
+#include "internal.h"
 #include "kernels.cuh"
 
 using namespace iblbm;
@@ -229,6 +230,14 @@ int stencil_ok(int S, int nx, int ny, double X, double Y) {
 
 int body_index_ok(iblbm_ctx* c, int id) { return c && id >= 0 && id < (int)c->bodies.size(); }
 
+// Bounding-box capacity of a body whose markers lie within `reach` of its centre.
+int box_capacity(double reach, int S) {
+    const int side = 2 * (int)std::ceil(reach) + S + 4;
+    return side * side;
+}
+
+size_t rounded(size_t b) { return std::max<size_t>(256, (b + 255) & ~size_t(255)); }
+
 BodyDev fetch_body(iblbm_ctx* c, int id) {
     BodyDev b;
     cudaMemcpy(&b, &c->dbodies[id], sizeof(BodyDev), cudaMemcpyDeviceToHost);
@@ -384,8 +393,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
                 return IBLBM_ERR_BODY_OVERLAP;
     }
     const size_t rb = real_bytes(c->hc.storage);
-    const int side = 2 * (int)std::ceil(reach) + S + 4;
-    const int box_cap = side * side;
+    const int box_cap = box_capacity(reach, S);
     const int nent = n * S * S;
     const int hist_cap = bd->history_cap > 0 ? bd->history_cap : 65536;
     BodyDev B;
@@ -458,6 +466,12 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     for (int b = 0; b < id; ++b) {
         int zero = 0;
         cudaMemcpyAsync(&c->dbodies[b].lam_valid, &zero, sizeof(int), cudaMemcpyHostToDevice, w);
+    }
+    // MDF relaxation from the markers as given (Sec. 2.5.2: computed once at initialisation)
+    if (scheme == SCH_MDF) {
+        IbLaunch setup{c->drefs + id, 1, 1};
+        int rc = check(launch_ib(c->hc.storage, setup, w));
+        if (rc) return rc;
     }
     c->dirty = true;
     c->version++;
@@ -752,6 +766,25 @@ int iblbm_kernel_timing(iblbm_ctx* c, double* ms, int* launches) {
 
 }  // extern "C"
 
+// Device bytes a lattice plus one body of n markers will hold (mirrors the
+// allocations of iblbm_create and iblbm_add_body); used for admission.
+size_t iblbm_internal_estimate_bytes(const iblbm_lattice_desc* d, int n, double reach, int kernel, int hist_cap) {
+    const size_t pitch = ((size_t)(d->nx + 1 + 31) / 32) * 32;
+    const size_t plane = pitch * (size_t)d->ny;
+    size_t b = 2 * rounded(9 * plane * storage_bytes(d->storage));
+    b += rounded(sizeof(CaseDev)) + rounded(sizeof(BodyDev) * kMaxBodies) + rounded(sizeof(BodyRef) * kMaxBodies) +
+         rounded(sizeof(CaseDev*)) + rounded(2 * sizeof(long long));
+    if (n > 0) {
+        const int S = kernel == K_HAT ? 2 : 4;
+        const size_t nent = (size_t)n * S * S, rb = real_bytes(d->storage);
+        const size_t hc = hist_cap > 0 ? (size_t)hist_cap : 65536;
+        b += 9 * rounded(8 * (size_t)n) + rounded(4 * (size_t)box_capacity(reach, S)) + 3 * rounded(4 * nent) +
+             rounded(4 * (nent + 1)) + rounded(8 * (size_t)n) + rounded(rb * 8 * n) + 2 * rounded(rb * 9 * nent) +
+             rounded(rb * 16 * n) + rounded(24 * hc);
+    }
+    return b;
+}
+
 // ------------------------------------------------------------------------------------------
 // Batched stepping: one launch per kernel per storage type per step over a
 // case/tile table spanning every lattice of the batch.
@@ -907,6 +940,10 @@ int batch_capture(BatchPlan* P, int nsteps, cudaGraphExec_t* out) {
 }  // namespace
 
 extern "C" int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps) {
+    return iblbm_internal_step_batch(ctxs, n, nsteps, 1);
+}
+
+int iblbm_internal_step_batch(iblbm_ctx** ctxs, int n, int nsteps, int use_graphs) {
     if (!ctxs || n <= 0 || nsteps < 0) return IBLBM_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device) return IBLBM_ERR_INVALID_ARG;
@@ -926,8 +963,8 @@ extern "C" int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps) {
             cudaStreamWaitEvent(P->st, P->joins[i], 0);
         }
     }
-    if (lead->timing) {
-        for (int s = 0; s < nsteps && !rc; ++s) rc = check(launch_batch_step(P, P->st, lead));
+    if (lead->timing || !use_graphs) {
+        for (int s = 0; s < nsteps && !rc; ++s) rc = check(launch_batch_step(P, P->st, lead->timing ? lead : nullptr));
     } else {
         if (!P->graphs.one) {
             rc = batch_capture(P, 1, &P->graphs.one);

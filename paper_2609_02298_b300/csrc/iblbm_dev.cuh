@@ -6,8 +6,13 @@
 // and FP16 storage keep the small deviations from rest at full relative precision.
 #pragma once
 
+#ifdef IBLBM_EMULATE
+#include "cuda_emu.h"   // host-thread emulation used only by the CPU test suite
+#else
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#define IBLBM_LAUNCH(kern, grid, block, stream, ...) kern<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__)
+#endif
 #include <stdint.h>
 
 namespace iblbm {
@@ -117,12 +122,16 @@ __device__ __forceinline__ void ld16(const float* p, float (&v)[4]) {
     float4 t = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
+union Half8 {   // 16 bytes viewed as four half pairs (union punning, no aliasing casts)
+    uint4 u;
+    __half2 h[4];
+};
 __device__ __forceinline__ void ld16(const __half* p, float (&v)[8]) {
-    uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
-    const __half2* h = reinterpret_cast<const __half2*>(&t);
+    Half8 t;
+    t.u = __ldg(reinterpret_cast<const uint4*>(p));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float2 f = __half22float2(h[k]);
+        float2 f = __half22float2(t.h[k]);
         v[2 * k] = f.x; v[2 * k + 1] = f.y;
     }
 }
@@ -133,11 +142,10 @@ __device__ __forceinline__ void st16(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 __device__ __forceinline__ void st16(__half* p, const float (&v)[8]) {
-    uint4 t;
-    __half2* h = reinterpret_cast<__half2*>(&t);
+    Half8 t;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
-    *reinterpret_cast<uint4*>(p) = t;
+    for (int k = 0; k < 4; ++k) t.h[k] = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+    *reinterpret_cast<uint4*>(p) = t.u;
 }
 
 // ---- collision parameters held in registers ------------------------------------------

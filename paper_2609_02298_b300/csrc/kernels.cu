@@ -271,6 +271,19 @@ __device__ __forceinline__ int block_min_i(int v, int* sh) {
     __syncthreads();
     return r;
 }
+__device__ __forceinline__ int block_max_i(int v, int* sh) {
+    const int t = threadIdx.x;
+    __syncthreads();
+    sh[t] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] = max(sh[t], sh[t + s]);
+        __syncthreads();
+    }
+    const int r = sh[0];
+    __syncthreads();
+    return r;
+}
 
 // Footprint of a body: stencil origins and weights, bounding box, box-local
 // node -> slot map and a node -> marker CSR whose lists are sorted by marker
@@ -292,9 +305,9 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         }
         mnx = min(mnx, i0); mny = min(mny, j0); mxx = max(mxx, i0); mxy = max(mxy, j0);
     }
-    const int e = -block_min_i(-err, shi);
+    const int e = block_max_i(err, shi);
     const int bx0 = block_min_i(mnx, shi), by0 = block_min_i(mny, shi);
-    const int bx1 = -block_min_i(-mxx, shi) + Sx, by1 = -block_min_i(-mxy, shi) + Sx;
+    const int bx1 = block_max_i(mxx, shi) + Sx, by1 = block_max_i(mxy, shi) + Sx;
     const int bw = bx1 - bx0, bh = by1 - by0;
     if (e || (long long)bw * bh > B.box_cap) {
         if (tid == 0) {
@@ -438,6 +451,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
         }
         __syncthreads();
     }
+    if (L.mode == 1) return;
 
     // DFC lambda_k of Eq. 17; W_total sums the markers of every DFC body of the case.
     if (scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
@@ -833,9 +847,9 @@ static int grid_for(long long work) {
 cudaError_t launch_stream_collide(int storage, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
     if (jobs <= 0) return cudaSuccess;
     switch (storage) {
-    case ST_F64: sc_kernel<double><<<grid, kThreads, 0, st>>>(L, jobs); break;
-    case ST_F32: sc_kernel<float><<<grid, kThreads, 0, st>>>(L, jobs); break;
-    default: sc_kernel<__half><<<grid, kThreads, 0, st>>>(L, jobs); break;
+    case ST_F64: IBLBM_LAUNCH(sc_kernel<double>, grid, kThreads, st, L, jobs); break;
+    case ST_F32: IBLBM_LAUNCH(sc_kernel<float>, grid, kThreads, st, L, jobs); break;
+    default: IBLBM_LAUNCH(sc_kernel<__half>, grid, kThreads, st, L, jobs); break;
     }
     return cudaGetLastError();
 }
@@ -853,9 +867,9 @@ int sc_blocks_per_sm(int storage) {
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     if (L.nrefs <= 0) return cudaSuccess;
     switch (storage) {
-    case ST_F64: ib_kernel<double><<<L.nrefs, kThreads, 0, st>>>(L); break;
-    case ST_F32: ib_kernel<float><<<L.nrefs, kThreads, 0, st>>>(L); break;
-    default: ib_kernel<__half><<<L.nrefs, kThreads, 0, st>>>(L); break;
+    case ST_F64: IBLBM_LAUNCH(ib_kernel<double>, L.nrefs, kThreads, st, L); break;
+    case ST_F32: IBLBM_LAUNCH(ib_kernel<float>, L.nrefs, kThreads, st, L); break;
+    default: IBLBM_LAUNCH(ib_kernel<__half>, L.nrefs, kThreads, st, L); break;
     }
     return cudaGetLastError();
 }
@@ -863,16 +877,16 @@ cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
 cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st) {
     const int g = L.nrefs + (mode == 1 ? L.ncases : 0);
     if (g <= 0) return cudaSuccess;
-    body_kernel<<<g, kThreads, 0, st>>>(L, mode);
+    IBLBM_LAUNCH(body_kernel, g, kThreads, st, L, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st) {
     const int g = grid_for(9LL * hc->nx * hc->ny);
     switch (hc->storage) {
-    case ST_F64: export_kernel<double><<<g, 256, 0, st>>>(dc, out, shifted); break;
-    case ST_F32: export_kernel<float><<<g, 256, 0, st>>>(dc, out, shifted); break;
-    default: export_kernel<__half><<<g, 256, 0, st>>>(dc, out, shifted); break;
+    case ST_F64: IBLBM_LAUNCH(export_kernel<double>, g, 256, st, dc, out, shifted); break;
+    case ST_F32: IBLBM_LAUNCH(export_kernel<float>, g, 256, st, dc, out, shifted); break;
+    default: IBLBM_LAUNCH(export_kernel<__half>, g, 256, st, dc, out, shifted); break;
     }
     return cudaGetLastError();
 }
@@ -880,9 +894,9 @@ cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shift
 cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st) {
     const int g = grid_for(9LL * hc->nx * hc->ny);
     switch (hc->storage) {
-    case ST_F64: import_kernel<double><<<g, 256, 0, st>>>(dc, in); break;
-    case ST_F32: import_kernel<float><<<g, 256, 0, st>>>(dc, in); break;
-    default: import_kernel<__half><<<g, 256, 0, st>>>(dc, in); break;
+    case ST_F64: IBLBM_LAUNCH(import_kernel<double>, g, 256, st, dc, in); break;
+    case ST_F32: IBLBM_LAUNCH(import_kernel<float>, g, 256, st, dc, in); break;
+    default: IBLBM_LAUNCH(import_kernel<__half>, g, 256, st, dc, in); break;
     }
     return cudaGetLastError();
 }
@@ -890,9 +904,9 @@ cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cuda
 cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st) {
     const int g = grid_for(9LL * hc->plane);
     switch (hc->storage) {
-    case ST_F64: fill_eq_kernel<double><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
-    case ST_F32: fill_eq_kernel<float><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
-    default: fill_eq_kernel<__half><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    case ST_F64: IBLBM_LAUNCH(fill_eq_kernel<double>, g, 256, st, dc, rho, ux, uy); break;
+    case ST_F32: IBLBM_LAUNCH(fill_eq_kernel<float>, g, 256, st, dc, rho, ux, uy); break;
+    default: IBLBM_LAUNCH(fill_eq_kernel<__half>, g, 256, st, dc, rho, ux, uy); break;
     }
     return cudaGetLastError();
 }
@@ -900,9 +914,9 @@ cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, 
 cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux, double* uy, cudaStream_t st) {
     const int g = grid_for((long long)hc->nx * hc->ny);
     switch (hc->storage) {
-    case ST_F64: macro_kernel<double><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
-    case ST_F32: macro_kernel<float><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
-    default: macro_kernel<__half><<<g, 256, 0, st>>>(dc, rho, ux, uy); break;
+    case ST_F64: IBLBM_LAUNCH(macro_kernel<double>, g, 256, st, dc, rho, ux, uy); break;
+    case ST_F32: IBLBM_LAUNCH(macro_kernel<float>, g, 256, st, dc, rho, ux, uy); break;
+    default: IBLBM_LAUNCH(macro_kernel<__half>, g, 256, st, dc, rho, ux, uy); break;
     }
     return cudaGetLastError();
 }

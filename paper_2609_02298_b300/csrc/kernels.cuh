@@ -26,7 +26,7 @@ struct ScLaunch {
 struct IbLaunch {
     BodyRef* refs;
     int nrefs;
-    int pad_;
+    int mode;       // 0: full IB stage; 1: set-up only (footprint and omega_MDF at the initial markers)
 };
 
 struct FinLaunch {

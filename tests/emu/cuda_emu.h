@@ -1,0 +1,79 @@
+// CPU emulation shim for the library's CUDA sources (TEST INFRASTRUCTURE).
+//
+// Compiling the kernels and the host runtime with g++ and -DIBLBM_EMULATE runs
+// every kernel on host threads: one std::thread per CUDA thread of a block,
+// blocks one after another, __syncthreads and warp shuffles as barriers with
+// a deadlock timeout.  The CUDA runtime calls the library makes are served by
+// host memory.  It lets the parity tests exercise the kernel logic without a
+// GPU; it is never part of the product library.
+#pragma once
+
+#define __shared__ static
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#ifndef __launch_bounds__
+#define __launch_bounds__(...)
+#endif
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+
+namespace emu {
+struct ThreadCoord {
+    uint3 tid, bid;
+    dim3 bdim, gdim;
+};
+extern thread_local ThreadCoord tc;
+void syncthreads();
+uint64_t exchange(uint64_t v, int src_lane);   // warp exchange: value of lane src_lane
+int any(int pred);
+void launch(dim3 grid, dim3 block, std::function<void()> body, cudaStream_t st);
+}  // namespace emu
+
+#define threadIdx (emu::tc.tid)
+#define blockIdx (emu::tc.bid)
+#define blockDim (emu::tc.bdim)
+#define gridDim (emu::tc.gdim)
+
+inline void __syncthreads() { emu::syncthreads(); }
+
+template <class T>
+inline T __ldg(const T* p) { return *p; }
+
+template <class T>
+inline T emu_from_bits(uint64_t b) {
+    T v;
+    std::memcpy(&v, &b, sizeof(T));
+    return v;
+}
+template <class T>
+inline uint64_t emu_to_bits(T v) {
+    uint64_t b = 0;
+    std::memcpy(&b, &v, sizeof(T));
+    return b;
+}
+template <class T>
+inline T __shfl_up_sync(unsigned, T v, unsigned d) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int src = lane - (int)d;
+    return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src < 0 ? lane : src));
+}
+template <class T>
+inline T __shfl_down_sync(unsigned, T v, unsigned d) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int src = lane + (int)d;
+    return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src > 31 ? lane : src));
+}
+inline int __any_sync(unsigned, int pred) { return emu::any(pred); }
+
+inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned atomicOr(unsigned* p, unsigned v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
+
+using std::max;
+using std::min;
+
+#define IBLBM_LAUNCH(kern, grid, block, stream, ...) \
+    emu::launch(dim3(grid), dim3(block), [=]() { kern(__VA_ARGS__); }, (stream))

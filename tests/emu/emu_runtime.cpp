@@ -1,0 +1,277 @@
+// Host emulation of the CUDA runtime calls and execution model used by the
+// library (TEST INFRASTRUCTURE, see cuda_emu.h).  Blocks run one at a time on
+// a pool of host threads, one per CUDA thread; barriers abort on deadlock.
+#include "cuda_emu.h"
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace emu {
+
+thread_local ThreadCoord tc;
+
+namespace {
+
+struct Barrier {
+    std::mutex m;
+    std::condition_variable cv;
+    int n = 0, count = 0;
+    unsigned gen = 0;
+    void wait(const char* what) {
+        std::unique_lock<std::mutex> lk(m);
+        const unsigned g = gen;
+        if (++count == n) {
+            count = 0;
+            ++gen;
+            cv.notify_all();
+            return;
+        }
+        if (!cv.wait_for(lk, std::chrono::seconds(60), [&] { return gen != g; })) {
+            std::fprintf(stderr, "emu: %s barrier timed out (divergent barrier)\n", what);
+            std::abort();
+        }
+    }
+};
+
+constexpr int kMaxThreads = 256;
+
+struct Pool {
+    std::vector<std::thread> workers;
+    std::mutex m;
+    std::condition_variable cv_go, cv_done;
+    unsigned long long go_gen = 0;
+    int active = 0, remaining = 0;
+    bool stop = false;
+    std::function<void()> body;
+    ThreadCoord base;
+    Barrier block_bar;
+    Barrier warp_bar[kMaxThreads / 32];
+    uint64_t warp_buf[kMaxThreads / 32][32];
+
+    Pool() {
+        for (int i = 0; i < kMaxThreads; ++i) workers.emplace_back([this, i] { run(i); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(m);
+            stop = true;
+            ++go_gen;
+        }
+        cv_go.notify_all();
+        for (auto& w : workers) w.join();
+    }
+    void run(int i) {
+        unsigned long long seen = 0;
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> lk(m);
+                cv_go.wait(lk, [&] { return stop || go_gen != seen; });
+                if (stop) return;
+                seen = go_gen;
+                if (i >= active) continue;
+                f = body;
+                tc = base;
+                tc.tid = make_uint3((unsigned)i, 0, 0);
+            }
+            f();
+            {
+                std::lock_guard<std::mutex> lk(m);
+                if (--remaining == 0) cv_done.notify_all();
+            }
+        }
+    }
+    void run_block(const ThreadCoord& c, int nthreads, const std::function<void()>& f) {
+        std::unique_lock<std::mutex> lk(m);
+        body = f;
+        base = c;
+        active = nthreads;
+        remaining = nthreads;
+        block_bar.n = nthreads;
+        for (int w = 0; w < (nthreads + 31) / 32; ++w) warp_bar[w].n = std::min(32, nthreads - 32 * w);
+        ++go_gen;
+        cv_go.notify_all();
+        cv_done.wait(lk, [&] { return remaining == 0; });
+    }
+};
+
+Pool& pool() {
+    static Pool* p = new Pool();   // never destroyed: workers live until exit
+    return *p;
+}
+
+struct Capture {
+    std::vector<std::function<void()>> ops;
+};
+std::map<cudaStream_t, std::shared_ptr<Capture>> g_capturing;
+std::mutex g_launch_mu;
+
+void run_now(dim3 grid, dim3 block, const std::function<void()>& body) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    const int nthreads = (int)(block.x * block.y * block.z);
+    if (nthreads > kMaxThreads || block.y != 1 || block.z != 1) {
+        std::fprintf(stderr, "emu: unsupported block shape\n");
+        std::abort();
+    }
+    for (unsigned bz = 0; bz < grid.z; ++bz)
+        for (unsigned by = 0; by < grid.y; ++by)
+            for (unsigned bx = 0; bx < grid.x; ++bx) {
+                ThreadCoord c;
+                c.bid = make_uint3(bx, by, bz);
+                c.bdim = block;
+                c.gdim = grid;
+                pool().run_block(c, nthreads, body);
+            }
+}
+
+}  // namespace
+
+void syncthreads() { pool().block_bar.wait("block"); }
+
+uint64_t exchange(uint64_t v, int src_lane) {
+    Pool& p = pool();
+    const int w = (int)(tc.tid.x / 32), lane = (int)(tc.tid.x & 31u);
+    p.warp_buf[w][lane] = v;
+    p.warp_bar[w].wait("warp");
+    const uint64_t r = p.warp_buf[w][src_lane];
+    p.warp_bar[w].wait("warp");
+    return r;
+}
+
+int any(int pred) {
+    Pool& p = pool();
+    const int w = (int)(tc.tid.x / 32), lane = (int)(tc.tid.x & 31u);
+    p.warp_buf[w][lane] = pred ? 1 : 0;
+    p.warp_bar[w].wait("warp");
+    int r = 0;
+    for (int l = 0; l < p.warp_bar[w].n; ++l) r |= (int)p.warp_buf[w][l];
+    p.warp_bar[w].wait("warp");
+    return r;
+}
+
+void launch(dim3 grid, dim3 block, std::function<void()> body, cudaStream_t st) {
+    auto it = g_capturing.find(st);
+    if (it != g_capturing.end()) {
+        it->second->ops.push_back([grid, block, body] { run_now(grid, block, body); });
+        return;
+    }
+    run_now(grid, block, body);
+}
+
+}  // namespace emu
+
+// ---- runtime API --------------------------------------------------------------------------
+struct EmuEvent {
+    std::chrono::steady_clock::time_point t;
+};
+struct EmuGraph {
+    std::vector<std::function<void()>> ops;
+};
+
+extern "C" {
+
+cudaError_t cudaMalloc(void** p, size_t n) {
+    *p = std::aligned_alloc(256, (n + 255) & ~size_t(255));
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaFree(void* p) {
+    std::free(p);
+    return cudaSuccess;
+}
+cudaError_t cudaMemcpy(void* d, const void* s, size_t n, cudaMemcpyKind) {
+    std::memmove(d, s, n);
+    return cudaSuccess;
+}
+cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, cudaMemcpyKind, cudaStream_t) {
+    std::memmove(d, s, n);
+    return cudaSuccess;
+}
+cudaError_t cudaMemsetAsync(void* d, int v, size_t n, cudaStream_t) {
+    std::memset(d, v, n);
+    return cudaSuccess;
+}
+cudaError_t cudaGetDevice(int* d) {
+    *d = 0;
+    return cudaSuccess;
+}
+cudaError_t cudaDeviceGetAttribute(int* v, cudaDeviceAttr a, int) {
+    *v = (a == cudaDevAttrMultiProcessorCount) ? 2 : 1;
+    return cudaSuccess;
+}
+cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, const void*, int, size_t) {
+    *n = 1;
+    return cudaSuccess;
+}
+cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(int* n, const void*, int, size_t, unsigned) {
+    *n = 1;
+    return cudaSuccess;
+}
+cudaError_t cudaGetLastError(void) { return cudaSuccess; }
+cudaError_t cudaDeviceSynchronize(void) { return cudaSuccess; }
+cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaStreamCreateWithFlags(cudaStream_t* s, unsigned) {
+    *s = reinterpret_cast<cudaStream_t>(new char[16]);
+    return cudaSuccess;
+}
+cudaError_t cudaStreamDestroy(cudaStream_t s) {
+    delete[] reinterpret_cast<char*>(s);
+    return cudaSuccess;
+}
+cudaError_t cudaEventCreate(cudaEvent_t* e) {
+    *e = reinterpret_cast<cudaEvent_t>(new EmuEvent());
+    return cudaSuccess;
+}
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned) { return cudaEventCreate(e); }
+cudaError_t cudaEventDestroy(cudaEvent_t e) {
+    delete reinterpret_cast<EmuEvent*>(e);
+    return cudaSuccess;
+}
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
+    reinterpret_cast<EmuEvent*>(e)->t = std::chrono::steady_clock::now();
+    return cudaSuccess;
+}
+cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t a, cudaEvent_t b) {
+    *ms = std::chrono::duration<float, std::milli>(reinterpret_cast<EmuEvent*>(b)->t -
+                                                   reinterpret_cast<EmuEvent*>(a)->t).count();
+    return cudaSuccess;
+}
+cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned) { return cudaSuccess; }
+cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode) {
+    emu::g_capturing[s] = std::make_shared<emu::Capture>();
+    return cudaSuccess;
+}
+cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t* g) {
+    auto it = emu::g_capturing.find(s);
+    if (it == emu::g_capturing.end()) return cudaErrorIllegalState;
+    EmuGraph* eg = new EmuGraph();
+    eg->ops = it->second->ops;
+    emu::g_capturing.erase(it);
+    *g = reinterpret_cast<cudaGraph_t>(eg);
+    return cudaSuccess;
+}
+cudaError_t cudaGraphInstantiate(cudaGraphExec_t* x, cudaGraph_t g, unsigned long long) {
+    EmuGraph* eg = new EmuGraph(*reinterpret_cast<EmuGraph*>(g));
+    *x = reinterpret_cast<cudaGraphExec_t>(eg);
+    return cudaSuccess;
+}
+cudaError_t cudaGraphDestroy(cudaGraph_t g) {
+    delete reinterpret_cast<EmuGraph*>(g);
+    return cudaSuccess;
+}
+cudaError_t cudaGraphExecDestroy(cudaGraphExec_t x) {
+    delete reinterpret_cast<EmuGraph*>(x);
+    return cudaSuccess;
+}
+cudaError_t cudaGraphLaunch(cudaGraphExec_t x, cudaStream_t) {
+    for (auto& op : reinterpret_cast<EmuGraph*>(x)->ops) op();
+    return cudaSuccess;
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+"""Parity checks of the library (through its C ABI) against the FP64 CPU oracle,
+written once and run twice: on the B300 by test_gpu_parity.py at full sizes,
+and on the host-thread emulation of the same sources by test_emu_parity.py at
+small sizes.
+
+Bars: streaming permutations and stencil indices bit-exact; FP64 storage within
+1e-12 relative L2 (populations' deviation from rest and velocity); FP32 shifted
+storage within 1e-5 relative L2 on velocity and 1e-4 on drag and lift
+(relative to the drag); FP16 shifted storage within the round-off bound derived
+in check_f16_storage."""
+import math
+
+import numpy as np
+
+import workloads as W
+from harness import W9, channel_spec, cylinder_body, gpu_case, oracle_case, rel_l2, velocity
+
+F64_TOL = 1e-12
+
+
+def dev(f):
+    """Deviation of populations from the rest weights (what carries the flow)."""
+    return f - W9[:, None, None]
+
+
+def stepped(g, c, n):
+    g.step(n)
+    c.step(n)
+    assert g.sync() >= 0
+
+
+def assert_f64_state(fg, fc, u_ref):
+    """FP64 bar for flows that start from rest: populations within 1e-12 of the
+    oracle's (max norm, relative to max|f|), and velocity within 1e-12 relative
+    L2 with the norm floored at u_ref per node.  The floor is needed because the
+    oracle keeps f unshifted (f ~ 0.44), so its own round-off (~1e-16 absolute)
+    is ~1e-12 of the velocity while the flow is still ~1e-4."""
+    assert np.abs(fg - fc).max() < F64_TOL * np.abs(fc).max()
+    ug, uc = np.stack(velocity(fg)), np.stack(velocity(fc))
+    den = max(np.sqrt((uc ** 2).sum()), u_ref * np.sqrt(uc[0].size))
+    assert np.sqrt(((ug - uc) ** 2).sum()) / den < F64_TOL
+
+
+# ---------------------------------------------------------------- streaming
+def check_streaming_bit_exact(storage, dt, nx, ny, full_cycle=True):
+    f0 = W.random_populations(11, nx, ny)
+    spec = W.CaseSpec(name="s", nx=nx, ny=ny, bc=(W.PERIODIC,) * 4, ubc=((0, 0),) * 4,
+                      collision=W.STREAM_ONLY, tau=0.8, storage=storage)
+    g = gpu_case(spec)
+    g.set_populations(f0)
+    stored0 = g.populations(shifted=True)
+    np.testing.assert_array_equal(stored0, (f0 - W9[:, None, None]).astype(dt).astype(np.float64))
+    c = oracle_case(spec)
+    c.set_populations(stored0)   # the permutation is value-blind: feed it the stored values
+    stepped(g, c, 1)
+    np.testing.assert_array_equal(g.populations(shifted=True), c.populations())
+    if full_cycle:
+        g.step(math.lcm(nx, ny) - 1)          # every population back at its start
+        np.testing.assert_array_equal(g.populations(shifted=True), stored0)
+
+
+# ---------------------------------------------------------------- collision
+def check_periodic_collision_f64(collision, nx=70, ny=23, steps=25):
+    f0 = W.random_populations(12, nx, ny, amp=0.05)
+    spec = W.CaseSpec(name="p", nx=nx, ny=ny, bc=(W.PERIODIC,) * 4, ubc=((0, 0),) * 4,
+                      collision=collision, tau=0.73, storage=W.F64, trt_lambda=3 / 16)
+    g, c = gpu_case(spec), oracle_case(spec)
+    g.set_populations(f0)
+    c.set_populations(f0)
+    stepped(g, c, steps)
+    fg, fc = g.populations(), c.populations()
+    assert rel_l2(dev(fg), dev(fc)) < F64_TOL
+    assert rel_l2(np.stack(velocity(fg)), np.stack(velocity(fc))) < F64_TOL
+
+
+def check_uniform_force_f64(collision, nx=40, ny=21, steps=300):
+    spec = W.CaseSpec(name="pf", nx=nx, ny=ny, bc=(W.PERIODIC, W.PERIODIC, W.VELOCITY, W.VELOCITY),
+                      ubc=((0, 0),) * 4, collision=collision, tau=0.8, storage=W.F64, force=(2e-5, -1e-5))
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    assert rel_l2(np.stack(velocity(g.populations())), np.stack(velocity(c.populations()))) < F64_TOL
+    rg, uxg, uyg = g.macro()
+    rc, uxc, uyc = c.macro()
+    assert rel_l2(np.stack([uxg, uyg]), np.stack([uxc, uyc])) < F64_TOL and rel_l2(rg, rc) < F64_TOL
+
+
+# ---------------------------------------------------------------- domain conditions
+BC_SETS = {
+    "channel": ((W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY), ((0.05, 0), (0, 0), (0.05, 0), (0.05, 0))),
+    "open": ((W.NEUMANN,) * 4, ((0, 0),) * 4),
+    "walls": ((W.VELOCITY,) * 4, ((0, 0), (0, 0), (0, 0), (0.03, 0.0))),
+    "periodic-y": ((W.VELOCITY, W.NEUMANN, W.PERIODIC, W.PERIODIC), ((0.04, 0), (0, 0), (0, 0), (0, 0))),
+    "periodic-x": ((W.PERIODIC, W.PERIODIC, W.VELOCITY, W.NEUMANN), ((0, 0), (0, 0), (0.0, 0.0), (0, 0))),
+}
+
+
+def check_domain_conditions_f64(name, nx, ny, storage=W.F64, rounds=3, steps=7):
+    bc, ubc = BC_SETS[name]
+    f0 = W.random_populations(13, nx, ny, amp=0.02)
+    spec = W.CaseSpec(name=name, nx=nx, ny=ny, bc=bc, ubc=ubc, collision=W.BGK, tau=0.7, storage=storage)
+    g, c = gpu_case(spec), oracle_case(spec)
+    g.set_populations(f0)
+    c.set_populations(f0)
+    for _ in range(rounds):
+        stepped(g, c, steps)
+        assert rel_l2(dev(g.populations()), dev(c.populations())) < F64_TOL
+
+
+# ---------------------------------------------------------------- immersed boundary
+def check_ib_channel_f64(scheme, kernel, collision, nx=150, ny=64, D=16.0, n=47, steps=60):
+    body = cylinder_body(0.27 * nx, 0.495 * ny, D, n, kernel, scheme, mdf_nmin=2, mdf_nmax=12, mdf_tol=1e-4)
+    spec = channel_spec(nx, ny, collision=collision, tau=0.68, storage=W.F64, u=0.06, bodies=[body])
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    fg, fc = g.populations(), c.populations()
+    assert rel_l2(dev(fg), dev(fc)) < F64_TOL
+    ug, uc = velocity(fg), velocity(fc)
+    assert rel_l2(np.stack([ug[0] - 0.06, ug[1]]), np.stack([uc[0] - 0.06, uc[1]])) < F64_TOL
+    Fg, Fc = g.body_forces(0), c.body_forces(0)
+    assert np.abs(Fg - Fc).max() < 1e-12 * np.abs(Fc[:2]).max()
+    np.testing.assert_array_equal(g.marker_stencils(0), c.marker_stencils(0))
+    mg, mc = g.marker_data(0), c.marker_data(0)
+    assert rel_l2(mg[:, 4:6], mc[:, 4:6]) < F64_TOL
+    if scheme == W.DFC:
+        assert rel_l2(mg[:, 6], mc[:, 6]) < F64_TOL
+    if scheme == W.MDF:
+        it, res, om = g.mdf_info(0)
+        assert it == c.mdf_iterations(0)
+        assert abs(om - c.mdf_omega(0)) < 1e-13 * c.mdf_omega(0)
+        assert abs(res - c.mdf_residual(0)) < 1e-9 * c.mdf_residual(0) + 1e-15
+    hg, hc = g.force_history(0), c.force_history(0)
+    assert hg.shape == hc.shape
+    assert np.abs(hg - hc).max() < 1e-12 * np.abs(hc[:, :2]).max()
+
+
+def check_cylinder_re20_f64(steps=2000, nx=200):
+    """200x100 lattice, D=20, 63 markers, DF + hat + BGK, U=0.05, tau=0.65."""
+    spec = W.fixed_cylinder_re20(storage=W.F64, steps=steps)
+    spec.nx = nx
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    fg, fc = g.populations(), c.populations()
+    assert rel_l2(np.stack(velocity(fg)), np.stack(velocity(fc))) < F64_TOL
+    hg, hc = g.force_history(0), c.force_history(0)
+    scale = 0.5 * 0.05 ** 2 * 20.0
+    assert np.abs(hg[:, :2] - hc[:, :2]).max() / scale < 1e-12 * np.abs(hc[:, 0] / scale).max()
+
+
+def check_cylinder_re20_f32(steps=2000, nx=200):
+    """FP32 shifted storage: velocity within 1e-5 relative L2; drag and lift
+    coefficients within 1e-4 (relative to the drag) of the FP64 oracle."""
+    spec = W.fixed_cylinder_re20(storage=W.F32, steps=steps)
+    spec.nx = nx
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    ug, uc = velocity(g.populations()), velocity(c.populations())
+    assert rel_l2(np.stack(ug), np.stack(uc)) < 1e-5
+    hg, hc = g.force_history(0), c.force_history(0)
+    scale = 0.5 * 0.05 ** 2 * 20.0
+    cd_c = hc[:, 0] / scale
+    assert np.abs(hg[:, 0] - hc[:, 0]).max() / scale < 1e-4 * np.abs(cd_c).max()
+    assert np.abs(hg[:, 1] - hc[:, 1]).max() / scale < 1e-4 * np.abs(cd_c).max()
+
+
+def check_f16_storage(steps=300, nx=200):
+    """FP16 stores s = f - w with unit round-off u16 = 2^-11.  One rounding per
+    stored population per step perturbs the velocity by at most about
+    max|s| u16 / |u| relative; a dissipative flow accumulates these like a
+    random walk, so the bound taken is 3 sqrt(n) u16 max|s| / |U|."""
+    spec = W.fixed_cylinder_re20(storage=W.F16S, steps=steps)
+    spec.nx = nx
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    fc = c.populations()
+    ug, uc = velocity(g.populations()), velocity(fc)
+    smax = np.abs(dev(fc)).max()
+    bound = 3.0 * math.sqrt(steps) * 2.0 ** -11 * smax / 0.05
+    assert rel_l2(np.stack(ug), np.stack(uc)) < bound
+
+
+# ---------------------------------------------------------------- moving bodies
+def check_prescribed_oscillation_f64(nx=128, ny=96, D=16.0, steps=120):
+    spec = W.oscillating_cylinder(storage=W.F64, kernel=W.PESKIN4, scheme=W.DF, nx=nx, ny=ny, diameter=D,
+                                  kc=5.0, u_max=0.05, re=60.0)
+    spec.bodies[0].osc_amp = 0.2 * D
+    spec.bodies[0].osc_period = 160.0
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.05)
+    np.testing.assert_allclose(g.body_state(0), c.body_state(0), rtol=1e-13, atol=1e-15)
+    mg, mc = g.marker_data(0), c.marker_data(0)
+    np.testing.assert_allclose(mg[:, :4], mc[:, :4], rtol=1e-13, atol=1e-13)
+
+
+def check_free_body_f64(scheme, internal_mass, nx=64, ny=160, D=12.0, steps=150):
+    spec = W.sedimentation(two_particles=False, storage=W.F64, internal_mass=internal_mass,
+                           kernel=W.PESKIN4, scheme=scheme, nx=nx, ny=ny, diameter=D, tau=0.7, g=4e-4)
+    spec.bodies[0].mdf_nmin, spec.bodies[0].mdf_nmax = 3, 10
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    sg, sc = g.body_state(0), c.body_state(0)
+    np.testing.assert_allclose(sg, sc, rtol=1e-11, atol=1e-14)
+    assert sc[3] < 0.0                                     # settling down
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
+    np.testing.assert_array_equal(g.marker_stencils(0), c.marker_stencils(0))
+
+
+def check_two_particle_dfc_f64(nx=64, ny=200, D=10.0, steps=80):
+    spec = W.sedimentation(two_particles=True, storage=W.F64, kernel=W.PESKIN4, scheme=W.DFC, nx=nx,
+                           ny=ny, diameter=D, tau=0.7, g=4e-4)
+    y0 = 0.6 * ny
+    for b, yc in zip(spec.bodies, (y0, y0 + 1.5 * D)):
+        b.xy, b.ds = W.circle_markers(b.xc, yc, D, 31)
+        b.yc = yc
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    for b in range(2):
+        np.testing.assert_allclose(g.body_state(b), c.body_state(b), rtol=1e-11, atol=1e-14)
+        assert rel_l2(g.marker_data(b)[:, 6], c.marker_data(b)[:, 6]) < F64_TOL
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
+
+
+# ---------------------------------------------------------------- batching, checkpoints, errors
+def batch_specs(scale=1.0):
+    s = lambda v: max(8, int(v * scale))  # noqa: E731
+    return [
+        channel_spec(s(150), s(64), collision=W.BGK, storage=W.F32,
+                     bodies=[cylinder_body(0.27 * s(150), 0.49 * s(64), 16.0 * scale, max(16, int(47 * scale)),
+                                           W.PESKIN4, W.DF)]),
+        channel_spec(s(96), s(40), collision=W.TRT, storage=W.F32,
+                     bodies=[cylinder_body(0.31 * s(96), 0.5 * s(40), 10.0 * scale, max(12, int(31 * scale)),
+                                           W.HAT, W.DFC)]),
+        channel_spec(s(200), s(50), collision=W.CMMRT, storage=W.F16S,
+                     bodies=[cylinder_body(0.25 * s(200), 0.5 * s(50), 12.0 * scale, max(12, int(37 * scale)),
+                                           W.PESKIN4, W.MDF, mdf_nmin=5, mdf_nmax=5)]),
+        channel_spec(s(64), s(64), collision=W.BGK, storage=W.F64),
+    ]
+
+
+def check_batch_equals_alone(L, specs, steps=37):
+    alone = [gpu_case(s) for s in specs]
+    mixed = [gpu_case(s) for s in specs]
+    for a in alone:
+        a.step(steps)
+    L.step_batch(mixed, steps)
+    for a, m in zip(alone, mixed):
+        assert m.sync() >= 0
+        np.testing.assert_array_equal(a.populations(shifted=True), m.populations(shifted=True))
+        if a.body_n:
+            np.testing.assert_array_equal(a.force_history(0), m.force_history(0))
+
+
+def check_snapshot_restore(nx=64, ny=160, D=12.0, steps=(40, 30)):
+    spec = W.sedimentation(two_particles=False, storage=W.F32, kernel=W.PESKIN4, scheme=W.DFC, nx=nx,
+                           ny=ny, diameter=D, tau=0.7, g=4e-4)
+    a = gpu_case(spec)
+    a.step(steps[0])
+    blob = a.snapshot()
+    a.step(steps[1])
+    b = gpu_case(spec)
+    b.restore(blob)
+    b.step(steps[1])
+    np.testing.assert_array_equal(a.populations(shifted=True), b.populations(shifted=True))
+    np.testing.assert_array_equal(a.body_state(0), b.body_state(0))
+    np.testing.assert_array_equal(a.force_history(0), b.force_history(0))
+
+
+def check_graph_equals_direct(nx=150, ny=64, steps=33):
+    spec = channel_spec(nx, ny, collision=W.BGK, storage=W.F32,
+                        bodies=[cylinder_body(0.27 * nx, 0.49 * ny, 16.0, 47, W.PESKIN4, W.MDF,
+                                              mdf_nmin=5, mdf_nmax=5)])
+    a, b = gpu_case(spec), gpu_case(spec)
+    a.step(steps)
+    b.set_timing(True)
+    b.step(steps)
+    ms, n = b.kernel_timing()
+    assert n == steps and ms >= 0
+    np.testing.assert_array_equal(a.populations(shifted=True), b.populations(shifted=True))
+
+
+def check_marker_out_of_domain(L, steps=200):
+    spec = W.sedimentation(two_particles=False, storage=W.F32, kernel=W.PESKIN4, scheme=W.DF, nx=40,
+                           ny=60, diameter=10.0, tau=0.7, g=5e-2)
+    spec.bodies[0].xy, spec.bodies[0].ds = W.circle_markers(20.0, 12.0, 10.0, 31)
+    spec.bodies[0].yc = 12.0
+    g = gpu_case(spec)
+    g.step(steps)
+    try:
+        g.sync()
+    except L.IblbmError as e:
+        assert e.code == -4
+    else:
+        raise AssertionError("a marker left the lattice but no error was reported")

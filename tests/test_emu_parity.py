@@ -1,0 +1,110 @@
+"""The parity checks of parity_cases.py run on CPU through the host-thread
+emulation of the library's own CUDA sources (tests/emu): same kernels, same C
+ABI, small lattices.  This exercises the kernel logic (streaming, domain
+conditions, footprint CSR, DF/MDF/DFC, rigid bodies, batching, checkpoints)
+without a GPU; the B300 run of test_gpu_parity.py is the parity claim."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import workloads as W
+import parity_cases as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "emu"))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import build_emu
+    import paper_2609_02298_b300 as lib
+    path = build_emu.build()
+    saved = lib._lib
+    lib._lib = None
+    lib.load_library(path)
+    yield lib
+    lib._close_all()
+    lib._lib = saved
+
+
+SCHEMES = [W.DF, W.MDF, W.DFC]
+KERNELS = [W.HAT, W.PESKIN4]
+COLLS = [W.BGK, W.TRT, W.CMMRT]
+
+
+@pytest.mark.parametrize("storage,dt", [(W.F64, np.float64), (W.F32, np.float32), (W.F16S, np.float16)])
+@pytest.mark.parametrize("nx,ny", [(7, 7), (37, 5)])
+def test_streaming_bit_exact(L, storage, dt, nx, ny):
+    P.check_streaming_bit_exact(storage, dt, nx, ny, full_cycle=(nx == 7))
+
+
+@pytest.mark.parametrize("collision", COLLS)
+def test_periodic_collision_f64(L, collision):
+    P.check_periodic_collision_f64(collision, nx=20, ny=9, steps=4)
+
+
+@pytest.mark.parametrize("collision", COLLS)
+def test_uniform_force_f64(L, collision):
+    P.check_uniform_force_f64(collision, nx=6, ny=9, steps=30)
+
+
+@pytest.mark.parametrize("name", list(P.BC_SETS))
+@pytest.mark.parametrize("nx,ny", [(37, 7), (65, 5), (5, 6)])
+def test_domain_conditions_f64(L, name, nx, ny):
+    P.check_domain_conditions_f64(name, nx, ny, rounds=2, steps=2)
+
+
+@pytest.mark.parametrize("name", ["channel", "open"])
+@pytest.mark.parametrize("storage", [W.F32, W.F16S])
+def test_domain_conditions_narrow_types(L, name, storage):
+    """FP32/FP16 vector paths (4 and 8 nodes per lane) against the FP64 oracle:
+    one step, tolerance of the storage round-off."""
+    bc, ubc = P.BC_SETS[name]
+    from harness import gpu_case, oracle_case, rel_l2
+    f0 = W.random_populations(13, 133, 6, amp=0.02)
+    spec = W.CaseSpec(name=name, nx=133, ny=6, bc=bc, ubc=ubc, collision=W.BGK, tau=0.7, storage=storage)
+    g, c = gpu_case(spec), oracle_case(spec)
+    g.set_populations(f0)
+    c.set_populations(g.populations())
+    g.step(1)
+    c.step(1)
+    tol = 1e-6 if storage == W.F32 else 2e-3
+    assert rel_l2(P.dev(g.populations()), P.dev(c.populations())) < tol
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("collision", COLLS)
+def test_ib_channel_f64(L, scheme, kernel, collision):
+    P.check_ib_channel_f64(scheme, kernel, collision, nx=36, ny=24, D=8.0, n=23, steps=3)
+
+
+def test_prescribed_oscillation_f64(L):
+    P.check_prescribed_oscillation_f64(nx=40, ny=24, D=8.0, steps=4)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_free_body_f64(L, scheme):
+    P.check_free_body_f64(scheme, 1, nx=24, ny=64, D=6.0, steps=4)
+
+
+def test_two_particle_dfc_f64(L):
+    P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3)
+
+
+def test_batch_equals_alone_bitwise(L):
+    P.check_batch_equals_alone(L, P.batch_specs(scale=0.3), steps=3)
+
+
+def test_snapshot_restore_continues_bitwise(L):
+    P.check_snapshot_restore(nx=24, ny=64, D=6.0, steps=(2, 2))
+
+
+def test_graph_replay_equals_timed_launches(L):
+    P.check_graph_equals_direct(nx=40, ny=24, steps=3)
+
+
+def test_marker_out_of_domain_is_reported(L):
+    P.check_marker_out_of_domain(L, steps=60)
