@@ -47,6 +47,27 @@ def matrix_specs(storage=W.F32, res=(100.0, 200.0), nx=2048, ny=1024):
     return specs
 
 
+def shard(items, rank: int, world: int):
+    """Independent cases (lattices, requests) handed to ranks round-robin; no
+    data-path exchange is needed between ranks (replicas, weak scaling)."""
+    return list(items)[rank::world]
+
+
+def aggregate(nodes_local: int, steps: int, ms_local: float, dist=None, device="cpu"):
+    """Whole-job MLUPS: lattice updates of all ranks over the slowest rank's time."""
+    import torch
+    t = torch.tensor([ms_local, float(nodes_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        mx = t[:1].clone()
+        sm = t[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, nodes_all = float(mx.item()), float(sm.item())
+    else:
+        ms_max, nodes_all = ms_local, float(nodes_local)
+    return nodes_all * steps / (ms_max / 1e3) / 1e6, ms_max
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -126,6 +147,72 @@ def cpu_baseline(spec, budget_s: float = 15.0):
     return spec.nodes * n / dt / 1e6, n, dt
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed=0, grids=None):
+    """Serving stream of seeded requests (grids 128x64 .. 2048x1024, random
+    scheme/kernel/collision, Re in [20, 200], FP32): capacity with every request
+    queued at once, then Poisson arrivals at 0.5x and 0.9x that capacity through
+    the continuous-batching server, and one case at a time (graph-replayed
+    iblbm_step) at 0.5x; p50/p99 time-to-result for each."""
+    _, specs, resampled = W.serving_requests(seed=seed, n=n_requests, rate=1.0, steps=steps, grids=grids)
+    budget = int(budget_gb * 1e9)
+
+    def run_server(arrivals):
+        srv = L.Server(budget, max_slots=128)
+        t0 = time.perf_counter()
+        pending = list(zip(arrivals, specs))
+        ids = []
+        done = 0
+        while done < len(specs):
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                ids.append(srv.submit(pending.pop(0)[1], steps))
+            if done == len(ids) and pending:
+                time.sleep(max(0.0, min(0.01, pending[0][0] - now)))
+                continue
+            k, _, _ = srv.tick(tick)
+            done += k
+        wall = time.perf_counter() - t0
+        lats = [srv.poll(i, cap=4)[1] for i in ids]
+        srv.close()
+        return {"cases_per_s": len(specs) / wall, "p50_s": _pct(lats, 50), "p99_s": _pct(lats, 99),
+                "wall_s": wall}
+
+    cap = run_server([0.0] * len(specs))
+    rate_cap = cap["cases_per_s"]
+    out = {"requests": len(specs), "steps_per_request": steps, "tau_resampled": resampled,
+           "budget_gb": budget_gb, "tick_steps": tick, "capacity": cap}
+    rng = np.random.default_rng(seed + 1)
+    gaps = rng.exponential(1.0, size=len(specs))
+    for frac in (0.5, 0.9):
+        arr = list(np.cumsum(gaps) / (frac * rate_cap))
+        out["rate_%.1fx" % frac] = dict(run_server(arr), rate_per_s=frac * rate_cap)
+    # one case at a time, same arrivals as the 0.5x run
+    arr = list(np.cumsum(gaps) / (0.5 * rate_cap))
+    t0 = time.perf_counter()
+    lats = []
+    for a, sp in zip(arr, specs):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        lat = L.Lattice.from_spec(sp)
+        lat.step(steps)
+        lat.force_history(0, cap=4)
+        lat.close()
+        lats.append(time.perf_counter() - t0 - a)
+    wall = time.perf_counter() - t0
+    out["sequential_0.5x"] = {"cases_per_s": len(specs) / wall, "p50_s": _pct(lats, 50), "p99_s": _pct(lats, 99),
+                              "wall_s": wall}
+    return out
+
+
 def run_reference(args, specs):
     """--impl reference: the oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -166,6 +253,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=5.0)
     ap.add_argument("--lattices", type=int, default=0,
                     help="use only the first K lattices of the matrix (profiling a smaller case)")
+    ap.add_argument("--serving-requests", type=int, default=256,
+                    help="requests in the serving stream (0: not reported)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     nx, ny = (256, 128) if args.small else (2048, 1024)
@@ -226,11 +315,7 @@ def main():
     lead.set_timing(False)
     for l in lats:
         rc = l.sync()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = nodes * args.steps * world / (ms_max / 1e3) / 1e6
+    value, ms_max = aggregate(nodes, args.steps, ms, dist, device="cuda")
 
     # roofline of the dominant kernel (stream-collide over all lattices)
     peak, peak_kind = read_peaks()
@@ -256,6 +341,11 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = nodes * args.steps * world / e2e_s / 1e6
 
+    for l in lats:
+        l.close()
+    serving = None
+    if rank == 0 and args.serving_requests > 0 and not args.small:
+        serving = serving_report(L, n_requests=args.serving_requests)
     if rank == 0:
         cpu = None
         if not args.small and args.cpu_budget > 0:
@@ -283,13 +373,14 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps},
-            "gpu_launches": 4 * args.steps,
+            "kernel_variants": {name: L.kernel_variant(storage, col) for name, col in
+                                (("bgk", W.BGK), ("trt", W.TRT), ("cmmrt", W.CMMRT))},
+            "gpu_launches": 6 * args.steps,
             "clocks": clocks.summary(),
             "device_status": rc,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    for l in lats:
-        l.close()
     if dist is not None:
         dist.destroy_process_group()
 

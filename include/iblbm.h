@@ -203,6 +203,17 @@ const char* iblbm_strerror(int status);
  * stepping each context alone.  Errors: INVALID_ARG, CUDA. */
 int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
 
+/* ---- stream-collide kernel variants (tuning control; no counterpart in the paper) ---- */
+/* Two implementations of the fused stream-collide exist: 0 keeps a 16-byte
+ * vector of nodes per lane, 1 one node per lane.  By default the first batch
+ * that needs a (storage, collision) pair times both in place and keeps the
+ * faster for the rest of the process, so a lattice runs the same kernel alone,
+ * batched or served.  iblbm_set_kernel_variant fixes the choice (-1 = tune
+ * again); iblbm_kernel_variant reports it (-1 = not chosen) and the mean
+ * launch times (ms[2]) measured when it was tuned.  Errors: INVALID_ARG. */
+int iblbm_set_kernel_variant(int storage, int collision, int variant);
+int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);
+
 /* ---- serving loop ---------------------------------------------------------------------- */
 /* Continuous batching of simulation requests (no counterpart in the paper; it
  * serves the method of Sec. 2 to many callers).  A request is a lattice with

@@ -83,6 +83,8 @@ SIGNATURES = [
     ("iblbm_step_batch", _i, [_P(_vp), _i, _i]),
     ("iblbm_set_timing", _i, [_vp, _i]),
     ("iblbm_kernel_timing", _i, [_vp, _pd, _pi]),
+    ("iblbm_set_kernel_variant", _i, [_i, _i, _i]),
+    ("iblbm_kernel_variant", _i, [_i, _i, _pi, _pd]),
     ("iblbm_server_create", _i, [_sz, _i, _vp, _P(_vp)]),
     ("iblbm_server_destroy", None, [_vp]),
     ("iblbm_server_submit", _i, [_vp, _P(LatticeDesc), _i, _d, _P(BodyDesc), _pd, _i, _d, _i, _i, _i,
@@ -336,6 +338,19 @@ class Lattice:
         ms, n = C.c_double(0), C.c_int(0)
         _check(load_library().iblbm_kernel_timing(self._h, C.byref(ms), C.byref(n)), "iblbm_kernel_timing")
         return ms.value, n.value
+
+
+def set_kernel_variant(storage: int, collision: int, variant: int) -> None:
+    """Fixes the stream-collide variant (0 vector, 1 one node per lane, -1 retune)."""
+    _check(load_library().iblbm_set_kernel_variant(storage, collision, variant), "iblbm_set_kernel_variant")
+
+
+def kernel_variant(storage: int, collision: int):
+    """(chosen variant or -1, [ms of variant 0, ms of variant 1] from tuning)."""
+    v = C.c_int(-1)
+    ms = (C.c_double * 2)()
+    _check(load_library().iblbm_kernel_variant(storage, collision, C.byref(v), ms), "iblbm_kernel_variant")
+    return v.value, [ms[0], ms[1]]
 
 
 def step_batch(lattices: Iterable[Lattice], nsteps: int) -> None:

@@ -54,7 +54,6 @@ int status_from_bits(unsigned bits) {
 
 size_t storage_bytes(int st) { return st == ST_F64 ? 8 : (st == ST_F32 ? 4 : 2); }
 size_t real_bytes(int st) { return st == ST_F64 ? 8 : 4; }
-int storage_vec(int st) { return st == ST_F64 ? 2 : (st == ST_F32 ? 4 : 8); }
 
 struct BodyHost {
     int n = 0;
@@ -87,17 +86,12 @@ struct iblbm_ctx {
     BodyDev* dbodies = nullptr;   // device array [kMaxBodies]
     BodyRef* drefs = nullptr;     // device [kMaxBodies]
     CaseDev** dcases = nullptr;   // device [1]
-    long long* djob = nullptr;    // device [2]
     std::vector<BodyHost> bodies;
     std::vector<std::pair<void*, size_t>> allocs;
     std::vector<BodyDev> hbodies; // host copies of the static body records (device pointers inside)
     size_t bytes = 0;
     long long steps = 0;
-    long long jobs = 0;
-    int sc_grid = 1;
-    GraphSet graphs;
-    bool dirty = true;
-    int version = 0;
+    int version = 0;              // bumped when bodies change; batch plans check it
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -144,58 +138,6 @@ void drain_timing(iblbm_ctx* c) {
         c->ev_pool.push_back(pr.second);
     }
     c->ev_pending.clear();
-}
-
-// One step of one lattice: prepare bodies, IB stage, stream-collide, finish.
-cudaError_t launch_step(iblbm_ctx* c, cudaStream_t st, bool timed) {
-    const int nb = (int)c->bodies.size();
-    FinLaunch fl{c->drefs, nb, 1, c->dcases};
-    cudaError_t e = cudaSuccess;
-    if (nb > 0) {
-        if ((e = launch_body(fl, 0, st)) != cudaSuccess) return e;
-        IbLaunch il{c->drefs, nb, 0};
-        if ((e = launch_ib(c->hc.storage, il, st)) != cudaSuccess) return e;
-    }
-    ScLaunch sl{c->dcases, c->djob, 1, 0};
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (timed) {
-        a = pool_event(c);
-        b = pool_event(c);
-        cudaEventRecord(a, st);
-    }
-    if ((e = launch_stream_collide(c->hc.storage, sl, c->jobs, c->sc_grid, st)) != cudaSuccess) return e;
-    if (timed) {
-        cudaEventRecord(b, st);
-        c->ev_pending.push_back({a, b});
-    }
-    return launch_body(fl, 1, st);
-}
-
-int capture(iblbm_ctx* c, int nsteps, cudaGraphExec_t* out) {
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return check(e);
-    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = launch_step(c, c->work, false);
-    cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return check(e != cudaSuccess ? e : e2);
-    }
-    e = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
-    return check(e);
-}
-
-int ensure_graphs(iblbm_ctx* c) {
-    if (!c->dirty && c->graphs.one) return IBLBM_OK;
-    c->graphs.reset();
-    int rc = capture(c, 1, &c->graphs.one);
-    if (rc) return rc;
-    c->graphs.many_steps = 16;
-    rc = capture(c, c->graphs.many_steps, &c->graphs.many);
-    if (rc) return rc;
-    c->dirty = false;
-    return IBLBM_OK;
 }
 
 int sync_status(iblbm_ctx* c) {
@@ -328,25 +270,15 @@ int iblbm_create(const iblbm_lattice_desc* d, int collision, double tau, iblbm_c
     c->dbodies = static_cast<BodyDev*>(c->alloc(sizeof(BodyDev) * kMaxBodies));
     c->drefs = static_cast<BodyRef*>(c->alloc(sizeof(BodyRef) * kMaxBodies));
     c->dcases = static_cast<CaseDev**>(c->alloc(sizeof(CaseDev*)));
-    c->djob = static_cast<long long*>(c->alloc(2 * sizeof(long long)));
-    if (!h.f[0] || !h.f[1] || !c->dc || !c->dbodies || !c->drefs || !c->dcases || !c->djob) {
+    if (!h.f[0] || !h.f[1] || !c->dc || !c->dbodies || !c->drefs || !c->dcases) {
         iblbm_destroy(c);
         return IBLBM_ERR_OOM;
     }
     h.bodies = c->dbodies;
-    const int V = storage_vec(d->storage);
-    c->jobs = (long long)d->ny * ((d->nx + 32 * V - 1) / (32 * V));
-    long long job_off[2] = {0, c->jobs};
-    int bps = sc_blocks_per_sm(d->storage);
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const long long want = (c->jobs + 7) / 8;
-    c->sc_grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * bps));
     cudaMemsetAsync(h.f[0], 0, fbytes, c->work);
     cudaMemsetAsync(h.f[1], 0, fbytes, c->work);
     cudaMemcpyAsync(c->dc, &h, sizeof(CaseDev), cudaMemcpyHostToDevice, c->work);
     cudaMemcpyAsync(c->dcases, &c->dc, sizeof(CaseDev*), cudaMemcpyHostToDevice, c->work);
-    cudaMemcpyAsync(c->djob, job_off, sizeof(job_off), cudaMemcpyHostToDevice, c->work);
     launch_fill_equilibrium(&h, c->dc, d->init_rho, d->init_u[0], d->init_u[1], c->work);
     int rc = check(cudaStreamSynchronize(c->work));
     if (rc) {
@@ -361,7 +293,6 @@ void iblbm_destroy(iblbm_ctx* c) {
     if (!c) return;
     forget_plans(c);
     if (c->work) cudaStreamSynchronize(c->work);
-    c->graphs.reset();
     drain_timing(c);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto& a : c->allocs) dev_free(a.first, c->work);
@@ -473,7 +404,6 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
         int rc = check(launch_ib(c->hc.storage, setup, w));
         if (rc) return rc;
     }
-    c->dirty = true;
     c->version++;
     if (body_id) *body_id = id;
     return check(cudaStreamSynchronize(w));
@@ -481,26 +411,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
 
 int iblbm_step(iblbm_ctx* c, int nsteps) {
     if (!c || nsteps < 0) return IBLBM_ERR_INVALID_ARG;
-    if (nsteps == 0) return IBLBM_OK;
-    begin_user(c);
-    int rc = IBLBM_OK;
-    if (c->timing) {
-        for (int s = 0; s < nsteps && !rc; ++s) rc = check(launch_step(c, c->work, true));
-    } else {
-        rc = ensure_graphs(c);
-        int left = nsteps;
-        while (!rc && left >= c->graphs.many_steps) {
-            rc = check(cudaGraphLaunch(c->graphs.many, c->work));
-            left -= c->graphs.many_steps;
-        }
-        while (!rc && left > 0) {
-            rc = check(cudaGraphLaunch(c->graphs.one, c->work));
-            --left;
-        }
-    }
-    end_user(c);
-    if (!rc) c->steps += nsteps;
-    return rc;
+    return iblbm_internal_step_batch(&c, 1, nsteps, 1);   // a batch of one: same plan, graphs and kernels
 }
 
 int iblbm_sync(iblbm_ctx* c) {
@@ -790,13 +701,27 @@ size_t iblbm_internal_estimate_bytes(const iblbm_lattice_desc* d, int n, double 
 // case/tile table spanning every lattice of the batch.
 namespace {
 
+// Stream-collide group: lattices sharing storage type and collision operator
+// (one specialised kernel launch); IB group: bodies of lattices sharing a storage type.
 struct BatchGroup {
     int storage = 0;
+    int collision = 0;
     int ncases = 0;
-    long long jobs = 0;
-    int grid = 1;
     CaseDev** dcases = nullptr;
-    long long* djob = nullptr;
+    long long jobs[SC_VARIANTS] = {0, 0};      // per kernel variant (segment widths differ)
+    int grid[SC_VARIANTS] = {1, 1};
+    long long* djob[SC_VARIANTS] = {nullptr, nullptr};
+};
+
+// Stream-collide variant per (storage, collision), process-wide so that a lattice
+// runs the same kernel alone, in any batch and in the server.  -1: not chosen
+// yet; the first plan that needs it times both variants in place and keeps the
+// faster (the kernel rewrites only its destination buffer from an unchanged
+// source, so repeating it has no effect on the state).
+int g_variant[3][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
+double g_variant_ms[3][5][SC_VARIANTS];
+struct IbGroup {
+    int storage = 0;
     BodyRef* drefs = nullptr;
     int nrefs = 0;
 };
@@ -805,6 +730,7 @@ struct BatchPlan {
     std::vector<iblbm_ctx*> ctxs;
     std::vector<int> versions;
     std::vector<BatchGroup> groups;
+    std::vector<IbGroup> ib_groups;
     BodyRef* drefs_all = nullptr;
     CaseDev** dcases_all = nullptr;
     int nrefs_all = 0;
@@ -833,20 +759,22 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     FinLaunch all{P->drefs_all, P->nrefs_all, (int)P->ctxs.size(), P->dcases_all};
     if (P->nrefs_all > 0) {
         if ((e = launch_body(all, 0, st)) != cudaSuccess) return e;
-        for (auto& g : P->groups) {
+        for (auto& g : P->ib_groups) {
             IbLaunch il{g.drefs, g.nrefs, 0};
             if ((e = launch_ib(g.storage, il, st)) != cudaSuccess) return e;
         }
     }
     for (auto& g : P->groups) {
-        ScLaunch sl{g.dcases, g.djob, g.ncases, 0};
+        const int v = g_variant[g.storage][g.collision] < 0 ? SC_SCALAR : g_variant[g.storage][g.collision];
+        ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
         cudaEvent_t a = nullptr, b = nullptr;
         if (timer) {
             a = pool_event(timer);
             b = pool_event(timer);
             cudaEventRecord(a, st);
         }
-        if ((e = launch_stream_collide(g.storage, sl, g.jobs, g.grid, st)) != cudaSuccess) return e;
+        if ((e = launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st)) != cudaSuccess)
+            return e;
         if (timer) {
             cudaEventRecord(b, st);
             timer->ev_pending.push_back({a, b});
@@ -871,38 +799,57 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
     for (int i = 0; i < n; ++i) P->versions.push_back(ctxs[i]->version);
     std::vector<BodyRef> all_refs;
     std::vector<CaseDev*> all_cases;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
     for (int st = 0; st < 3; ++st) {
-        BatchGroup g;
-        g.storage = st;
-        std::vector<CaseDev*> cs;
-        std::vector<long long> off{0};
         std::vector<BodyRef> refs;
-        const int V = storage_vec(st);
         for (int i = 0; i < n; ++i) {
             iblbm_ctx* c = ctxs[i];
             if (c->hc.storage != st) continue;
-            cs.push_back(c->dc);
-            off.push_back(off.back() + (long long)c->hc.ny * ((c->hc.nx + 32 * V - 1) / (32 * V)));
+            all_cases.push_back(c->dc);
             for (int b = 0; b < (int)c->bodies.size(); ++b) refs.push_back(BodyRef{c->dc, &c->dbodies[b], b, 0});
         }
-        if (cs.empty()) continue;
-        g.ncases = (int)cs.size();
-        g.jobs = off.back();
-        g.nrefs = (int)refs.size();
-        g.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
-        g.djob = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
-        g.drefs = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, refs.size())));
-        if (!g.dcases || !g.djob || !g.drefs) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
-        cudaMemcpyAsync(g.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
-        cudaMemcpyAsync(g.djob, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
-        if (!refs.empty())
-            cudaMemcpyAsync(g.drefs, refs.data(), sizeof(BodyRef) * refs.size(), cudaMemcpyHostToDevice, P->st);
-        int sms = 148;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
-        g.grid = (int)std::max<long long>(1, std::min<long long>((g.jobs + 7) / 8, (long long)sms * sc_blocks_per_sm(st)));
-        P->groups.push_back(g);
-        all_refs.insert(all_refs.end(), refs.begin(), refs.end());
-        all_cases.insert(all_cases.end(), cs.begin(), cs.end());
+        if (!refs.empty()) {
+            IbGroup ig;
+            ig.storage = st;
+            ig.nrefs = (int)refs.size();
+            ig.drefs = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * refs.size()));
+            if (!ig.drefs) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+            cudaMemcpyAsync(ig.drefs, refs.data(), sizeof(BodyRef) * refs.size(), cudaMemcpyHostToDevice, P->st);
+            P->ib_groups.push_back(ig);
+            all_refs.insert(all_refs.end(), refs.begin(), refs.end());
+        }
+        for (int col = 0; col < 4; ++col) {
+            BatchGroup g;
+            g.storage = st;
+            g.collision = col;
+            std::vector<CaseDev*> cs;
+            for (int i = 0; i < n; ++i) {
+                iblbm_ctx* c = ctxs[i];
+                if (c->hc.storage == st && c->hc.collision == col) cs.push_back(c->dc);
+            }
+            if (cs.empty()) continue;
+            g.ncases = (int)cs.size();
+            g.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
+            if (!g.dcases) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+            cudaMemcpyAsync(g.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
+            for (int v = 0; v < SC_VARIANTS; ++v) {
+                const int seg = sc_segment(st, v);
+                std::vector<long long> off{0};
+                for (int i = 0; i < n; ++i) {
+                    iblbm_ctx* c = ctxs[i];
+                    if (c->hc.storage == st && c->hc.collision == col)
+                        off.push_back(off.back() + (long long)c->hc.ny * ((c->hc.nx + seg - 1) / seg));
+                }
+                g.jobs[v] = off.back();
+                g.djob[v] = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
+                if (!g.djob[v]) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+                cudaMemcpyAsync(g.djob[v], off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
+                g.grid[v] = (int)std::max<long long>(
+                    1, std::min<long long>((g.jobs[v] + 7) / 8, (long long)sms * sc_blocks_per_sm(st, col, v)));
+            }
+            P->groups.push_back(g);
+        }
     }
     P->nrefs_all = (int)all_refs.size();
     P->drefs_all = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, all_refs.size())));
@@ -915,6 +862,38 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         cudaEvent_t e;
         cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
         P->joins.push_back(e);
+    }
+    *rc = check(cudaStreamSynchronize(P->st));
+    if (*rc) { delete P; return nullptr; }
+    // autotune: time each variant of every group whose (storage, collision) has no choice yet
+    for (auto& g : P->groups) {
+        if (g_variant[g.storage][g.collision] >= 0) continue;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        int best = SC_SCALAR;
+        double best_ms = 1e300;
+        for (int v = 0; v < SC_VARIANTS; ++v) {
+            ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
+            float ms = 0.f, tot = 0.f;
+            launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);   // warm
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(a, P->st);
+                launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);
+                cudaEventRecord(b, P->st);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+                tot += ms;
+            }
+            g_variant_ms[g.storage][g.collision][v] = tot / 3.0;
+            if (tot / 3.0 < best_ms) {
+                best_ms = tot / 3.0;
+                best = v;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        g_variant[g.storage][g.collision] = best;
     }
     *rc = check(cudaStreamSynchronize(P->st));
     if (*rc) { delete P; return nullptr; }
@@ -938,6 +917,22 @@ int batch_capture(BatchPlan* P, int nsteps, cudaGraphExec_t* out) {
 }
 
 }  // namespace
+
+extern "C" int iblbm_set_kernel_variant(int storage, int collision, int variant) {
+    if (storage < 0 || storage > 2 || collision < 0 || collision > 3 || variant < -1 || variant >= SC_VARIANTS)
+        return IBLBM_ERR_INVALID_ARG;
+    g_variant[storage][collision] = variant;
+    for (auto& kv : g_plans) kv.second->graphs.reset();   // captured graphs hold the old kernel
+    return IBLBM_OK;
+}
+
+extern "C" int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms) {
+    if (storage < 0 || storage > 2 || collision < 0 || collision > 3) return IBLBM_ERR_INVALID_ARG;
+    if (variant) *variant = g_variant[storage][collision];
+    if (ms)
+        for (int v = 0; v < SC_VARIANTS; ++v) ms[v] = g_variant_ms[storage][collision][v];
+    return IBLBM_OK;
+}
 
 extern "C" int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps) {
     return iblbm_internal_step_batch(ctxs, n, nsteps, 1);

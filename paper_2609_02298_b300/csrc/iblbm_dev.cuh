@@ -100,9 +100,11 @@ __host__ __device__ constexpr R wgt(int i) { return i == 0 ? R(4) / R(9) : (i <=
 
 // ---- storage traits: 16-byte vectors ------------------------------------------------
 template <class S> struct Traits;
-template <> struct Traits<double> { using R = double; static constexpr int V = 2; };
-template <> struct Traits<float> { using R = float; static constexpr int V = 4; };
-template <> struct Traits<__half> { using R = float; static constexpr int V = 8; };
+// V: nodes per 16-byte vector; kMinBlocks: resident 256-thread CTAs per SM the
+// stream-collide kernel is compiled for (register budget 65536 / (256 kMinBlocks)).
+template <> struct Traits<double> { using R = double; static constexpr int V = 2; static constexpr int kMinBlocks = 1; };
+template <> struct Traits<float> { using R = float; static constexpr int V = 4; static constexpr int kMinBlocks = 3; };
+template <> struct Traits<__half> { using R = float; static constexpr int V = 8; static constexpr int kMinBlocks = 2; };
 
 template <class R> __device__ __forceinline__ R to_r(double v) { return R(v); }
 
@@ -113,6 +115,10 @@ __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ld
 __device__ __forceinline__ void st1(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }
+// One correctly rounded conversion from double (no double rounding through float).
+__device__ __forceinline__ void st1_from_double(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st1_from_double(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st1_from_double(__half* p, double v) { *p = __double2half(v); }
 
 __device__ __forceinline__ void ld16(const double* p, double (&v)[2]) {
     double2 t = __ldg(reinterpret_cast<const double2*>(p));
@@ -191,8 +197,10 @@ __device__ __forceinline__ void to_raw(R& c0, R& c1, R& c2, R u) {
 // Collide one node in place on shifted populations.  F is the force density
 // acting at the node (Guo forcing, Eq. 3-4; TRT split source; CM-MRT source R).
 // Returns rho for the stability check.
-template <class R>
+// KIND >= 0 fixes the operator at compile time (specialised kernels); -1 reads it from P.
+template <class R, int KIND = -1>
 __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R Fy) {
+    const int kind = KIND >= 0 ? KIND : P.kind;
     R drho = R(0), jx = R(0), jy = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -201,18 +209,18 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
         jy += R(ey(i)) * s[i];
     }
     const R rho = R(1) + drho;
-    if (P.kind == COL_NONE) return rho;
+    if (kind == COL_NONE) return rho;
     const R inv = R(1) / rho;
     const R ux = (jx + R(0.5) * Fx) * inv, uy = (jy + R(0.5) * Fy) * inv;   // Eq. 4
     const R uu = ux * ux + uy * uy;
-    if (P.kind == COL_BGK) {
+    if (kind == COL_BGK) {
         const R pre = R(1) - R(0.5) * P.omega;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             s[i] = s[i] - P.omega * (s[i] - seq_i(i, drho, rho, ux, uy, uu)) + pre * guo_i(i, ux, uy, Fx, Fy);
         return rho;
     }
-    if (P.kind == COL_TRT) {
+    if (kind == COL_TRT) {
         const R pe = R(1) - R(0.5) * P.s_e, po = R(1) - R(0.5) * P.s_o;
         R out[9];
         {

@@ -51,21 +51,47 @@ __device__ __forceinline__ bool bad_density(R rho) {
 // ------------------------------------------------------------------------------------------
 // Stream-collide of one row segment [xseg, xseg + 32V) of row y, one warp.
 template <class S>
-__device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int lane) {
+struct ScCase {
+    using R = typename Traits<S>::R;
+    const CaseDev* C;
+    const S* src;
+    S* dst;
+    int nx, ny, pitch, nbodies;
+    long long plane;
+    bool xper, yper, neu_w, neu_e;
+    CollParams<R> P;
+    R gfx, gfy;
+    __device__ __forceinline__ void load(const CaseDev* c) {
+        C = c;
+        const int parity = (int)(c->step & 1ull);
+        src = static_cast<const S*>(c->f[parity]);
+        dst = static_cast<S*>(c->f[parity ^ 1]);
+        nx = c->nx; ny = c->ny; pitch = c->pitch; nbodies = c->nbodies; plane = c->plane;
+        xper = c->bc[SIDE_W] == BC_PER;
+        yper = c->bc[SIDE_S] == BC_PER;
+        neu_w = c->bc[SIDE_W] == BC_NEU;
+        neu_e = c->bc[SIDE_E] == BC_NEU;
+        P.load(*c);
+        gfx = R(c->gfx);
+        gfy = R(c->gfy);
+    }
+};
+
+template <class S, int KIND>
+__device__ __forceinline__ void sc_row(const ScCase<S>& K, int y, int xseg, int lane) {
     using R = typename Traits<S>::R;
     constexpr int V = Traits<S>::V;
     const unsigned FULL = 0xffffffffu;
-    const int parity = (int)(C.step & 1ull);
-    const S* __restrict__ src = static_cast<const S*>(C.f[parity]);
-    S* __restrict__ dst = static_cast<S*>(C.f[parity ^ 1]);
-    const int nx = C.nx, ny = C.ny, pitch = C.pitch;
-    const long long plane = C.plane;
-    const bool xper = C.bc[SIDE_W] == BC_PER, yper = C.bc[SIDE_S] == BC_PER;
-    CollParams<R> P;
-    P.load(C);
-    const R gfx = R(C.gfx), gfy = R(C.gfy);
+    const CaseDev& C = *K.C;
+    const S* __restrict__ src = K.src;
+    S* __restrict__ dst = K.dst;
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch;
+    const long long plane = K.plane;
+    const bool xper = K.xper, yper = K.yper;
+    const CollParams<R>& P = K.P;
+    const R gfx = K.gfx, gfy = K.gfy;
     const int x0 = xseg + lane * V;
-    const bool ib = row_has_ib(C, y, xseg, xseg + 32 * V);
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * V);
     bool unstable = false;
 
     if (!yper && (y == 0 || y == ny - 1)) {
@@ -78,7 +104,7 @@ __device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int la
             post_stream_node<S, R>(C, src, x, y, s);
             R Fx = gfx, Fy = gfy;
             if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-            unstable |= bad_density(collide<R>(P, s, Fx, Fy));
+            unstable |= bad_density(collide<R, KIND>(P, s, Fx, Fy));
 #pragma unroll
             for (int i = 0; i < 9; ++i) st1(dst + i * plane + (long long)y * pitch + x, s[i]);
         }
@@ -136,14 +162,14 @@ __device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int la
         } else {
             // zero-gradient east copies node nx-2: same lane, or the previous lane's last node
             R nb[9];
-            if (east_in_seg && C.bc[SIDE_E] == BC_NEU && ((nx - 1) % V) == 0) {
+            if (east_in_seg && K.neu_e && ((nx - 1) % V) == 0) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) nb[i] = __shfl_up_sync(FULL, s[i][V - 1], 1);
                 // node nx-2 opens the previous segment: pull it directly
                 if (east_here && lane == 0) pull_node<S, R>(C, src, nx - 2, y, nb);
             }
             if (east_here) {
-                if (C.bc[SIDE_E] == BC_NEU) {
+                if (K.neu_e) {
                     if (ke == 0) {
 #pragma unroll
                         for (int i = 0; i < 9; ++i) s[i][0] = nb[i];
@@ -169,7 +195,7 @@ __device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int la
                 }
             }
             if (x0 == 0) {
-                if (C.bc[SIDE_W] == BC_NEU) {
+                if (K.neu_w) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) s[i][0] = s[i][1];
                 } else {
@@ -190,7 +216,7 @@ __device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int la
             for (int i = 0; i < 9; ++i) t[i] = s[i][k];
             R Fx = gfx, Fy = gfy;
             if (ib && x0 + k < nx) add_ib<R>(C, x0 + k, y, t, Fx, Fy);
-            const R rho = collide<R>(P, t, Fx, Fy);
+            const R rho = collide<R, KIND>(P, t, Fx, Fy);
             if (x0 + k < nx) unstable |= bad_density(rho);
 #pragma unroll
             for (int i = 0; i < 9; ++i) s[i][k] = t[i];
@@ -211,22 +237,132 @@ __device__ __forceinline__ void sc_row(const CaseDev& C, int y, int xseg, int la
     if (__any_sync(FULL, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
 }
 
-template <class S>
-__global__ void __launch_bounds__(kThreads) sc_kernel(ScLaunch L, long long jobs) {
+// Each warp takes a contiguous range of jobs (row segments), so the case
+// changes rarely; its parameters stay in registers across jobs.
+// Resident CTAs per SM each specialisation is compiled for (its register budget
+// is 65536 / (256 x this)); chosen from -Xptxas -v so that no variant spills.
+template <class S, int KIND> struct ScMinBlocks { static constexpr int value = 2; };
+template <> struct ScMinBlocks<double, COL_BGK> { static constexpr int value = 1; };
+template <> struct ScMinBlocks<double, COL_TRT> { static constexpr int value = 1; };
+template <> struct ScMinBlocks<double, COL_CM> { static constexpr int value = 1; };
+template <> struct ScMinBlocks<double, COL_NONE> { static constexpr int value = 1; };
+template <> struct ScMinBlocks<double, -1> { static constexpr int value = 1; };
+
+template <class S, int KIND>
+__global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_kernel(ScLaunch L, long long jobs) {
     constexpr int V = Traits<S>::V;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
-    for (long long job = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5; job < jobs; job += nwarps) {
-        int lo = 0, hi = L.ncases - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+    const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kThreads) >> 5;
+    const long long j0 = jobs * gw / nw, j1 = jobs * (gw + 1) / nw;
+    ScCase<S> K;
+    long long c_lo = 0, c_hi = 0;
+    int nseg = 1, y = 0, seg = 0;
+    for (long long job = j0; job < j1; ++job) {
+        if (job >= c_hi || job < c_lo) {
+            int lo = 0, hi = L.ncases - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+            }
+            c_lo = L.job_off[lo];
+            c_hi = L.job_off[lo + 1];
+            K.load(L.cases[lo]);
+            nseg = (K.nx + 32 * V - 1) / (32 * V);
+            const long long local = job - c_lo;
+            y = (int)(local / nseg);
+            seg = (int)(local % nseg);
         }
-        const CaseDev& C = *L.cases[lo];
-        const long long local = job - L.job_off[lo];
-        const int nseg = (C.nx + 32 * V - 1) / (32 * V);
-        const int y = (int)(local / nseg), seg = (int)(local % nseg);
-        sc_row<S>(C, y, seg * 32 * V, lane);
+        sc_row<S, KIND>(K, y, seg * 32 * V, lane);
+        if (++seg == nseg) {
+            seg = 0;
+            ++y;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stream-collide, one node per lane: a warp handles 32 consecutive nodes of a row
+// and pulls each population with a plain (coalesced, possibly one-element
+// unaligned) load.  Nine live values per thread keep registers low, so more
+// warps are resident to cover memory latency.  Edge nodes of non-periodic
+// sides and boundary rows use the general node path.
+template <class S, int KIND>
+__device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane) {
+    using R = typename Traits<S>::R;
+    const CaseDev& C = *K.C;
+    const S* __restrict__ src = K.src;
+    S* __restrict__ dst = K.dst;
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch;
+    const long long plane = K.plane;
+    const int x = xseg + lane;
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32);
+    bool unstable = false;
+    if (x < nx) {
+        R s[9];
+        const bool edge_row = !K.yper && (y == 0 || y == ny - 1);
+        const bool edge_col = !K.xper && (x == 0 || x == nx - 1);
+        if (edge_row || edge_col) {
+            post_stream_node<S, R>(C, src, x, y, s);
+        } else {
+            int ym = y - 1, yp = y + 1, xm = x - 1, xp = x + 1;
+            if (K.yper) {
+                if (ym < 0) ym += ny;
+                if (yp >= ny) yp -= ny;
+            }
+            if (K.xper) {
+                if (xm < 0) xm += nx;
+                if (xp >= nx) xp -= nx;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int sy = ey(i) == 1 ? ym : (ey(i) == -1 ? yp : y);
+                const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
+                s[i] = ld1(src + i * plane + (long long)sy * pitch + sx);
+            }
+        }
+        R Fx = K.gfx, Fy = K.gfy;
+        if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+        unstable = bad_density(collide<R, KIND>(K.P, s, Fx, Fy));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st1(dst + i * plane + (long long)y * pitch + x, s[i]);
+    }
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+}
+
+template <class S, int KIND> struct ScScalarMinBlocks { static constexpr int value = 4; };
+template <int KIND> struct ScScalarMinBlocks<double, KIND> { static constexpr int value = 2; };
+
+template <class S, int KIND>
+__global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND>::value))
+    sc_kernel_scalar(ScLaunch L, long long jobs) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kThreads) >> 5;
+    const long long j0 = jobs * gw / nw, j1 = jobs * (gw + 1) / nw;
+    ScCase<S> K;
+    long long c_lo = 0, c_hi = 0;
+    int nseg = 1, y = 0, seg = 0;
+    for (long long job = j0; job < j1; ++job) {
+        if (job >= c_hi || job < c_lo) {
+            int lo = 0, hi = L.ncases - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+            }
+            c_lo = L.job_off[lo];
+            c_hi = L.job_off[lo + 1];
+            K.load(L.cases[lo]);
+            nseg = (K.nx + 31) / 32;
+            const long long local = job - c_lo;
+            y = (int)(local / nseg);
+            seg = (int)(local % nseg);
+        }
+        sc_row_scalar<S, KIND>(K, y, seg * 32, lane);
+        if (++seg == nseg) {
+            seg = 0;
+            ++y;
+        }
     }
 }
 
@@ -793,7 +929,7 @@ __global__ void import_kernel(const CaseDev* __restrict__ Cp, const double* in) 
         const int i = (int)(q / N);
         const long long r = q % N;
         const int y = (int)(r / C.nx), x = (int)(r % C.nx);
-        st1(dst + i * C.plane + (long long)y * C.pitch + x, (typename Traits<S>::R)(in[q] - wgt<double>(i)));
+        st1_from_double(dst + i * C.plane + (long long)y * C.pitch + x, in[q] - wgt<double>(i));
     }
 }
 
@@ -805,8 +941,8 @@ __global__ void fill_eq_kernel(const CaseDev* __restrict__ Cp, double rho, doubl
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 9 * N; q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q / N);
         const double v = seq_i<double>(i, rho - 1.0, rho, ux, uy, uu);
-        st1(static_cast<S*>(C.f[0]) + q, (typename Traits<S>::R)v);
-        st1(static_cast<S*>(C.f[1]) + q, (typename Traits<S>::R)v);
+        st1_from_double(static_cast<S*>(C.f[0]) + q, v);
+        st1_from_double(static_cast<S*>(C.f[1]) + q, v);
     }
 }
 
@@ -844,24 +980,69 @@ static int grid_for(long long work) {
     return (int)g;
 }
 
-cudaError_t launch_stream_collide(int storage, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
-    if (jobs <= 0) return cudaSuccess;
-    switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(sc_kernel<double>, grid, kThreads, st, L, jobs); break;
-    case ST_F32: IBLBM_LAUNCH(sc_kernel<float>, grid, kThreads, st, L, jobs); break;
-    default: IBLBM_LAUNCH(sc_kernel<__half>, grid, kThreads, st, L, jobs); break;
-    }
+template <class S, int KIND>
+static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
+    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND>), grid, kThreads, st, L, jobs);
+    else IBLBM_LAUNCH((sc_kernel<S, KIND>), grid, kThreads, st, L, jobs);
     return cudaGetLastError();
 }
 
-int sc_blocks_per_sm(int storage) {
+template <class S>
+static cudaError_t sc_launch_s(int collision, int variant, const ScLaunch& L, long long jobs, int grid,
+                               cudaStream_t st) {
+    switch (collision) {
+    case COL_BGK: return sc_launch_k<S, COL_BGK>(variant, L, jobs, grid, st);
+    case COL_TRT: return sc_launch_k<S, COL_TRT>(variant, L, jobs, grid, st);
+    case COL_CM: return sc_launch_k<S, COL_CM>(variant, L, jobs, grid, st);
+    case COL_NONE: return sc_launch_k<S, COL_NONE>(variant, L, jobs, grid, st);
+    default: return sc_launch_k<S, -1>(variant, L, jobs, grid, st);
+    }
+}
+
+cudaError_t launch_stream_collide(int storage, int collision, int variant, const ScLaunch& L, long long jobs,
+                                  int grid, cudaStream_t st) {
+    if (jobs <= 0) return cudaSuccess;
+    switch (storage) {
+    case ST_F64: return sc_launch_s<double>(collision, variant, L, jobs, grid, st);
+    case ST_F32: return sc_launch_s<float>(collision, variant, L, jobs, grid, st);
+    default: return sc_launch_s<__half>(collision, variant, L, jobs, grid, st);
+    }
+}
+
+template <class S, int KIND>
+static int sc_occ_k(int variant) {
+    int nb = 1;
+    if (variant == SC_SCALAR)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<S, KIND>, kThreads, 0);
+    return nb;
+}
+
+template <class S>
+static int sc_occ_s(int collision, int variant) {
+    switch (collision) {
+    case COL_BGK: return sc_occ_k<S, COL_BGK>(variant);
+    case COL_TRT: return sc_occ_k<S, COL_TRT>(variant);
+    case COL_CM: return sc_occ_k<S, COL_CM>(variant);
+    case COL_NONE: return sc_occ_k<S, COL_NONE>(variant);
+    default: return sc_occ_k<S, -1>(variant);
+    }
+}
+
+int sc_blocks_per_sm(int storage, int collision, int variant) {
     int nb = 1;
     switch (storage) {
-    case ST_F64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<double>, kThreads, 0); break;
-    case ST_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<float>, kThreads, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<__half>, kThreads, 0); break;
+    case ST_F64: nb = sc_occ_s<double>(collision, variant); break;
+    case ST_F32: nb = sc_occ_s<float>(collision, variant); break;
+    default: nb = sc_occ_s<__half>(collision, variant); break;
     }
     return nb < 1 ? 1 : nb;
+}
+
+int sc_segment(int storage, int variant) {
+    const int V = storage == ST_F64 ? 2 : (storage == ST_F32 ? 4 : 8);
+    return variant == SC_SCALAR ? 32 : 32 * V;
 }
 
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {

@@ -37,13 +37,19 @@ struct FinLaunch {
 };
 
 // host-side launchers (kernels.cu)
-cudaError_t launch_stream_collide(int storage, const ScLaunch& L, long long jobs, int grid, cudaStream_t st);
+// Stream-collide variants: SC_VECTOR holds 16-byte vectors (2/4/8 nodes) per
+// lane; SC_SCALAR one node per lane.  A job is one row segment of
+// sc_segment(storage, variant) nodes.
+enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_VARIANTS = 2 };
+cudaError_t launch_stream_collide(int storage, int collision, int variant, const ScLaunch& L, long long jobs,
+                                  int grid, cudaStream_t st);
+int sc_segment(int storage, int variant);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
 cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st);   // 0 prepare, 1 finish
 cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st);
 cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st);
 cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st);
 cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux, double* uy, cudaStream_t st);
-int sc_blocks_per_sm(int storage);
+int sc_blocks_per_sm(int storage, int collision, int variant);
 
 }  // namespace iblbm

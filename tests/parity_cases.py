@@ -103,7 +103,8 @@ def check_domain_conditions_f64(name, nx, ny, storage=W.F64, rounds=3, steps=7):
     c.set_populations(f0)
     for _ in range(rounds):
         stepped(g, c, steps)
-        assert rel_l2(dev(g.populations()), dev(c.populations())) < F64_TOL
+        # the random perturbation decays towards rest, so the bar is floored (assert_f64_state)
+        assert_f64_state(g.populations(), c.populations(), u_ref=0.02)
 
 
 # ---------------------------------------------------------------- immersed boundary
@@ -193,9 +194,15 @@ def check_prescribed_oscillation_f64(nx=128, ny=96, D=16.0, steps=120):
 
 
 def check_free_body_f64(scheme, internal_mass, nx=64, ny=160, D=12.0, steps=150):
+    """Settling disk, FP64.  MDF is checked over its first 15 steps only: with the
+    explicit Velocity-Verlet coupling of Eq. 23 the converged MDF force makes a
+    rho_s/rho_f = 1.5 disk diverge after some 20-40 steps, in the oracle exactly
+    as on the device (DF and DFC stay stable)."""
     spec = W.sedimentation(two_particles=False, storage=W.F64, internal_mass=internal_mass,
-                           kernel=W.PESKIN4, scheme=scheme, nx=nx, ny=ny, diameter=D, tau=0.7, g=4e-4)
+                           kernel=W.PESKIN4, scheme=scheme, nx=nx, ny=ny, diameter=D, tau=0.7, g=1e-4)
     spec.bodies[0].mdf_nmin, spec.bodies[0].mdf_nmax = 3, 10
+    if scheme == W.MDF:
+        steps = min(steps, 15)
     g, c = gpu_case(spec), oracle_case(spec)
     stepped(g, c, steps)
     sg, sc = g.body_state(0), c.body_state(0)
@@ -205,10 +212,12 @@ def check_free_body_f64(scheme, internal_mass, nx=64, ny=160, D=12.0, steps=150)
     np.testing.assert_array_equal(g.marker_stencils(0), c.marker_stencils(0))
 
 
-def check_two_particle_dfc_f64(nx=64, ny=200, D=10.0, steps=80):
+def check_two_particle_dfc_f64(nx=100, ny=260, D=20.0, steps=100):
+    """Two settling disks (rho_s/rho_f 1.5 below 1.01, 1.5 D apart), DFC with a
+    shared W_total, g and tau of the 400x1600 sedimentation workload."""
     spec = W.sedimentation(two_particles=True, storage=W.F64, kernel=W.PESKIN4, scheme=W.DFC, nx=nx,
-                           ny=ny, diameter=D, tau=0.7, g=4e-4)
-    y0 = 0.6 * ny
+                           ny=ny, diameter=D, tau=0.65, g=8.33e-5)
+    y0 = 0.5 * ny
     for b, yc in zip(spec.bodies, (y0, y0 + 1.5 * D)):
         b.xy, b.ds = W.circle_markers(b.xc, yc, D, 31)
         b.yc = yc
@@ -291,3 +300,69 @@ def check_marker_out_of_domain(L, steps=200):
         assert e.code == -4
     else:
         raise AssertionError("a marker left the lattice but no error was reported")
+
+
+# ---------------------------------------------------------------- serving loop
+def serving_specs(scale=1.0, n=6, steps=(24, 16, 40, 8, 30, 12)):
+    """Mixed requests: sizes, schemes, kernels, collisions and storages differ."""
+    s = lambda v: max(12, int(v * scale))  # noqa: E731
+    combos = [(W.DF, W.HAT, W.BGK, W.F32), (W.MDF, W.PESKIN4, W.TRT, W.F32), (W.DFC, W.PESKIN4, W.CMMRT, W.F32),
+              (W.DF, W.PESKIN4, W.CMMRT, W.F16S), (W.DFC, W.HAT, W.BGK, W.F64), (W.MDF, W.HAT, W.BGK, W.F32)]
+    sizes = [(128, 64), (96, 48), (160, 64), (128, 48), (64, 40), (112, 56)]
+    out = []
+    for i in range(n):
+        scheme, kernel, col, st = combos[i % len(combos)]
+        nx, ny = sizes[i % len(sizes)]
+        nx, ny = s(nx), s(ny)
+        D = max(4.0, ny / 6.0)
+        body = cylinder_body(0.3 * nx + 0.37, 0.5 * ny + 0.21, D, max(12, int(round(math.pi * D))), kernel, scheme,
+                             mdf_nmin=5, mdf_nmax=5)
+        sp = channel_spec(nx, ny, collision=col, tau=0.62 + 0.02 * i, storage=st, u=0.06, bodies=[body])
+        out.append((sp, steps[i % len(steps)]))
+    return out
+
+
+def check_server_alone_vs_mix(L, cases, budget_lattices=2.5, max_steps=8):
+    """Requests admitted under an HBM budget that holds about budget_lattices of
+    them run in a continuous batch; each result equals the same case run alone
+    (bitwise), and the budget is never exceeded."""
+    alone = []
+    for sp, n in cases:
+        g = gpu_case(sp)
+        g.step(n)
+        assert g.sync() >= 0
+        alone.append(g.force_history(0))
+        g.close()
+    sizes = []
+    for sp, _ in cases:
+        g = gpu_case(sp)
+        sizes.append(g.device_bytes)
+        g.close()
+    budget = int(budget_lattices * max(sizes))
+    srv = L.Server(budget, max_slots=8)
+    ids = [srv.submit(sp, n) for sp, n in cases]
+    done, peak_resident, ticks = 0, 0, 0
+    while done < len(ids):
+        k, res, que = srv.tick(max_steps)
+        used, _, _ = srv.stats()
+        assert used <= budget
+        peak_resident = max(peak_resident, res)
+        done += k
+        ticks += 1
+        assert ticks < 10000
+    assert peak_resident >= 2                       # cases overlapped on the device
+    for rid, ref in zip(ids, alone):
+        hist, lat = srv.poll(rid)
+        assert lat > 0
+        np.testing.assert_array_equal(hist, ref)
+    # a request that can never fit the budget is rejected, not queued forever
+    big = channel_spec(1024, 1024, storage=W.F64)
+    rid = srv.submit(big, 4)
+    srv.tick(4)
+    try:
+        srv.poll(rid)
+    except L.IblbmError as e:
+        assert e.code == -7
+    else:
+        raise AssertionError("oversized request was not rejected")
+    srv.close()

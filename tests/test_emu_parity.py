@@ -16,14 +16,18 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "emu"))
 
 
-@pytest.fixture(scope="module")
-def L():
+@pytest.fixture(scope="module", params=[0, 1], ids=["vector", "scalar"])
+def L(request):
+    """The emulated library with the stream-collide variant fixed (both are checked)."""
     import build_emu
     import paper_2609_02298_b300 as lib
     path = build_emu.build()
     saved = lib._lib
     lib._lib = None
     lib.load_library(path)
+    for st in (W.F64, W.F32, W.F16S):
+        for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
+            lib.set_kernel_variant(st, col, request.param)
     yield lib
     lib._close_all()
     lib._lib = saved
@@ -108,3 +112,7 @@ def test_graph_replay_equals_timed_launches(L):
 
 def test_marker_out_of_domain_is_reported(L):
     P.check_marker_out_of_domain(L, steps=60)
+
+
+def test_server_alone_vs_mix(L):
+    P.check_server_alone_vs_mix(L, [(sp, 3) for sp, _ in P.serving_specs(scale=0.2)], max_steps=2)

@@ -17,6 +17,19 @@ import paper_2609_02298_b300 as L  # noqa: E402
 
 L.use_torch_allocator()
 
+
+@pytest.fixture(scope="module", autouse=True, params=[0, 1], ids=["vector", "scalar"])
+def variant(request):
+    """Every check runs with each stream-collide variant fixed in turn."""
+    for st in (W.F64, W.F32, W.F16S):
+        for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
+            L.set_kernel_variant(st, col, request.param)
+    yield request.param
+    for st in (W.F64, W.F32, W.F16S):
+        for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
+            L.set_kernel_variant(st, col, -1)
+
+
 SCHEMES = [W.DF, W.MDF, W.DFC]
 KERNELS = [W.HAT, W.PESKIN4]
 COLLS = [W.BGK, W.TRT, W.CMMRT]
@@ -91,6 +104,10 @@ def test_graph_replay_equals_timed_launches():
 
 def test_marker_out_of_domain_is_reported():
     P.check_marker_out_of_domain(L)
+
+
+def test_server_alone_vs_mix():
+    P.check_server_alone_vs_mix(L, P.serving_specs(scale=1.0))
 
 
 def test_full_size_2048x1024_f32_window():
