@@ -180,10 +180,15 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
             k, _, _ = srv.tick(tick)
             done += k
         wall = time.perf_counter() - t0
-        lats = [srv.poll(i, cap=4)[1] for i in ids]
+        lats, failed = [], 0
+        for i in ids:
+            try:
+                lats.append(srv.poll(i, cap=4)[1])
+            except L.IblbmError:       # a request whose case went unstable or did not fit
+                failed += 1
         srv.close()
         return {"cases_per_s": len(specs) / wall, "p50_s": _pct(lats, 50), "p99_s": _pct(lats, 99),
-                "wall_s": wall}
+                "wall_s": wall, "failed": failed}
 
     cap = run_server([0.0] * len(specs))
     rate_cap = cap["cases_per_s"]
@@ -197,19 +202,22 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
     # one case at a time, same arrivals as the 0.5x run
     arr = list(np.cumsum(gaps) / (0.5 * rate_cap))
     t0 = time.perf_counter()
-    lats = []
+    lats, failed = [], 0
     for a, sp in zip(arr, specs):
         now = time.perf_counter() - t0
         if a > now:
             time.sleep(a - now)
         lat = L.Lattice.from_spec(sp)
         lat.step(steps)
-        lat.force_history(0, cap=4)
+        try:
+            lat.force_history(0, cap=4)
+            lats.append(time.perf_counter() - t0 - a)
+        except L.IblbmError:
+            failed += 1
         lat.close()
-        lats.append(time.perf_counter() - t0 - a)
     wall = time.perf_counter() - t0
     out["sequential_0.5x"] = {"cases_per_s": len(specs) / wall, "p50_s": _pct(lats, 50), "p99_s": _pct(lats, 99),
-                              "wall_s": wall}
+                              "wall_s": wall, "failed": failed}
     return out
 
 
@@ -345,7 +353,10 @@ def main():
         l.close()
     serving = None
     if rank == 0 and args.serving_requests > 0 and not args.small:
-        serving = serving_report(L, n_requests=args.serving_requests)
+        try:
+            serving = serving_report(L, n_requests=args.serving_requests)
+        except Exception as exc:      # the headline line is printed whatever happens here
+            serving = {"error": repr(exc)}
     if rank == 0:
         cpu = None
         if not args.small and args.cpu_budget > 0:
