@@ -21,7 +21,10 @@ def build(force=False):
     if not force and os.path.exists(LIB) and all(os.path.getmtime(d) <= os.path.getmtime(LIB) for d in deps):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-g", "-fPIC", "-shared", "-DIBLBM_EMULATE", "-Wno-attributes",
+    # -Bsymbolic: the library's CUDA runtime calls bind to the emulation in this
+    # library even when the real libcudart is already loaded in the process.
+    cmd = ["g++", "-std=c++17", "-O2", "-g", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-DIBLBM_EMULATE",
+           "-Wno-attributes",
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", HERE, "-I", "/usr/local/cuda/include",
            "-x", "c++"] + SOURCES[:-1] + ["-x", "none", SOURCES[-1], "-o", tmp, "-lpthread"]
     subprocess.check_call(cmd)
