@@ -247,6 +247,31 @@ int iblbm_server_poll(iblbm_server* srv, long long req_id, double* forces_out, i
 /* Device bytes held by resident cases and the resident / queued counts. */
 int iblbm_server_stats(const iblbm_server* srv, size_t* used_bytes, int* resident, int* queued);
 
+/* ---- allocation-free lambda_k ------------------------------------------------------------ */
+/* No counterpart in the paper.  For callers that cannot allocate device memory
+ * where they need the DFC factors lambda_k of Eq. 17 (during CUDA stream
+ * capture, inside frameworks that own every device allocation, in real-time
+ * loops), this call computes lambda_k for one marker set without allocating:
+ * no cudaMalloc, cudaFree or allocating library routine.  Its scratch (W_total
+ * on the markers' bounding box) is a library-wide device array of 2^18 FP64
+ * values, so the box -- (max - min stencil origin + S) in x times the same in y,
+ * S = 2 (hat) or 4 (Peskin) -- may hold at most 262144 nodes (512 x 512).
+ *   xy      device pointer, 2*n doubles (x0, y0, x1, y1, ...), lattice units
+ *   n, ds   marker count and arc length (Eq. 17 uses ds; rho_f = 1)
+ *   kernel  IBLBM_HAT or IBLBM_PESKIN4
+ *   nx, ny  lattice size; every footprint must lie inside it
+ *   lambda  device pointer, n doubles, written with lambda_k
+ *   stream  cudaStream_t the work is ordered on (NULL = legacy default); the
+ *           call syncs that stream to report errors.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.
+ * The array is shared by all calls and keeps the last call's contents; calls
+ * that overlap on the GPU race and must be serialised by the caller.
+ * Errors: INVALID_ARG, CAPACITY (box above 262144 nodes),
+ * MARKER_OUT_OF_DOMAIN, CUDA. */
+int iblbm_dfc_lambda_noalloc(const double* xy, int n, double ds, int kernel, int nx, int ny, double* lambda,
+                             void* stream);
+
 /* ---- timing of the stream-collide kernel ------------------------------------------ */
 /* While enabled, steps launch their kernels one by one (no graph) and bracket
  * each stream-collide launch with CUDA events on the launching stream.

@@ -83,6 +83,7 @@ SIGNATURES = [
     ("iblbm_step_batch", _i, [_P(_vp), _i, _i]),
     ("iblbm_set_timing", _i, [_vp, _i]),
     ("iblbm_kernel_timing", _i, [_vp, _pd, _pi]),
+    ("iblbm_dfc_lambda_noalloc", _i, [_vp, _i, _d, _i, _i, _i, _vp, _vp]),
     ("iblbm_set_kernel_variant", _i, [_i, _i, _i]),
     ("iblbm_kernel_variant", _i, [_i, _i, _pi, _pd]),
     ("iblbm_server_create", _i, [_sz, _i, _vp, _P(_vp)]),

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_2609_02298_b300", "csrc")
 LIB = os.path.join(HERE, "libiblbm_emu.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "server.cu")] + \
+SOURCES = [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "server.cu", "noalloc.cu")] + \
           [os.path.join(HERE, "emu_runtime.cpp")]
 
 
