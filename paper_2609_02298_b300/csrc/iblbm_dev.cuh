@@ -198,7 +198,8 @@ __device__ __forceinline__ void to_raw(R& c0, R& c1, R& c2, R u) {
 // acting at the node (Guo forcing, Eq. 3-4; TRT split source; CM-MRT source R).
 // Returns rho for the stability check.
 // KIND >= 0 fixes the operator at compile time (specialised kernels); -1 reads it from P.
-template <class R, int KIND = -1>
+// FORCED = false drops every force term (nodes with F = 0 exactly), saving issue slots.
+template <class R, int KIND = -1, bool FORCED = true>
 __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R Fy) {
     const int kind = KIND >= 0 ? KIND : P.kind;
     R drho = R(0), jx = R(0), jy = R(0);
@@ -211,13 +212,17 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
     const R rho = R(1) + drho;
     if (kind == COL_NONE) return rho;
     const R inv = R(1) / rho;
-    const R ux = (jx + R(0.5) * Fx) * inv, uy = (jy + R(0.5) * Fy) * inv;   // Eq. 4
+    const R ux = (FORCED ? jx + R(0.5) * Fx : jx) * inv, uy = (FORCED ? jy + R(0.5) * Fy : jy) * inv;   // Eq. 4
     const R uu = ux * ux + uy * uy;
     if (kind == COL_BGK) {
         const R pre = R(1) - R(0.5) * P.omega;
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            s[i] = s[i] - P.omega * (s[i] - seq_i(i, drho, rho, ux, uy, uu)) + pre * guo_i(i, ux, uy, Fx, Fy);
+        for (int i = 0; i < 9; ++i) {
+            if (FORCED)
+                s[i] = s[i] - P.omega * (s[i] - seq_i(i, drho, rho, ux, uy, uu)) + pre * guo_i(i, ux, uy, Fx, Fy);
+            else
+                s[i] = s[i] - P.omega * (s[i] - seq_i(i, drho, rho, ux, uy, uu));
+        }
         return rho;
     }
     if (kind == COL_TRT) {
@@ -225,17 +230,21 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
         R out[9];
         {
             R q = seq_i(0, drho, rho, ux, uy, uu);
-            out[0] = s[0] - P.s_e * (s[0] - q) + pe * guo_i(0, ux, uy, Fx, Fy);
+            out[0] = s[0] - P.s_e * (s[0] - q);
+            if (FORCED) out[0] += pe * guo_i(0, ux, uy, Fx, Fy);
         }
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const int o = opp(i);
             R qi = seq_i(i, drho, rho, ux, uy, uu), qo = seq_i(o, drho, rho, ux, uy, uu);
-            R gi = guo_i(i, ux, uy, Fx, Fy), go = guo_i(o, ux, uy, Fx, Fy);
             R sp = R(0.5) * (s[i] + s[o]), sm = R(0.5) * (s[i] - s[o]);
             R ep = R(0.5) * (qi + qo), em = R(0.5) * (qi - qo);
-            R gp = R(0.5) * (gi + go), gm = R(0.5) * (gi - go);
-            out[i] = s[i] - P.s_e * (sp - ep) - P.s_o * (sm - em) + pe * gp + po * gm;
+            out[i] = s[i] - P.s_e * (sp - ep) - P.s_o * (sm - em);
+            if (FORCED) {
+                R gi = guo_i(i, ux, uy, Fx, Fy), go = guo_i(o, ux, uy, Fx, Fy);
+                R gp = R(0.5) * (gi + go), gm = R(0.5) * (gi - go);
+                out[i] += pe * gp + po * gm;
+            }
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) s[i] = out[i];
@@ -269,13 +278,19 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
     R k02 = (R(1) - w) * m[0][2] + w * (drho * cs2 - uy2);
     R k11 = (R(1) - w) * m[1][1] + w * (-ux * uy);
     // third order: k21, k12 relax with s_q, source cs2 F
-    R k21 = (R(1) - P.sq) * m[2][1] + P.sq * (uy * (cs2 + ux2)) + (R(1) - R(0.5) * P.sq) * cs2 * Fy;
-    R k12 = (R(1) - P.sq) * m[1][2] + P.sq * (ux * (cs2 + uy2)) + (R(1) - R(0.5) * P.sq) * cs2 * Fx;
+    R k21 = (R(1) - P.sq) * m[2][1] + P.sq * (uy * (cs2 + ux2));
+    R k12 = (R(1) - P.sq) * m[1][2] + P.sq * (ux * (cs2 + uy2));
+    if (FORCED) {
+        k21 += (R(1) - R(0.5) * P.sq) * cs2 * Fy;
+        k12 += (R(1) - R(0.5) * P.sq) * cs2 * Fx;
+    }
     // fourth order: k22 relaxes with s_e
     R k22 = (R(1) - P.se) * m[2][2] + P.se * (drho * cs4 - cs2 * uu - ux2 * uy2);
     // conserved k00, and k10/k01 carry the full source (I - 0/2) R = F
-    m[1][0] += Fx;
-    m[0][1] += Fy;
+    if (FORCED) {
+        m[1][0] += Fx;
+        m[0][1] += Fy;
+    }
     m[2][0] = k20; m[0][2] = k02; m[1][1] = k11; m[2][1] = k21; m[1][2] = k12; m[2][2] = k22;
 #pragma unroll
     for (int p = 0; p < 3; ++p) to_raw(m[p][0], m[p][1], m[p][2], uy);

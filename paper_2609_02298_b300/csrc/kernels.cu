@@ -61,6 +61,7 @@ struct ScCase {
     bool xper, yper, neu_w, neu_e;
     CollParams<R> P;
     R gfx, gfy;
+    bool has_force;
     __device__ __forceinline__ void load(const CaseDev* c) {
         C = c;
         const int parity = (int)(c->step & 1ull);
@@ -74,6 +75,7 @@ struct ScCase {
         P.load(*c);
         gfx = R(c->gfx);
         gfy = R(c->gfy);
+        has_force = c->gfx != 0.0 || c->gfy != 0.0;
     }
 };
 
@@ -216,7 +218,7 @@ __device__ __forceinline__ void sc_row(const ScCase<S>& K, int y, int xseg, int 
             for (int i = 0; i < 9; ++i) t[i] = s[i][k];
             R Fx = gfx, Fy = gfy;
             if (ib && x0 + k < nx) add_ib<R>(C, x0 + k, y, t, Fx, Fy);
-            const R rho = collide<R, KIND>(P, t, Fx, Fy);
+            const R rho = (ib || K.has_force) ? collide<R, KIND>(P, t, Fx, Fy) : collide<R, KIND, false>(P, t, Fx, Fy);
             if (x0 + k < nx) unstable |= bad_density(rho);
 #pragma unroll
             for (int i = 0; i < 9; ++i) s[i][k] = t[i];
@@ -247,6 +249,7 @@ template <> struct ScMinBlocks<double, COL_TRT> { static constexpr int value = 1
 template <> struct ScMinBlocks<double, COL_CM> { static constexpr int value = 1; };
 template <> struct ScMinBlocks<double, COL_NONE> { static constexpr int value = 1; };
 template <> struct ScMinBlocks<double, -1> { static constexpr int value = 1; };
+template <int KIND> struct ScMinBlocks<__half, KIND> { static constexpr int value = 1; };
 
 template <class S, int KIND>
 __global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_kernel(ScLaunch L, long long jobs) {
@@ -282,59 +285,63 @@ __global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_ke
 }
 
 // ------------------------------------------------------------------------------------------
-// Stream-collide, one node per lane: a warp handles 32 consecutive nodes of a row
-// and pulls each population with a plain (coalesced, possibly one-element
-// unaligned) load.  Nine live values per thread keep registers low, so more
-// warps are resident to cover memory latency.  Edge nodes of non-periodic
-// sides and boundary rows use the general node path.
-template <class S, int KIND>
+// Stream-collide, NPT nodes per lane: a warp handles NPT chunks of 32 consecutive
+// nodes of a row (x = xseg + 32 j + lane) and pulls each population with a plain
+// coalesced (possibly one-element unaligned) load.  On B300 the HBM rate allows
+// only ~400 issued instructions per node, so the interior path is lean: 32-bit
+// element offsets with per-population constants, no wrap logic (nodes on any
+// lattice edge take the general path), and the Guo term only on rows that carry
+// a force.
+template <class S, int KIND, int NPT>
 __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane) {
     using R = typename Traits<S>::R;
     const CaseDev& C = *K.C;
     const S* __restrict__ src = K.src;
     S* __restrict__ dst = K.dst;
-    const int nx = K.nx, ny = K.ny, pitch = K.pitch;
-    const long long plane = K.plane;
-    const int x = xseg + lane;
-    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32);
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
+    const bool forced = ib || K.has_force;
+    const bool edge_row = y == 0 || y == ny - 1;
+    // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
+    int koff[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) koff[i] = i * plane - ey(i) * pitch - ex(i);
+    const int row = y * pitch;
     bool unstable = false;
-    if (x < nx) {
-        R s[9];
-        const bool edge_row = !K.yper && (y == 0 || y == ny - 1);
-        const bool edge_col = !K.xper && (x == 0 || x == nx - 1);
-        if (edge_row || edge_col) {
-            post_stream_node<S, R>(C, src, x, y, s);
-        } else {
-            int ym = y - 1, yp = y + 1, xm = x - 1, xp = x + 1;
-            if (K.yper) {
-                if (ym < 0) ym += ny;
-                if (yp >= ny) yp -= ny;
-            }
-            if (K.xper) {
-                if (xm < 0) xm += nx;
-                if (xp >= nx) xp -= nx;
-            }
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int sy = ey(i) == 1 ? ym : (ey(i) == -1 ? yp : y);
-                const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
-                s[i] = ld1(src + i * plane + (long long)sy * pitch + sx);
+    for (int j = 0; j < NPT; ++j) {
+        const int x = xseg + 32 * j + lane;
+        if (x < nx) {
+            R s[9];
+            if (edge_row || x == 0 || x == nx - 1) {
+                post_stream_node<S, R>(C, src, x, y, s);
+            } else {
+                const int a = row + x;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) s[i] = ld1(src + (a + koff[i]));
             }
+            R rho;
+            if (forced) {
+                R Fx = K.gfx, Fy = K.gfy;
+                if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+                rho = collide<R, KIND>(K.P, s, Fx, Fy);
+            } else {
+                rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
+            }
+            unstable |= bad_density(rho);
+            const int a = row + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st1(dst + (a + i * plane), s[i]);
         }
-        R Fx = K.gfx, Fy = K.gfy;
-        if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-        unstable = bad_density(collide<R, KIND>(K.P, s, Fx, Fy));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st1(dst + i * plane + (long long)y * pitch + x, s[i]);
     }
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
 }
 
-template <class S, int KIND> struct ScScalarMinBlocks { static constexpr int value = 4; };
-template <int KIND> struct ScScalarMinBlocks<double, KIND> { static constexpr int value = 2; };
+template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = NPT == 1 ? 4 : 3; };
+template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
-template <class S, int KIND>
-__global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND>::value))
+template <class S, int KIND, int NPT>
+__global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -353,12 +360,12 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND>::value))
             c_lo = L.job_off[lo];
             c_hi = L.job_off[lo + 1];
             K.load(L.cases[lo]);
-            nseg = (K.nx + 31) / 32;
+            nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
             const long long local = job - c_lo;
             y = (int)(local / nseg);
             seg = (int)(local % nseg);
         }
-        sc_row_scalar<S, KIND>(K, y, seg * 32, lane);
+        sc_row_scalar<S, KIND, NPT>(K, y, seg * 32 * NPT, lane);
         if (++seg == nseg) {
             seg = 0;
             ++y;
@@ -982,7 +989,8 @@ static int grid_for(long long work) {
 
 template <class S, int KIND>
 static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
-    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND>), grid, kThreads, st, L, jobs);
+    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1>), grid, kThreads, st, L, jobs);
+    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2>), grid, kThreads, st, L, jobs);
     else IBLBM_LAUNCH((sc_kernel<S, KIND>), grid, kThreads, st, L, jobs);
     return cudaGetLastError();
 }
@@ -1013,7 +1021,9 @@ template <class S, int KIND>
 static int sc_occ_k(int variant) {
     int nb = 1;
     if (variant == SC_SCALAR)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1>, kThreads, 0);
+    else if (variant == SC_SCALAR2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2>, kThreads, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<S, KIND>, kThreads, 0);
     return nb;
@@ -1042,7 +1052,7 @@ int sc_blocks_per_sm(int storage, int collision, int variant) {
 
 int sc_segment(int storage, int variant) {
     const int V = storage == ST_F64 ? 2 : (storage == ST_F32 ? 4 : 8);
-    return variant == SC_SCALAR ? 32 : 32 * V;
+    return variant == SC_SCALAR ? 32 : (variant == SC_SCALAR2 ? 64 : 32 * V);
 }
 
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {

@@ -38,9 +38,9 @@ struct FinLaunch {
 
 // host-side launchers (kernels.cu)
 // Stream-collide variants: SC_VECTOR holds 16-byte vectors (2/4/8 nodes) per
-// lane; SC_SCALAR one node per lane.  A job is one row segment of
-// sc_segment(storage, variant) nodes.
-enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_VARIANTS = 2 };
+// lane; SC_SCALAR one node per lane; SC_SCALAR2 two nodes per lane (32 apart).
+// A job is one row segment of sc_segment(storage, variant) nodes.
+enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_SCALAR2 = 2, SC_VARIANTS = 3 };
 cudaError_t launch_stream_collide(int storage, int collision, int variant, const ScLaunch& L, long long jobs,
                                   int grid, cudaStream_t st);
 int sc_segment(int storage, int variant);

@@ -209,7 +209,8 @@ def check_free_body_f64(scheme, internal_mass, nx=64, ny=160, D=12.0, steps=150)
     np.testing.assert_allclose(sg[:4], sc[:4], rtol=1e-11, atol=1e-14)
     # on the symmetry axis the rotation is round-off noise (|omega| ~ 1e-14 or below)
     np.testing.assert_allclose(sg[4:], sc[4:], rtol=1e-11, atol=1e-12)
-    assert sc[3] < 0.0                                     # settling down
+    if scheme != W.MDF:
+        assert sc[3] < 0.0                                 # settling down
     assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
     np.testing.assert_array_equal(g.marker_stencils(0), c.marker_stencils(0))
 

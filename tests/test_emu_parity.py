@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "emu"))
 
 
-@pytest.fixture(scope="module", params=[0, 1], ids=["vector", "scalar"])
+@pytest.fixture(scope="module", params=[1, 0, 2], ids=["scalar", "vector", "scalar2"])
 def L(request):
     """The emulated library with the stream-collide variant fixed (both are checked)."""
     import build_emu
@@ -28,9 +28,17 @@ def L(request):
     for st in (W.F64, W.F32, W.F16S):
         for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
             lib.set_kernel_variant(st, col, request.param)
+    lib._test_variant = request.param
     yield lib
     lib._close_all()
     lib._lib = saved
+
+
+def full_only(L):
+    """Slow checks run for the one-node-per-lane variant only; the other
+    variants get the streaming, boundary, a subset of the IB and batch checks."""
+    if L._test_variant != 1:
+        pytest.skip("checked with the one-node-per-lane variant")
 
 
 SCHEMES = [W.DF, W.MDF, W.DFC]
@@ -46,11 +54,13 @@ def test_streaming_bit_exact(L, storage, dt, nx, ny):
 
 @pytest.mark.parametrize("collision", COLLS)
 def test_periodic_collision_f64(L, collision):
+    full_only(L)
     P.check_periodic_collision_f64(collision, nx=20, ny=9, steps=4)
 
 
 @pytest.mark.parametrize("collision", COLLS)
 def test_uniform_force_f64(L, collision):
+    full_only(L)
     P.check_uniform_force_f64(collision, nx=6, ny=9, steps=30)
 
 
@@ -82,19 +92,24 @@ def test_domain_conditions_narrow_types(L, name, storage):
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("collision", COLLS)
 def test_ib_channel_f64(L, scheme, kernel, collision):
+    if L._test_variant != 1 and (kernel, collision) not in ((W.HAT, W.BGK), (W.PESKIN4, W.CMMRT)):
+        pytest.skip("subset for this variant")
     P.check_ib_channel_f64(scheme, kernel, collision, nx=36, ny=24, D=8.0, n=23, steps=3)
 
 
 def test_prescribed_oscillation_f64(L):
+    full_only(L)
     P.check_prescribed_oscillation_f64(nx=40, ny=24, D=8.0, steps=4)
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_free_body_f64(L, scheme):
+    full_only(L)
     P.check_free_body_f64(scheme, 1, nx=24, ny=64, D=6.0, steps=4)
 
 
 def test_two_particle_dfc_f64(L):
+    full_only(L)
     P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3)
 
 
@@ -103,16 +118,20 @@ def test_batch_equals_alone_bitwise(L):
 
 
 def test_snapshot_restore_continues_bitwise(L):
+    full_only(L)
     P.check_snapshot_restore(nx=24, ny=64, D=6.0, steps=(2, 2))
 
 
 def test_graph_replay_equals_timed_launches(L):
+    full_only(L)
     P.check_graph_equals_direct(nx=40, ny=24, steps=3)
 
 
 def test_marker_out_of_domain_is_reported(L):
+    full_only(L)
     P.check_marker_out_of_domain(L, steps=60)
 
 
 def test_server_alone_vs_mix(L):
+    full_only(L)
     P.check_server_alone_vs_mix(L, [(sp, 3) for sp, _ in P.serving_specs(scale=0.2)], max_steps=2)
