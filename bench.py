@@ -14,6 +14,7 @@ on the host cores instead, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import math
 import os
@@ -25,6 +26,7 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+faulthandler.enable()   # a crash prints the Python stack to stderr
 
 import numpy as np  # noqa: E402
 
@@ -221,6 +223,33 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
     return out
 
 
+def single_case_report(L, torch, steps=2000):
+    """One lattice stepped alone (graph-replayed iblbm_step): the 200x100 Re=20
+    cylinder (DF, hat, BGK) in FP64 and FP32, and one 2048x1024 lattice of the
+    matrix (DF, Peskin, BGK, FP32).  Small lattices are latency-bound, so these
+    are reported as microseconds per step beside MLUPS."""
+    out = {}
+    cases = [("cyl-re20-200x100-f64", W.fixed_cylinder_re20(storage=W.F64), steps),
+             ("cyl-re20-200x100-f32", W.fixed_cylinder_re20(storage=W.F32), steps),
+             ("cyl-re100-2048x1024-f32", W.fixed_cylinder_2048(re=100.0, storage=W.F32, collision=W.BGK,
+                                                               kernel=W.PESKIN4, scheme=W.DF), steps // 4)]
+    for name, spec, n in cases:
+        lat = L.Lattice.from_spec(spec)
+        lat.step(20)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        lat.step(n)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        lat.sync()
+        lat.close()
+        out[name] = {"us_per_step": 1e3 * ms / n, "mlups": spec.nodes * n / (ms / 1e3) / 1e6, "steps": n}
+    return out
+
+
 def run_reference(args, specs):
     """--impl reference: the oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -353,6 +382,12 @@ def main():
 
     for l in lats:
         l.close()
+    single = None
+    if rank == 0 and not args.small and args.serving_requests > 0:
+        try:
+            single = single_case_report(L, torch)
+        except Exception as exc:
+            single = {"error": repr(exc)}
     serving = None
     if rank == 0 and args.serving_requests > 0 and not args.small:
         try:
@@ -392,6 +427,7 @@ def main():
             "gpu_launches": 6 * args.steps,
             "clocks": clocks.summary(),
             "device_status": rc,
+            "single_lattice": single,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

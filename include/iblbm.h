@@ -204,13 +204,16 @@ const char* iblbm_strerror(int status);
 int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
 
 /* ---- stream-collide kernel variants (tuning control; no counterpart in the paper) ---- */
-/* Two implementations of the fused stream-collide exist: 0 keeps a 16-byte
- * vector of nodes per lane, 1 one node per lane.  By default the first batch
- * that needs a (storage, collision) pair times both in place and keeps the
- * faster for the rest of the process, so a lattice runs the same kernel alone,
- * batched or served.  iblbm_set_kernel_variant fixes the choice (-1 = tune
- * again); iblbm_kernel_variant reports it (-1 = not chosen) and the mean
- * launch times (ms[2]) measured when it was tuned.  Errors: INVALID_ARG. */
+/* IBLBM_KERNEL_VARIANTS implementations of the fused stream-collide exist:
+ * 0 keeps a 16-byte vector of nodes per lane, 1 one node per lane, 2 two nodes
+ * per lane.  By default the first batch that needs a (storage, collision) pair
+ * times all of them in place and keeps the fastest for the rest of the
+ * process, so a lattice runs the same kernel alone, batched or served.
+ * iblbm_set_kernel_variant fixes the choice (-1 = tune again);
+ * iblbm_kernel_variant reports it (-1 = not chosen) and, if ms is not NULL,
+ * writes the mean launch time of each variant measured when it was tuned
+ * into ms[IBLBM_KERNEL_VARIANTS].  Errors: INVALID_ARG. */
+#define IBLBM_KERNEL_VARIANTS 3
 int iblbm_set_kernel_variant(int storage, int collision, int variant);
 int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);
 

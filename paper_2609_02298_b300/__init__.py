@@ -346,12 +346,15 @@ def set_kernel_variant(storage: int, collision: int, variant: int) -> None:
     _check(load_library().iblbm_set_kernel_variant(storage, collision, variant), "iblbm_set_kernel_variant")
 
 
+KERNEL_VARIANTS = 3   # IBLBM_KERNEL_VARIANTS
+
+
 def kernel_variant(storage: int, collision: int):
-    """(chosen variant or -1, [ms of variant 0, ms of variant 1] from tuning)."""
+    """(chosen variant or -1, [tuning time in ms of each variant])."""
     v = C.c_int(-1)
-    ms = (C.c_double * 2)()
+    ms = (C.c_double * KERNEL_VARIANTS)()
     _check(load_library().iblbm_kernel_variant(storage, collision, C.byref(v), ms), "iblbm_kernel_variant")
-    return v.value, [ms[0], ms[1]]
+    return v.value, list(ms)
 
 
 def step_batch(lattices: Iterable[Lattice], nsteps: int) -> None:

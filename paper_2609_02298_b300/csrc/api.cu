@@ -720,6 +720,7 @@ struct BatchGroup {
 // source, so repeating it has no effect on the state).
 int g_variant[3][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
 double g_variant_ms[3][5][SC_VARIANTS];
+static_assert(SC_VARIANTS == IBLBM_KERNEL_VARIANTS, "public variant count must match the kernels");
 struct IbGroup {
     int storage = 0;
     BodyRef* drefs = nullptr;
