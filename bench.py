@@ -292,6 +292,8 @@ def main():
                     help="use only the first K lattices of the matrix (profiling a smaller case)")
     ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests in the serving stream (0: not reported)")
+    ap.add_argument("--kernel-variant", type=int, default=-1,
+                    help="fix the stream-collide variant (0-3) instead of tuning it (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     nx, ny = (256, 128) if args.small else (2048, 1024)
@@ -318,6 +320,9 @@ def main():
 
     import paper_2609_02298_b300 as L
     L.use_torch_allocator()
+    if args.kernel_variant >= 0:
+        for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
+            L.set_kernel_variant(specs[0].storage, col, args.kernel_variant)
     lats = [L.Lattice.from_spec(s) for s in specs]
     nodes = sum(s.nodes for s in specs)
     storage = specs[0].storage

@@ -109,7 +109,10 @@ typedef struct {
 /* ---- memory --------------------------------------------------------------------- */
 /* Installs the device allocator used by every later context (process-wide).
  * alloc(bytes, stream, user) returns a device pointer or NULL; free(ptr, stream,
- * user) releases it.  Passing NULL functions restores cudaMalloc/cudaFree. */
+ * user) releases it.  Pointers should be at least 16-byte aligned (256 like
+ * cudaMalloc is best); the bulk-staged stream-collide variant is skipped for a
+ * lattice whose population buffers are not.  Passing NULL functions restores
+ * cudaMalloc/cudaFree. */
 typedef void* (*iblbm_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void (*iblbm_free_fn)(void* ptr, void* stream, void* user);
 int iblbm_set_allocator(iblbm_alloc_fn alloc, iblbm_free_fn free_fn, void* user);
@@ -206,14 +209,17 @@ int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
 /* ---- stream-collide kernel variants (tuning control; no counterpart in the paper) ---- */
 /* IBLBM_KERNEL_VARIANTS implementations of the fused stream-collide exist:
  * 0 keeps a 16-byte vector of nodes per lane, 1 one node per lane, 2 two nodes
- * per lane.  By default the first batch that needs a (storage, collision) pair
+ * per lane, 3 stages each tile's source rows in shared memory with bulk
+ * asynchronous copies (needs 16-byte aligned population buffers, see
+ * iblbm_set_allocator; otherwise variant 1 runs in its place and its tuning
+ * time reads 0).  By default the first batch that needs a (storage, collision) pair
  * times all of them in place and keeps the fastest for the rest of the
  * process, so a lattice runs the same kernel alone, batched or served.
  * iblbm_set_kernel_variant fixes the choice (-1 = tune again);
  * iblbm_kernel_variant reports it (-1 = not chosen) and, if ms is not NULL,
  * writes the mean launch time of each variant measured when it was tuned
  * into ms[IBLBM_KERNEL_VARIANTS].  Errors: INVALID_ARG. */
-#define IBLBM_KERNEL_VARIANTS 3
+#define IBLBM_KERNEL_VARIANTS 4
 int iblbm_set_kernel_variant(int storage, int collision, int variant);
 int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);
 

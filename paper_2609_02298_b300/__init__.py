@@ -342,11 +342,11 @@ class Lattice:
 
 
 def set_kernel_variant(storage: int, collision: int, variant: int) -> None:
-    """Fixes the stream-collide variant (0 vector, 1 one node per lane, -1 retune)."""
+    """Fixes the stream-collide variant (0 vector, 1 / 2 nodes per lane, 3 bulk-staged; -1 retune)."""
     _check(load_library().iblbm_set_kernel_variant(storage, collision, variant), "iblbm_set_kernel_variant")
 
 
-KERNEL_VARIANTS = 3   # IBLBM_KERNEL_VARIANTS
+KERNEL_VARIANTS = 4   # IBLBM_KERNEL_VARIANTS
 
 
 def kernel_variant(storage: int, collision: int):

@@ -45,6 +45,7 @@ void dev_free(void* p, cudaStream_t st) {
 }
 
 int status_from_bits(unsigned bits) {
+    if (bits & STAT_TIMEOUT) return IBLBM_ERR_TIMEOUT;
     if (bits & STAT_MARKER_OUT) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
     if (bits & STAT_UNSTABLE) return IBLBM_ERR_UNSTABLE;
     if (bits & STAT_CAPACITY) return IBLBM_ERR_CAPACITY;
@@ -349,6 +350,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     B.csr_off = (int*)c->alloc(4 * (size_t)(nent + 1));
     B.csr_ent = (int*)c->alloc(4 * (size_t)nent);
     B.fill = (int*)c->alloc(4 * (size_t)nent);
+    B.csr_w = c->alloc(rb * (size_t)nent);
     B.ij = (int*)c->alloc(8 * (size_t)n);
     B.wts = c->alloc(rb * 8 * (size_t)n);
     B.fpdata = c->alloc(rb * 9 * (size_t)nent);
@@ -356,7 +358,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     B.mk = c->alloc(rb * 16 * (size_t)n);
     B.hist = (double*)c->alloc(24 * (size_t)hist_cap);
     if (!B.X || !B.Y || !B.r0x || !B.r0y || !B.Udx || !B.Udy || !B.Fx || !B.Fy || !B.lam || !B.node_map ||
-        !B.fp_node || !B.csr_off || !B.csr_ent || !B.fill || !B.ij || !B.wts || !B.fpdata || !B.patch || !B.mk ||
+        !B.fp_node || !B.csr_off || !B.csr_ent || !B.fill || !B.csr_w || !B.ij || !B.wts || !B.fpdata || !B.patch || !B.mk ||
         !B.hist)
         return IBLBM_ERR_OOM;
     std::vector<double> X(n), Y(n), rx(n), ry(n);
@@ -691,7 +693,7 @@ size_t iblbm_internal_estimate_bytes(const iblbm_lattice_desc* d, int n, double 
         const size_t hc = hist_cap > 0 ? (size_t)hist_cap : 65536;
         b += 9 * rounded(8 * (size_t)n) + rounded(4 * (size_t)box_capacity(reach, S)) + 3 * rounded(4 * nent) +
              rounded(4 * (nent + 1)) + rounded(8 * (size_t)n) + rounded(rb * 8 * n) + 2 * rounded(rb * 9 * nent) +
-             rounded(rb * 16 * n) + rounded(24 * hc);
+             rounded(rb * nent) + rounded(rb * 16 * n) + rounded(24 * hc);
     }
     return b;
 }
@@ -708,9 +710,10 @@ struct BatchGroup {
     int collision = 0;
     int ncases = 0;
     CaseDev** dcases = nullptr;
-    long long jobs[SC_VARIANTS] = {0, 0};      // per kernel variant (segment widths differ)
-    int grid[SC_VARIANTS] = {1, 1};
-    long long* djob[SC_VARIANTS] = {nullptr, nullptr};
+    long long jobs[SC_VARIANTS] = {};          // per kernel variant (segment widths differ)
+    int grid[SC_VARIANTS] = {};
+    long long* djob[SC_VARIANTS] = {};
+    bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
 };
 
 // Stream-collide variant per (storage, collision), process-wide so that a lattice
@@ -766,7 +769,8 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         }
     }
     for (auto& g : P->groups) {
-        const int v = g_variant[g.storage][g.collision] < 0 ? SC_SCALAR : g_variant[g.storage][g.collision];
+        int v = g_variant[g.storage][g.collision] < 0 ? SC_SCALAR : g_variant[g.storage][g.collision];
+        if (!g.ok[v]) v = SC_SCALAR;
         ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
         cudaEvent_t a = nullptr, b = nullptr;
         if (timer) {
@@ -837,10 +841,13 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             for (int v = 0; v < SC_VARIANTS; ++v) {
                 const int seg = sc_segment(st, v);
                 std::vector<long long> off{0};
+                g.ok[v] = true;
                 for (int i = 0; i < n; ++i) {
                     iblbm_ctx* c = ctxs[i];
-                    if (c->hc.storage == st && c->hc.collision == col)
+                    if (c->hc.storage == st && c->hc.collision == col) {
                         off.push_back(off.back() + (long long)c->hc.ny * ((c->hc.nx + seg - 1) / seg));
+                        g.ok[v] = g.ok[v] && sc_variant_ok(v, c->hc.f[0], c->hc.f[1]);
+                    }
                 }
                 g.jobs[v] = off.back();
                 g.djob[v] = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
@@ -875,6 +882,10 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         int best = SC_SCALAR;
         double best_ms = 1e300;
         for (int v = 0; v < SC_VARIANTS; ++v) {
+            if (!g.ok[v]) {
+                g_variant_ms[g.storage][g.collision][v] = 0.0;
+                continue;
+            }
             ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
             float ms = 0.f, tot = 0.f;
             launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);   // warm

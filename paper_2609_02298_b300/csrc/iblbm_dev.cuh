@@ -12,6 +12,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #define IBLBM_LAUNCH(kern, grid, block, stream, ...) kern<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__)
+#define IBLBM_LAUNCH_SMEM(kern, grid, block, smem, stream, ...) \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__)
+#define IBLBM_DYNAMIC_SMEM(name) extern __shared__ __align__(128) unsigned char name[]
 #endif
 #include <stdint.h>
 
@@ -31,6 +34,7 @@ enum : unsigned {
     STAT_MARKER_OUT = 2u,
     STAT_CAPACITY = 4u,
     STAT_MDF_WARN = 8u,
+    STAT_TIMEOUT = 16u,   // a bounded device-side wait gave up
 };
 
 constexpr int kMaxBodies = 64;   // bodies per lattice
@@ -81,6 +85,7 @@ struct BodyDev {
     int* csr_off;                 // [nent + 1]
     int* csr_ent;                 // [nent] entry = k*S*S + b*S + a, sorted by k per slot
     int* fill;                    // [nent]
+    void* csr_w;                  // [nent] kernel weight D of each CSR entry (R)
     int* ij;                      // [2n] stencil origins
     void* wts;                    // [n][8] kernel weights phi_x[4], phi_y[4] (R)
     void* fpdata;                 // [nent][9] gathered slot data (R)

@@ -9,6 +9,7 @@
 //                  the step counters.
 #include <climits>
 
+#include "async_copy.cuh"
 #include "kernels.cuh"
 
 namespace iblbm {
@@ -374,13 +375,164 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
 }
 
 // ------------------------------------------------------------------------------------------
+// Stream-collide with bulk-staged sources (SC_BULK).  A job is a tile of TW nodes
+// of one row; its nine source rows (row y - e_iy of plane i, columns x0 - H ..
+// x0 + TW + H, H = one 16-byte halo) arrive in shared memory by cp.async.bulk
+// on an mbarrier, NST tiles ahead of the one being computed.  The copy engine
+// keeps ~NST x 9 rows per CTA in flight without holding registers, which is what
+// a pull-streaming sweep needs to cover HBM latency; the compute side reads each
+// population with one shared load at a constant offset.  Lattice-edge nodes and
+// the first and last rows take the general path (global pulls with the domain
+// conditions), as in the other variants.
+template <class S> struct BulkCfg;
+template <> struct BulkCfg<float> { static constexpr int NPT = 2, NST = 4, MINB = 2; };
+template <> struct BulkCfg<__half> { static constexpr int NPT = 2, NST = 6, MINB = 2; };
+template <> struct BulkCfg<double> { static constexpr int NPT = 1, NST = 4, MINB = 2; };
+template <class S> struct BulkGeom {
+    static constexpr int H = 16 / (int)sizeof(S);
+    static constexpr int TW = kThreads * BulkCfg<S>::NPT;
+    static constexpr int RS = TW + 2 * H;                          // elements per staged row
+    static constexpr int STAGE = 9 * RS * (int)sizeof(S);          // bytes per stage
+    static constexpr int BAR = 128;                                // barriers + abort flag; keeps stages aligned
+    static_assert(8 * BulkCfg<S>::NST + 4 <= BAR, "barrier block too small");
+    static constexpr int SMEM = BAR + BulkCfg<S>::NST * STAGE;
+    static_assert((RS * (int)sizeof(S)) % 16 == 0, "staged rows must stay 16-byte aligned");
+};
+constexpr long kBulkSpinLimit = 1L << 22;   // polls of an mbarrier before the kernel gives up
+
+__device__ __forceinline__ double lds1(const double* p) { return *p; }
+__device__ __forceinline__ float lds1(const float* p) { return *p; }
+__device__ __forceinline__ float lds1(const __half* p) { return __half2float(*p); }
+
+// Case index, row and first column of tile `job`.
+template <int TW>
+__device__ __forceinline__ int bulk_locate(const ScLaunch& L, long long job, int& y, int& x0) {
+    int lo = 0, hi = L.ncases - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+    }
+    const CaseDev& C = *L.cases[lo];
+    const int nseg = (C.nx + TW - 1) / TW;
+    const long long local = job - L.job_off[lo];
+    y = (int)(local / nseg);
+    x0 = (int)(local % nseg) * TW;
+    return lo;
+}
+
+// Issued by one thread: the nine source rows of tile `job` into `st`, completing on `bar`.
+template <class S>
+__device__ __forceinline__ void bulk_issue(const ScLaunch& L, long long job, S* st, uint64_t* bar) {
+    using G = BulkGeom<S>;
+    int y, x0;
+    const CaseDev& C = *L.cases[bulk_locate<G::TW>(L, job, y, x0)];
+    if (y == 0 || y == C.ny - 1) {   // general path: nothing to stage
+        bar_arrive_tx(bar, 0);
+        return;
+    }
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    const int xs = max(x0 - G::H, 0), xe = min(x0 + G::TW + G::H, C.pitch);
+    const unsigned bytes = (unsigned)((xe - xs) * (int)sizeof(S));
+    bar_arrive_tx(bar, 9u * bytes);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        bulk_g2s(st + i * G::RS + (xs - x0 + G::H), src + i * C.plane + (long long)(y - ey(i)) * C.pitch + xs, bytes,
+                 bar);
+}
+
+template <class S, int KIND>
+__global__ void __launch_bounds__(kThreads, (BulkCfg<S>::MINB)) sc_kernel_bulk(ScLaunch L, long long jobs) {
+    using R = typename Traits<S>::R;
+    using G = BulkGeom<S>;
+    constexpr int NST = BulkCfg<S>::NST, NPT = BulkCfg<S>::NPT, TW = G::TW, RS = G::RS, H = G::H;
+    IBLBM_DYNAMIC_SMEM(smem);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    volatile int& abort_at = *reinterpret_cast<int*>(smem + 8 * NST);
+    S* stages = reinterpret_cast<S*>(smem + G::BAR);
+    const int tid = threadIdx.x;
+    const long long j0 = jobs * blockIdx.x / gridDim.x, j1 = jobs * (blockIdx.x + 1) / gridDim.x;
+    if (tid == 0) {
+        for (int k = 0; k < NST; ++k) bar_init(&bars[k], 1);
+        fence_bar_init();
+        abort_at = -1;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < NST && j0 + k < j1; ++k) bulk_issue<S>(L, j0 + k, stages + k * 9 * RS, &bars[k]);
+
+    ScCase<S> K;
+    int cur = -1;
+    long long stop = -1;
+    for (long long job = j0; job < j1; ++job) {
+        const int k = (int)((job - j0) % NST);
+        const unsigned parity = (unsigned)(((job - j0) / NST) & 1);
+        int y, x0;
+        const int c = bulk_locate<TW>(L, job, y, x0);
+        if (c != cur) {
+            K.load(L.cases[c]);
+            cur = c;
+        }
+        const CaseDev& C = *K.C;
+        if (!bar_wait(&bars[k], parity, kBulkSpinLimit)) abort_at = k;
+        __syncthreads();
+        if (abort_at >= 0) {
+            stop = job;
+            break;
+        }
+        const S* st = stages + k * 9 * RS;
+        const bool ib = K.nbodies > 0 && row_has_ib(C, y, x0, x0 + TW);
+        const bool forced = ib || K.has_force;
+        const bool edge_row = y == 0 || y == K.ny - 1;
+        bool unstable = false;
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int x = x0 + tid + kThreads * j;
+            if (x < K.nx) {
+                R s[9];
+                if (edge_row || x == 0 || x == K.nx - 1) {
+                    post_stream_node<S, R>(C, K.src, x, y, s);
+                } else {
+                    const S* b = st + tid + kThreads * j + H;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) s[i] = lds1(b + i * RS - ex(i));
+                }
+                R rho;
+                if (forced) {
+                    R Fx = K.gfx, Fy = K.gfy;
+                    if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+                    rho = collide<R, KIND>(K.P, s, Fx, Fy);
+                } else {
+                    rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
+                }
+                unstable |= bad_density(rho);
+                S* d = K.dst + ((long long)y * K.pitch + x);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+            }
+        }
+        if (__any_sync(0xffffffffu, unstable) && (tid & 31) == 0)
+            atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+        __syncthreads();   // stage k fully read before it is refilled
+        if (tid == 0 && job + NST < j1) bulk_issue<S>(L, job + NST, stages + k * 9 * RS, &bars[k]);
+    }
+    if (stop >= 0 && tid == 0) {
+        // a copy never completed: report it, then wait (bounded) for the stages still in flight
+        int yy, xx;
+        atomicOr(const_cast<unsigned*>(&L.cases[bulk_locate<TW>(L, stop, yy, xx)]->status), STAT_TIMEOUT);
+        for (long long jj = stop; jj < j1 && jj < stop + NST; ++jj)
+            bar_wait(&bars[(jj - j0) % NST], (unsigned)(((jj - j0) / NST) & 1), kBulkSpinLimit);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Block helpers (fixed-order reductions so results do not depend on timing).
+constexpr int kIbThreads = 512;   // threads of the per-body IB CTA
 __device__ __forceinline__ double block_max(double v, double* sh) {
     const int t = threadIdx.x;
     __syncthreads();
     sh[t] = v;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
+    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
         if (t < s) sh[t] = fmax(sh[t], sh[t + s]);
         __syncthreads();
     }
@@ -388,25 +540,29 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
     __syncthreads();
     return r;
 }
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Three sums in one pass of a fixed-order pairwise tree (deterministic).
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
     const int t = threadIdx.x;
     __syncthreads();
-    sh[t] = v;
+    sh[t] = a; sh[kIbThreads + t] = b; sh[2 * kIbThreads + t] = c;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if (t < s) sh[t] = sh[t] + sh[t + s];
+    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            sh[t] += sh[t + s];
+            sh[kIbThreads + t] += sh[kIbThreads + t + s];
+            sh[2 * kIbThreads + t] += sh[2 * kIbThreads + t + s];
+        }
         __syncthreads();
     }
-    const double r = sh[0];
+    a = sh[0]; b = sh[kIbThreads]; c = sh[2 * kIbThreads];
     __syncthreads();
-    return r;
 }
 __device__ __forceinline__ int block_min_i(int v, int* sh) {
     const int t = threadIdx.x;
     __syncthreads();
     sh[t] = v;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
+    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
         if (t < s) sh[t] = min(sh[t], sh[t + s]);
         __syncthreads();
     }
@@ -419,7 +575,7 @@ __device__ __forceinline__ int block_max_i(int v, int* sh) {
     __syncthreads();
     sh[t] = v;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
+    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
         if (t < s) sh[t] = max(sh[t], sh[t + s]);
         __syncthreads();
     }
@@ -436,7 +592,7 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
     const int tid = threadIdx.x, n = B.n, Sx = B.S, SS = Sx * Sx, kern = B.kernel;
     R* wts = static_cast<R*>(B.wts);
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, err = 0;
-    for (int k = tid; k < n; k += kThreads) {
+    for (int k = tid; k < n; k += kIbThreads) {
         const double X = B.X[k], Y = B.Y[k];
         const int i0 = (int)floor(X) - (Sx == 4 ? 1 : 0), j0 = (int)floor(Y) - (Sx == 4 ? 1 : 0);
         if (!(X == X) || !(Y == Y) || i0 < 0 || j0 < 0 || i0 + Sx > C.nx || j0 + Sx > C.ny) err = 1;
@@ -462,16 +618,16 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         return false;
     }
     const int area = bw * bh;
-    for (int q = tid; q < area; q += kThreads) B.node_map[q] = 0;
+    for (int q = tid; q < area; q += kIbThreads) B.node_map[q] = 0;
     __syncthreads();
-    for (int en = tid; en < n * SS; en += kThreads) {
+    for (int en = tid; en < n * SS; en += kIbThreads) {
         const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
         const int node = (B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0);
         atomicAdd(&B.node_map[node], 1);
     }
     __syncthreads();
     // chunked exclusive scans: slot index and CSR offset
-    const int chunk = (area + kThreads - 1) / kThreads;
+    const int chunk = (area + kIbThreads - 1) / kIbThreads;
     const int beg = min(area, tid * chunk), end = min(area, beg + chunk);
     int nz = 0, cnt = 0;
     for (int q = beg; q < end; ++q) {
@@ -480,19 +636,19 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         cnt += c;
     }
     int* sa = shi;
-    int* sb = shi + kThreads + 1;
+    int* sb = shi + kIbThreads + 1;
     sa[tid] = nz;
     sb[tid] = cnt;
     __syncthreads();
     if (tid == 0) {
         int a = 0, b = 0;
-        for (int t = 0; t < kThreads; ++t) {
+        for (int t = 0; t < kIbThreads; ++t) {
             const int ta = sa[t], tb = sb[t];
             sa[t] = a; sb[t] = b;
             a += ta; b += tb;
         }
-        sa[kThreads] = a;
-        sb[kThreads] = b;
+        sa[kIbThreads] = a;
+        sb[kIbThreads] = b;
     }
     __syncthreads();
     int slot = sa[tid], off = sb[tid];
@@ -508,21 +664,22 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
             B.node_map[q] = -1;
         }
     }
-    const int nfp = sa[kThreads];
+    const int nfp = sa[kIbThreads];
     if (tid == 0) {
-        B.csr_off[nfp] = sb[kThreads];
+        B.csr_off[nfp] = sb[kIbThreads];
         B.bx0 = bx0; B.by0 = by0; B.bw = bw; B.bh = bh; B.nfp = nfp;
     }
-    for (int q = tid; q < nfp; q += kThreads) B.fill[q] = 0;
+    for (int q = tid; q < nfp; q += kIbThreads) B.fill[q] = 0;
     __syncthreads();
-    for (int en = tid; en < n * SS; en += kThreads) {
+    for (int en = tid; en < n * SS; en += kIbThreads) {
         const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
         const int node = (B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0);
         const int sl = B.node_map[node];
         B.csr_ent[B.csr_off[sl] + atomicAdd(&B.fill[sl], 1)] = en;
     }
     __syncthreads();
-    for (int q = tid; q < nfp; q += kThreads) {   // insertion sort of each short list
+    R* cw = static_cast<R*>(B.csr_w);
+    for (int q = tid; q < nfp; q += kIbThreads) {   // insertion sort of each short list
         const int o0 = B.csr_off[q], o1 = B.csr_off[q + 1];
         for (int i = o0 + 1; i < o1; ++i) {
             const int v = B.csr_ent[i];
@@ -532,6 +689,10 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
                 --j;
             }
             B.csr_ent[j + 1] = v;
+        }
+        for (int o = o0; o < o1; ++o) {             // D(x - X_k) of each entry, kept with it
+            const int en = B.csr_ent[o], k = en / SS, r = en % SS;
+            cw[o] = wts[k * 8 + (r % Sx)] * wts[k * 8 + 4 + (r / Sx)];
         }
     }
     __syncthreads();
@@ -544,13 +705,13 @@ __device__ __forceinline__ int slot_of(const BodyDev& B, int k, int a, int b, in
 }
 
 template <class S>
-__global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
+__global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
     using R = typename Traits<S>::R;
     const BodyRef ref = L.refs[blockIdx.x];
     const CaseDev& C = *ref.c;
     BodyDev& B = *ref.b;
-    __shared__ int shi[2 * kThreads + 4];
-    __shared__ double shd[kThreads];
+    __shared__ int shi[2 * kIbThreads + 4];
+    __shared__ double shd[3 * kIbThreads];
     const int tid = threadIdx.x;
     if (B.nfp < 0) return;
     const int n = B.n, Sx = B.S, scheme = B.scheme;
@@ -564,22 +725,20 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
     R* fp = static_cast<R*>(B.fpdata);
     R* patch = static_cast<R*>(B.patch);
     R* mk = static_cast<R*>(B.mk);
+    const R* cw = static_cast<const R*>(B.csr_w);
     const R ds = R(B.ds);
 
     // MDF relaxation 1/||A||_inf (Sec. 2.5.2): sum_m A_lm = ds sum_x D_l(x) W(x),
     // W(x) = sum_m D_m(x); computed once on the first step.
     if (scheme == SCH_MDF && !B.st.omega_valid) {
-        for (int q = tid; q < nfp; q += kThreads) {
+        for (int q = tid; q < nfp; q += kIbThreads) {
             R w = R(0);
-            for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-                const int en = B.csr_ent[o], k = en / (Sx * Sx), r = en % (Sx * Sx);
-                w += wts[k * 8 + (r % Sx)] * wts[k * 8 + 4 + (r / Sx)];
-            }
+            for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) w += cw[o];
             patch[(size_t)q * 9] = w;
         }
         __syncthreads();
         double best = 0.0;
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             double row = 0.0;
             for (int b = 0; b < Sx; ++b)
                 for (int a = 0; a < Sx; ++a)
@@ -598,7 +757,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
 
     // DFC lambda_k of Eq. 17; W_total sums the markers of every DFC body of the case.
     if (scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
-        for (int q = tid; q < nfp; q += kThreads) {
+        for (int q = tid; q < nfp; q += kIbThreads) {
             const int node = B.fp_node[q];
             const int x = bx0 + node % bw, y = by0 + node / bw;
             R w = R(0);
@@ -606,10 +765,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
                 const BodyDev& O = C.bodies[ob];
                 if (O.scheme != SCH_DFC) continue;
                 if (ob == ref.index) {
-                    for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-                        const int en = B.csr_ent[o], k = en / (Sx * Sx), r = en % (Sx * Sx);
-                        w += wts[k * 8 + (r % Sx)] * wts[k * 8 + 4 + (r / Sx)];
-                    }
+                    for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) w += cw[o];
                 } else {
                     for (int k = 0; k < O.n; ++k) {
                         const double dx = (double)x - O.X[k], dy = (double)y - O.Y[k];
@@ -621,7 +777,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
             patch[(size_t)q * 9] = w;
         }
         __syncthreads();
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             R ws = R(0);
             for (int b = 0; b < Sx; ++b)
                 for (int a = 0; a < Sx; ++a)
@@ -636,7 +792,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
 
     // gather the post-streaming state at every footprint node
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
-    for (int q = tid; q < nfp; q += kThreads) {
+    for (int q = tid; q < nfp; q += kIbThreads) {
         const int node = B.fp_node[q];
         const int x = bx0 + node % bw, y = by0 + node / bw;
         R s[9];
@@ -665,7 +821,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
 
     if (scheme == SCH_DF) {
         // Eq. 7 on rho and u_raw, Eq. 11
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             R rk = R(0), Ux = R(0), Uy = R(0);
             for (int b = 0; b < Sx; ++b)
                 for (int a = 0; a < Sx; ++a) {
@@ -685,7 +841,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
         // Eqs. 12-14: at least N_min increments; tolerance and 1.5x guard are
         // tested on U^(n) before increment n; a diverging iterate is not applied.
         const R om = R(B.st.mdf_omega);
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             R rk = R(0);
             for (int b = 0; b < Sx; ++b)
                 for (int a = 0; a < Sx; ++a)
@@ -700,7 +856,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
         bool guard = false, tol_met = false;
         for (int it = 1; it <= B.mdf_nmax; ++it) {
             double e = 0.0;
-            for (int k = tid; k < n; k += kThreads) {
+            for (int k = tid; k < n; k += kIbThreads) {
                 R Ux = R(0), Uy = R(0);
                 for (int b = 0; b < Sx; ++b)
                     for (int a = 0; a < Sx; ++a) {
@@ -717,11 +873,11 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
             r = block_max(e, shd);
             if (applied >= B.mdf_nmin && r < B.mdf_tol) { tol_met = true; break; }
             if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
-            for (int q = tid; q < nfp; q += kThreads) {
+            for (int q = tid; q < nfp; q += kIbThreads) {
                 R sx = R(0), sy = R(0);
                 for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-                    const int en = B.csr_ent[o], k = en / (Sx * Sx), rr = en % (Sx * Sx);
-                    const R D = wts[k * 8 + (rr % Sx)] * wts[k * 8 + 4 + (rr / Sx)];
+                    const int k = B.csr_ent[o] / (Sx * Sx);
+                    const R D = cw[o];
                     sx += mk[k * 16 + 5] * D * ds;
                     sy += mk[k * 16 + 6] * D * ds;
                 }
@@ -729,7 +885,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
                 g[3] += om / (R(2) * g[0]) * sx;   // Eq. 14 with the node density
                 g[4] += om / (R(2) * g[0]) * sy;
             }
-            for (int k = tid; k < n; k += kThreads) {
+            for (int k = tid; k < n; k += kIbThreads) {
                 mk[k * 16 + 3] += om * mk[k * 16 + 5];
                 mk[k * 16 + 4] += om * mk[k * 16 + 6];
             }
@@ -737,7 +893,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
             rprev = r;
             ++applied;
         }
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             mk[k * 16 + 0] = mk[k * 16 + 3];
             mk[k * 16 + 1] = mk[k * 16 + 4];
             B.Fx[k] = (double)mk[k * 16 + 3];
@@ -754,7 +910,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
     } else {
         // DFC, Eqs. 15, 16, 18, 20 on shifted populations: the w_i parts of
         // f*_opp - f*_i cancel, leaving s*_opp - s*_i + 6 w_i e_i.U_d (rho_f = 1).
-        for (int k = tid; k < n; k += kThreads) {
+        for (int k = tid; k < n; k += kIbThreads) {
             R st[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) st[i] = R(0);
@@ -784,13 +940,13 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
     __syncthreads();
 
     // spread (Eq. 8 / Eq. 19) as a gather over each node's marker list in ascending order
-    for (int q = tid; q < nfp; q += kThreads) {
+    for (int q = tid; q < nfp; q += kIbThreads) {
         R p[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) p[i] = R(0);
         for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-            const int en = B.csr_ent[o], k = en / (Sx * Sx), rr = en % (Sx * Sx);
-            const R D = wts[k * 8 + (rr % Sx)] * wts[k * 8 + 4 + (rr / Sx)];
+            const int k = B.csr_ent[o] / (Sx * Sx);
+            const R D = cw[o];
             if (scheme == SCH_DFC) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) p[i] += mk[k * 16 + 2 + i] * D * ds;
@@ -806,7 +962,7 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
 
     // force and torque on the body (Sec. 2.7), FP64, fixed-order tree
     double gxs = 0.0, gys = 0.0, ts = 0.0;
-    for (int k = tid; k < n; k += kThreads) {
+    for (int k = tid; k < n; k += kIbThreads) {
         double gx, gy;
         if (scheme == SCH_DFC) { gx = B.Fx[k]; gy = B.Fy[k]; }
         else { gx = -B.Fx[k] * B.ds; gy = -B.Fy[k] * B.ds; }
@@ -815,8 +971,9 @@ __global__ void __launch_bounds__(kThreads) ib_kernel(IbLaunch L) {
         gys += gy;
         ts += rx * gy - ry * gx;
     }
-    const double Fhx = block_sum(gxs, shd), Fhy = block_sum(gys, shd), Th = block_sum(ts, shd);
+    block_sum3(gxs, gys, ts, shd);
     if (tid == 0) {
+        const double Fhx = gxs, Fhy = gys, Th = ts;
         B.st.Fhx = Fhx;
         B.st.Fhy = Fhy;
         B.st.Th = Th;
@@ -991,7 +1148,13 @@ template <class S, int KIND>
 static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
     if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1>), grid, kThreads, st, L, jobs);
     else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2>), grid, kThreads, st, L, jobs);
-    else IBLBM_LAUNCH((sc_kernel<S, KIND>), grid, kThreads, st, L, jobs);
+    else if (variant == SC_BULK) {
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);
+        if (attr != cudaSuccess) return attr;
+        IBLBM_LAUNCH_SMEM((sc_kernel_bulk<S, KIND>), grid, kThreads, BulkGeom<S>::SMEM, st, L, jobs);
+    } else IBLBM_LAUNCH((sc_kernel<S, KIND>), grid, kThreads, st, L, jobs);
     return cudaGetLastError();
 }
 
@@ -1024,7 +1187,11 @@ static int sc_occ_k(int variant) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1>, kThreads, 0);
     else if (variant == SC_SCALAR2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2>, kThreads, 0);
-    else
+    else if (variant == SC_BULK) {
+        const void* fn = reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, BulkGeom<S>::SMEM);
+    } else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<S, KIND>, kThreads, 0);
     return nb;
 }
@@ -1052,15 +1219,22 @@ int sc_blocks_per_sm(int storage, int collision, int variant) {
 
 int sc_segment(int storage, int variant) {
     const int V = storage == ST_F64 ? 2 : (storage == ST_F32 ? 4 : 8);
+    if (variant == SC_BULK)
+        return storage == ST_F64 ? BulkGeom<double>::TW : (storage == ST_F32 ? BulkGeom<float>::TW : BulkGeom<__half>::TW);
     return variant == SC_SCALAR ? 32 : (variant == SC_SCALAR2 ? 64 : 32 * V);
+}
+
+bool sc_variant_ok(int variant, const void* f0, const void* f1) {
+    // bulk copies need 16-byte aligned population buffers
+    return variant != SC_BULK || (((uintptr_t)f0 | (uintptr_t)f1) & 15u) == 0;
 }
 
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     if (L.nrefs <= 0) return cudaSuccess;
     switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(ib_kernel<double>, L.nrefs, kThreads, st, L); break;
-    case ST_F32: IBLBM_LAUNCH(ib_kernel<float>, L.nrefs, kThreads, st, L); break;
-    default: IBLBM_LAUNCH(ib_kernel<__half>, L.nrefs, kThreads, st, L); break;
+    case ST_F64: IBLBM_LAUNCH(ib_kernel<double>, L.nrefs, kIbThreads, st, L); break;
+    case ST_F32: IBLBM_LAUNCH(ib_kernel<float>, L.nrefs, kIbThreads, st, L); break;
+    default: IBLBM_LAUNCH(ib_kernel<__half>, L.nrefs, kIbThreads, st, L); break;
     }
     return cudaGetLastError();
 }

@@ -38,12 +38,14 @@ struct FinLaunch {
 
 // host-side launchers (kernels.cu)
 // Stream-collide variants: SC_VECTOR holds 16-byte vectors (2/4/8 nodes) per
-// lane; SC_SCALAR one node per lane; SC_SCALAR2 two nodes per lane (32 apart).
+// lane; SC_SCALAR one node per lane; SC_SCALAR2 two nodes per lane (32 apart);
+// SC_BULK stages each tile's source rows in shared memory with bulk async copies.
 // A job is one row segment of sc_segment(storage, variant) nodes.
-enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_SCALAR2 = 2, SC_VARIANTS = 3 };
+enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_SCALAR2 = 2, SC_BULK = 3, SC_VARIANTS = 4 };
 cudaError_t launch_stream_collide(int storage, int collision, int variant, const ScLaunch& L, long long jobs,
                                   int grid, cudaStream_t st);
 int sc_segment(int storage, int variant);
+bool sc_variant_ok(int variant, const void* f0, const void* f1);   // alignment a variant needs
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
 cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st);   // 0 prepare, 1 finish
 cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st);

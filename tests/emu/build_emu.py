@@ -23,7 +23,7 @@ def build(force=False):
     tmp = LIB + ".tmp%d" % os.getpid()
     # -Bsymbolic: the library's CUDA runtime calls bind to the emulation in this
     # library even when the real libcudart is already loaded in the process.
-    cmd = ["g++", "-std=c++17", "-O2", "-g", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-DIBLBM_EMULATE",
+    cmd = ["g++", "-std=c++20", "-O2", "-g", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-DIBLBM_EMULATE",
            "-Wno-attributes",
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", HERE, "-I", "/usr/local/cuda/include",
            "-x", "c++"] + SOURCES[:-1] + ["-x", "none", SOURCES[-1], "-o", tmp, "-lpthread"]

@@ -31,6 +31,8 @@ void syncthreads();
 uint64_t exchange(uint64_t v, int src_lane);   // warp exchange: value of lane src_lane
 int any(int pred);
 void launch(dim3 grid, dim3 block, std::function<void()> body, cudaStream_t st);
+unsigned char* dyn_smem();   // dynamic shared memory of the running block (256 KB)
+void yield();
 }  // namespace emu
 
 #define threadIdx (emu::tc.tid)
@@ -77,3 +79,6 @@ using std::min;
 
 #define IBLBM_LAUNCH(kern, grid, block, stream, ...) \
     emu::launch(dim3(grid), dim3(block), [=]() { kern(__VA_ARGS__); }, (stream))
+#define IBLBM_LAUNCH_SMEM(kern, grid, block, smem, stream, ...) \
+    emu::launch(dim3(grid), dim3(block), [=]() { kern(__VA_ARGS__); }, (stream))
+#define IBLBM_DYNAMIC_SMEM(name) unsigned char* name = emu::dyn_smem()

@@ -1,8 +1,9 @@
 // Host emulation of the CUDA runtime calls and execution model used by the
 // library (TEST INFRASTRUCTURE, see cuda_emu.h).  Blocks run one at a time on
-// a pool of host threads, one per CUDA thread; barriers abort on deadlock.
+// a pool of host threads, one per CUDA thread; a block that deadlocks aborts.
 #include "cuda_emu.h"
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -10,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <semaphore>
 #include <thread>
 #include <vector>
 
@@ -19,35 +21,34 @@ thread_local ThreadCoord tc;
 
 namespace {
 
+// Generation-counting barrier on futex-backed atomic waits.  A divergent
+// barrier leaves its block unfinished; run_block reports that after a timeout.
 struct Barrier {
-    std::mutex m;
-    std::condition_variable cv;
-    int n = 0, count = 0;
-    unsigned gen = 0;
-    void wait(const char* what) {
-        std::unique_lock<std::mutex> lk(m);
-        const unsigned g = gen;
-        if (++count == n) {
-            count = 0;
-            ++gen;
-            cv.notify_all();
+    std::atomic<int> count{0};
+    std::atomic<unsigned> gen{0};
+    int n = 0;
+    void wait(const char*) {
+        const unsigned g = gen.load(std::memory_order_acquire);
+        if (count.fetch_add(1, std::memory_order_acq_rel) + 1 == n) {
+            count.store(0, std::memory_order_relaxed);
+            gen.fetch_add(1, std::memory_order_release);
+            gen.notify_all();
             return;
         }
-        if (!cv.wait_for(lk, std::chrono::seconds(60), [&] { return gen != g; })) {
-            std::fprintf(stderr, "emu: %s barrier timed out (divergent barrier)\n", what);
-            std::abort();
-        }
+        while (gen.load(std::memory_order_acquire) == g) gen.wait(g, std::memory_order_acquire);
     }
 };
 
-constexpr int kMaxThreads = 256;
+constexpr int kMaxThreads = 512;
 
 struct Pool {
+    // Each worker waits on its own semaphore, so a launch wakes only the
+    // threads of its block, not the whole pool.
     std::vector<std::thread> workers;
+    std::vector<std::unique_ptr<std::binary_semaphore>> go;
     std::mutex m;
-    std::condition_variable cv_go, cv_done;
-    unsigned long long go_gen = 0;
-    int active = 0, remaining = 0;
+    std::condition_variable cv_done;
+    int remaining = 0;
     bool stop = false;
     std::function<void()> body;
     ThreadCoord base;
@@ -56,49 +57,40 @@ struct Pool {
     uint64_t warp_buf[kMaxThreads / 32][32];
 
     Pool() {
+        for (int i = 0; i < kMaxThreads; ++i) go.emplace_back(new std::binary_semaphore(0));
         for (int i = 0; i < kMaxThreads; ++i) workers.emplace_back([this, i] { run(i); });
     }
     ~Pool() {
-        {
-            std::lock_guard<std::mutex> lk(m);
-            stop = true;
-            ++go_gen;
-        }
-        cv_go.notify_all();
+        stop = true;
+        for (auto& g : go) g->release();
         for (auto& w : workers) w.join();
     }
     void run(int i) {
-        unsigned long long seen = 0;
         for (;;) {
-            std::function<void()> f;
-            {
-                std::unique_lock<std::mutex> lk(m);
-                cv_go.wait(lk, [&] { return stop || go_gen != seen; });
-                if (stop) return;
-                seen = go_gen;
-                if (i >= active) continue;
-                f = body;
-                tc = base;
-                tc.tid = make_uint3((unsigned)i, 0, 0);
-            }
-            f();
-            {
-                std::lock_guard<std::mutex> lk(m);
-                if (--remaining == 0) cv_done.notify_all();
-            }
+            go[i]->acquire();
+            if (stop) return;
+            tc = base;
+            tc.tid = make_uint3((unsigned)i, 0, 0);
+            body();
+            std::lock_guard<std::mutex> lk(m);
+            if (--remaining == 0) cv_done.notify_all();
         }
     }
     void run_block(const ThreadCoord& c, int nthreads, const std::function<void()>& f) {
-        std::unique_lock<std::mutex> lk(m);
         body = f;
         base = c;
-        active = nthreads;
-        remaining = nthreads;
         block_bar.n = nthreads;
         for (int w = 0; w < (nthreads + 31) / 32; ++w) warp_bar[w].n = std::min(32, nthreads - 32 * w);
-        ++go_gen;
-        cv_go.notify_all();
-        cv_done.wait(lk, [&] { return remaining == 0; });
+        {
+            std::lock_guard<std::mutex> lk(m);
+            remaining = nthreads;
+        }
+        for (int i = 0; i < nthreads; ++i) go[i]->release();   // release orders the writes above
+        std::unique_lock<std::mutex> lk(m);
+        if (!cv_done.wait_for(lk, std::chrono::seconds(120), [&] { return remaining == 0; })) {
+            std::fprintf(stderr, "emu: block did not finish (divergent barrier)\n");
+            std::abort();
+        }
     }
 };
 
@@ -165,6 +157,14 @@ void launch(dim3 grid, dim3 block, std::function<void()> body, cudaStream_t st) 
     run_now(grid, block, body);
 }
 
+unsigned char* dyn_smem() {
+    // blocks run one at a time, so one buffer serves every block's dynamic shared memory
+    static unsigned char* buf = static_cast<unsigned char*>(std::aligned_alloc(256, 256 * 1024));
+    return buf;
+}
+
+void yield() { std::this_thread::yield(); }
+
 }  // namespace emu
 
 // ---- runtime API --------------------------------------------------------------------------
@@ -213,6 +213,7 @@ cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(int* n, const
     *n = 1;
     return cudaSuccess;
 }
+cudaError_t cudaFuncSetAttribute(const void*, cudaFuncAttribute, int) { return cudaSuccess; }
 cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 cudaError_t cudaDeviceSynchronize(void) { return cudaSuccess; }
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "emu"))
 
 
-@pytest.fixture(scope="module", params=[1, 0, 2], ids=["scalar", "vector", "scalar2"])
+@pytest.fixture(scope="module", params=[1, 0, 2, 3], ids=["scalar", "vector", "scalar2", "bulk"])
 def L(request):
     """The emulated library with the stream-collide variant fixed (both are checked)."""
     import build_emu

@@ -18,7 +18,7 @@ import paper_2609_02298_b300 as L  # noqa: E402
 L.use_torch_allocator()
 
 
-@pytest.fixture(scope="module", autouse=True, params=[0, 1, 2], ids=["vector", "scalar", "scalar2"])
+@pytest.fixture(scope="module", autouse=True, params=[0, 1, 2, 3], ids=["vector", "scalar", "scalar2", "bulk"])
 def variant(request):
     """Every check runs with each stream-collide variant fixed in turn."""
     for st in (W.F64, W.F32, W.F16S):
