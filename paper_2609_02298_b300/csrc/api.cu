@@ -351,6 +351,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     B.csr_ent = (int*)c->alloc(4 * (size_t)nent);
     B.fill = (int*)c->alloc(4 * (size_t)nent);
     B.csr_w = c->alloc(rb * (size_t)nent);
+    B.mslot = (int*)c->alloc(4 * (size_t)nent);
     B.ij = (int*)c->alloc(8 * (size_t)n);
     B.wts = c->alloc(rb * 8 * (size_t)n);
     B.fpdata = c->alloc(rb * 9 * (size_t)nent);
@@ -358,7 +359,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     B.mk = c->alloc(rb * 16 * (size_t)n);
     B.hist = (double*)c->alloc(24 * (size_t)hist_cap);
     if (!B.X || !B.Y || !B.r0x || !B.r0y || !B.Udx || !B.Udy || !B.Fx || !B.Fy || !B.lam || !B.node_map ||
-        !B.fp_node || !B.csr_off || !B.csr_ent || !B.fill || !B.csr_w || !B.ij || !B.wts || !B.fpdata || !B.patch || !B.mk ||
+        !B.fp_node || !B.csr_off || !B.csr_ent || !B.fill || !B.csr_w || !B.mslot || !B.ij || !B.wts || !B.fpdata || !B.patch || !B.mk ||
         !B.hist)
         return IBLBM_ERR_OOM;
     std::vector<double> X(n), Y(n), rx(n), ry(n);
@@ -691,7 +692,7 @@ size_t iblbm_internal_estimate_bytes(const iblbm_lattice_desc* d, int n, double 
         const int S = kernel == K_HAT ? 2 : 4;
         const size_t nent = (size_t)n * S * S, rb = real_bytes(d->storage);
         const size_t hc = hist_cap > 0 ? (size_t)hist_cap : 65536;
-        b += 9 * rounded(8 * (size_t)n) + rounded(4 * (size_t)box_capacity(reach, S)) + 3 * rounded(4 * nent) +
+        b += 9 * rounded(8 * (size_t)n) + rounded(4 * (size_t)box_capacity(reach, S)) + 4 * rounded(4 * nent) +
              rounded(4 * (nent + 1)) + rounded(8 * (size_t)n) + rounded(rb * 8 * n) + 2 * rounded(rb * 9 * nent) +
              rounded(rb * nent) + rounded(rb * 16 * n) + rounded(24 * hc);
     }

@@ -29,6 +29,10 @@ __device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
+// Plain arrival (release semantics: the caller's earlier shared-memory reads are done).
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 // Contiguous copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
     asm volatile(
@@ -76,6 +80,7 @@ inline void bar_init(uint64_t* bar, unsigned count) {
 }
 inline void fence_bar_init() {}
 inline void bar_arrive_tx(uint64_t* bar, unsigned bytes) { emu_bar_update(bar, 1, (int)bytes); }
+inline void bar_arrive(uint64_t* bar) { emu_bar_update(bar, 1, 0); }
 inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
     std::memcpy(dst, src, bytes);
     emu_bar_update(bar, 0, -(int)bytes);

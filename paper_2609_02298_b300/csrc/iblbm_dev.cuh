@@ -86,6 +86,7 @@ struct BodyDev {
     int* csr_ent;                 // [nent] entry = k*S*S + b*S + a, sorted by k per slot
     int* fill;                    // [nent]
     void* csr_w;                  // [nent] kernel weight D of each CSR entry (R)
+    int* mslot;                   // [nent] footprint slot of stencil node r of marker k (k S^2 + r)
     int* ij;                      // [2n] stencil origins
     void* wts;                    // [n][8] kernel weights phi_x[4], phi_y[4] (R)
     void* fpdata;                 // [nent][9] gathered slot data (R)

@@ -377,26 +377,35 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
 // ------------------------------------------------------------------------------------------
 // Stream-collide with bulk-staged sources (SC_BULK).  A job is a tile of TW nodes
 // of one row; its nine source rows (row y - e_iy of plane i, columns x0 - H ..
-// x0 + TW + H, H = one 16-byte halo) arrive in shared memory by cp.async.bulk
-// on an mbarrier, NST tiles ahead of the one being computed.  The copy engine
-// keeps ~NST x 9 rows per CTA in flight without holding registers, which is what
-// a pull-streaming sweep needs to cover HBM latency; the compute side reads each
-// population with one shared load at a constant offset.  Lattice-edge nodes and
-// the first and last rows take the general path (global pulls with the domain
-// conditions), as in the other variants.
+// x0 + TW + H, H = one 16-byte halo) arrive in shared memory by cp.async.bulk.
+// Warp-specialised pipeline over NST stages: one producer warp fills stage k and
+// signals full[k] through the transaction count; eight consumer warps compute the
+// tile from shared memory (one load per population at a constant offset) and
+// release the stage on empty[k].  The copy engine keeps several tiles per CTA in
+// flight without holding registers, which a pull-streaming sweep needs to cover
+// HBM latency.  Lattice-edge nodes and the first and last rows take the general
+// path (global pulls with the domain conditions), as in the other variants.
 template <class S> struct BulkCfg;
-template <> struct BulkCfg<float> { static constexpr int NPT = 2, NST = 4, MINB = 2; };
-template <> struct BulkCfg<__half> { static constexpr int NPT = 2, NST = 6, MINB = 2; };
-template <> struct BulkCfg<double> { static constexpr int NPT = 1, NST = 4, MINB = 2; };
+template <> struct BulkCfg<float> { static constexpr int NPT = 2, NST = 6, MINB = 2; };
+template <> struct BulkCfg<__half> { static constexpr int NPT = 2, NST = 8, MINB = 2; };
+template <> struct BulkCfg<double> { static constexpr int NPT = 1, NST = 6, MINB = 2; };
+constexpr int kBulkConsumers = kThreads;          // eight consumer warps
+constexpr int kBulkThreads = kThreads + 32;       // plus one producer warp
+struct BulkDesc {                                 // tile of a stage, written by the producer
+    int c, y, x0, flags;
+};
+enum : int { BULK_STAGED = 1, BULK_INTERIOR = 2, BULK_IB = 4 };
 template <class S> struct BulkGeom {
+    static constexpr int NST = BulkCfg<S>::NST;
     static constexpr int H = 16 / (int)sizeof(S);
-    static constexpr int TW = kThreads * BulkCfg<S>::NPT;
-    static constexpr int RS = TW + 2 * H;                          // elements per staged row
-    static constexpr int STAGE = 9 * RS * (int)sizeof(S);          // bytes per stage
-    static constexpr int BAR = 128;                                // barriers + abort flag; keeps stages aligned
-    static_assert(8 * BulkCfg<S>::NST + 4 <= BAR, "barrier block too small");
-    static constexpr int SMEM = BAR + BulkCfg<S>::NST * STAGE;
+    static constexpr int TW = kBulkConsumers * BulkCfg<S>::NPT;
+    static constexpr int RS = TW + 2 * H;                           // elements per staged row
+    static constexpr int STAGE = 9 * RS * (int)sizeof(S);           // bytes per stage
+    static constexpr int HDR = 16 * NST + 16 * NST + 16;            // full + empty barriers, descriptors, flag
+    static constexpr int BAR = (HDR + 127) / 128 * 128;             // header, keeps stages aligned
+    static constexpr int SMEM = BAR + NST * STAGE;
     static_assert((RS * (int)sizeof(S)) % 16 == 0, "staged rows must stay 16-byte aligned");
+    static_assert(SMEM <= 113 * 1024, "two CTAs per SM must fit");
 };
 constexpr long kBulkSpinLimit = 1L << 22;   // polls of an mbarrier before the kernel gives up
 
@@ -420,107 +429,164 @@ __device__ __forceinline__ int bulk_locate(const ScLaunch& L, long long job, int
     return lo;
 }
 
-// Issued by one thread: the nine source rows of tile `job` into `st`, completing on `bar`.
+// Producer side (one thread): describe tile `job` and start its nine row copies.
 template <class S>
-__device__ __forceinline__ void bulk_issue(const ScLaunch& L, long long job, S* st, uint64_t* bar) {
+__device__ __forceinline__ void bulk_issue(const ScLaunch& L, long long job, S* st, uint64_t* full, BulkDesc* desc) {
     using G = BulkGeom<S>;
     int y, x0;
-    const CaseDev& C = *L.cases[bulk_locate<G::TW>(L, job, y, x0)];
-    if (y == 0 || y == C.ny - 1) {   // general path: nothing to stage
-        bar_arrive_tx(bar, 0);
+    const int c = bulk_locate<G::TW>(L, job, y, x0);
+    const CaseDev& C = *L.cases[c];
+    const bool staged = y > 0 && y < C.ny - 1;
+    const bool interior = staged && x0 > 0 && x0 + G::TW < C.nx - 1;
+    const bool ib = C.nbodies > 0 && row_has_ib(C, y, x0, x0 + G::TW);
+    desc->c = c;
+    desc->y = y;
+    desc->x0 = x0;
+    desc->flags = (staged ? BULK_STAGED : 0) | (interior ? BULK_INTERIOR : 0) | (ib ? BULK_IB : 0);
+    if (!staged) {   // general path: nothing to copy
+        bar_arrive_tx(full, 0);
         return;
     }
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
     const int xs = max(x0 - G::H, 0), xe = min(x0 + G::TW + G::H, C.pitch);
     const unsigned bytes = (unsigned)((xe - xs) * (int)sizeof(S));
-    bar_arrive_tx(bar, 9u * bytes);
+    bar_arrive_tx(full, 9u * bytes);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         bulk_g2s(st + i * G::RS + (xs - x0 + G::H), src + i * C.plane + (long long)(y - ey(i)) * C.pitch + xs, bytes,
-                 bar);
+                 full);
+}
+
+// One node of a staged tile: pull from the stage, IB patch, collision, store.
+template <class S, int KIND, bool FORCED>
+__device__ __forceinline__ bool bulk_node(const ScCase<S>& K, const S* b, S* d, int x, int y, bool ib) {
+    using R = typename Traits<S>::R;
+    R s[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s[i] = lds1(b + i * BulkGeom<S>::RS - ex(i));
+    R rho;
+    if (FORCED) {
+        R Fx = K.gfx, Fy = K.gfy;
+        if (ib) add_ib<R>(*K.C, x, y, s, Fx, Fy);
+        rho = collide<R, KIND>(K.P, s, Fx, Fy);
+    } else {
+        rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+    return bad_density(rho);
 }
 
 template <class S, int KIND>
-__global__ void __launch_bounds__(kThreads, (BulkCfg<S>::MINB)) sc_kernel_bulk(ScLaunch L, long long jobs) {
+__global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bulk(ScLaunch L, long long jobs) {
     using R = typename Traits<S>::R;
     using G = BulkGeom<S>;
-    constexpr int NST = BulkCfg<S>::NST, NPT = BulkCfg<S>::NPT, TW = G::TW, RS = G::RS, H = G::H;
+    constexpr int NST = G::NST, NPT = BulkCfg<S>::NPT, TW = G::TW, RS = G::RS, H = G::H;
     IBLBM_DYNAMIC_SMEM(smem);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    volatile int& abort_at = *reinterpret_cast<int*>(smem + 8 * NST);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + NST;
+    BulkDesc* desc = reinterpret_cast<BulkDesc*>(smem + 16 * NST);
+    volatile int& abort_flag = *reinterpret_cast<int*>(smem + 32 * NST);
     S* stages = reinterpret_cast<S*>(smem + G::BAR);
     const int tid = threadIdx.x;
     const long long j0 = jobs * blockIdx.x / gridDim.x, j1 = jobs * (blockIdx.x + 1) / gridDim.x;
     if (tid == 0) {
-        for (int k = 0; k < NST; ++k) bar_init(&bars[k], 1);
+        for (int k = 0; k < NST; ++k) {
+            bar_init(&full[k], 1);
+            bar_init(&empty[k], kBulkConsumers / 32);
+        }
         fence_bar_init();
-        abort_at = -1;
+        abort_flag = 0;
     }
     __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < NST && j0 + k < j1; ++k) bulk_issue<S>(L, j0 + k, stages + k * 9 * RS, &bars[k]);
 
-    ScCase<S> K;
-    int cur = -1;
-    long long stop = -1;
-    for (long long job = j0; job < j1; ++job) {
-        const int k = (int)((job - j0) % NST);
-        const unsigned parity = (unsigned)(((job - j0) / NST) & 1);
-        int y, x0;
-        const int c = bulk_locate<TW>(L, job, y, x0);
-        if (c != cur) {
-            K.load(L.cases[c]);
-            cur = c;
-        }
-        const CaseDev& C = *K.C;
-        if (!bar_wait(&bars[k], parity, kBulkSpinLimit)) abort_at = k;
-        __syncthreads();
-        if (abort_at >= 0) {
-            stop = job;
-            break;
-        }
-        const S* st = stages + k * 9 * RS;
-        const bool ib = K.nbodies > 0 && row_has_ib(C, y, x0, x0 + TW);
-        const bool forced = ib || K.has_force;
-        const bool edge_row = y == 0 || y == K.ny - 1;
-        bool unstable = false;
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            const int x = x0 + tid + kThreads * j;
-            if (x < K.nx) {
-                R s[9];
-                if (edge_row || x == 0 || x == K.nx - 1) {
-                    post_stream_node<S, R>(C, K.src, x, y, s);
-                } else {
-                    const S* b = st + tid + kThreads * j + H;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) s[i] = lds1(b + i * RS - ex(i));
+    if (tid >= kBulkConsumers) {
+        // producer warp: lane 0 streams the CTA's tiles through the stages
+        if (tid == kBulkConsumers) {
+            long long job = j0;
+            for (; job < j1 && !abort_flag; ++job) {
+                const long long t = job - j0;
+                const int k = (int)(t % NST);
+                if (t >= NST && !bar_wait(&empty[k], (unsigned)(((t / NST) - 1) & 1), kBulkSpinLimit)) {
+                    abort_flag = 1;
+                    break;
                 }
-                R rho;
-                if (forced) {
-                    R Fx = K.gfx, Fy = K.gfy;
-                    if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-                    rho = collide<R, KIND>(K.P, s, Fx, Fy);
-                } else {
-                    rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
-                }
-                unstable |= bad_density(rho);
-                S* d = K.dst + ((long long)y * K.pitch + x);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+                bulk_issue<S>(L, job, stages + k * 9 * RS, &full[k], &desc[k]);
+            }
+            if (abort_flag) {
+                // report, then wait (bounded) for copies that may still be landing
+                int yy, xx;
+                atomicOr(const_cast<unsigned*>(&L.cases[bulk_locate<TW>(L, j0, yy, xx)]->status), STAT_TIMEOUT);
+                for (long long jj = job - 1; jj >= j0 && jj >= job - NST; --jj)
+                    bar_wait(&full[(jj - j0) % NST], (unsigned)(((jj - j0) / NST) & 1), kBulkSpinLimit);
             }
         }
-        if (__any_sync(0xffffffffu, unstable) && (tid & 31) == 0)
-            atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
-        __syncthreads();   // stage k fully read before it is refilled
-        if (tid == 0 && job + NST < j1) bulk_issue<S>(L, job + NST, stages + k * 9 * RS, &bars[k]);
+        return;
     }
-    if (stop >= 0 && tid == 0) {
-        // a copy never completed: report it, then wait (bounded) for the stages still in flight
-        int yy, xx;
-        atomicOr(const_cast<unsigned*>(&L.cases[bulk_locate<TW>(L, stop, yy, xx)]->status), STAT_TIMEOUT);
-        for (long long jj = stop; jj < j1 && jj < stop + NST; ++jj)
-            bar_wait(&bars[(jj - j0) % NST], (unsigned)(((jj - j0) / NST) & 1), kBulkSpinLimit);
+
+    // consumer warps
+    const int lane = tid & 31;
+    ScCase<S> K;
+    int cur = -1;
+    for (long long job = j0; job < j1; ++job) {
+        const long long t = job - j0;
+        const int k = (int)(t % NST);
+        if (!bar_wait(&full[k], (unsigned)((t / NST) & 1), kBulkSpinLimit) || abort_flag) {
+            abort_flag = 1;
+            break;
+        }
+        const BulkDesc dk = desc[k];
+        if (dk.c != cur) {
+            K.load(L.cases[dk.c]);
+            cur = dk.c;
+        }
+        const int y = dk.y, x0 = dk.x0;
+        const bool ib = (dk.flags & BULK_IB) != 0;
+        const bool forced = ib || K.has_force;
+        const S* st = stages + k * 9 * RS + tid + H;
+        S* d = K.dst + ((long long)y * K.pitch + x0 + tid);
+        bool unstable = false;
+        if (dk.flags & BULK_INTERIOR) {
+            if (forced) {
+#pragma unroll
+                for (int j = 0; j < NPT; ++j)
+                    unstable |= bulk_node<S, KIND, true>(K, st + kBulkConsumers * j, d + kBulkConsumers * j,
+                                                         x0 + tid + kBulkConsumers * j, y, ib);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NPT; ++j)
+                    unstable |= bulk_node<S, KIND, false>(K, st + kBulkConsumers * j, d + kBulkConsumers * j,
+                                                          x0 + tid + kBulkConsumers * j, y, false);
+            }
+        } else {
+            const CaseDev& C = *K.C;
+            const bool staged = (dk.flags & BULK_STAGED) != 0;
+#pragma unroll 1
+            for (int j = 0; j < NPT; ++j) {
+                const int x = x0 + tid + kBulkConsumers * j;
+                if (x >= K.nx) continue;
+                if (staged && x > 0 && x < K.nx - 1) {
+                    unstable |= forced ? bulk_node<S, KIND, true>(K, st + kBulkConsumers * j,
+                                                                  d + kBulkConsumers * j, x, y, ib)
+                                       : bulk_node<S, KIND, false>(K, st + kBulkConsumers * j,
+                                                                   d + kBulkConsumers * j, x, y, false);
+                } else {
+                    R s[9];
+                    post_stream_node<S, R>(C, K.src, x, y, s);
+                    R Fx = K.gfx, Fy = K.gfy;
+                    if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+                    const R rho = collide<R, KIND>(K.P, s, Fx, Fy);
+                    unstable |= bad_density(rho);
+                    S* dd = d + kBulkConsumers * j;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) st1(dd + i * K.plane, s[i]);
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, unstable) && lane == 0)
+            atomicOr(const_cast<unsigned*>(&K.C->status), STAT_UNSTABLE);
+        __syncwarp();
+        if (lane == 0) bar_arrive(&empty[k]);   // this warp is done with stage k
     }
 }
 
@@ -675,6 +741,7 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
         const int node = (B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0);
         const int sl = B.node_map[node];
+        B.mslot[en] = sl;
         B.csr_ent[B.csr_off[sl] + atomicAdd(&B.fill[sl], 1)] = en;
     }
     __syncthreads();
@@ -699,28 +766,36 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
     return true;
 }
 
-// Slot of stencil node (a, b) of marker k.
-__device__ __forceinline__ int slot_of(const BodyDev& B, int k, int a, int b, int bx0, int by0, int bw) {
-    return B.node_map[(B.ij[2 * k + 1] + b - by0) * bw + (B.ij[2 * k] + a - bx0)];
+// Stencil of marker k: footprint slots and weights D(x - X_k) of its SX x SX nodes,
+// ordered b-major (ascending j, then i).  Fixed-width loops let every load of a
+// marker's stencil be in flight at once.
+template <int SX, class R>
+__device__ __forceinline__ void marker_stencil(const BodyDev& B, const R* wts, int k, int (&sl)[SX * SX],
+                                               R (&D)[SX * SX]) {
+#pragma unroll
+    for (int r = 0; r < SX * SX; ++r) {
+        sl[r] = B.mslot[k * SX * SX + r];
+        D[r] = wts[k * 8 + (r % SX)] * wts[k * 8 + 4 + (r / SX)];
+    }
 }
 
-template <class S>
-__global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
+constexpr int kSpreadChunk = 8;   // CSR entries whose loads are issued together
+
+// Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
+template <class S, int SX>
+__device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd) {
     using R = typename Traits<S>::R;
-    const BodyRef ref = L.refs[blockIdx.x];
+    constexpr int SS = SX * SX;
     const CaseDev& C = *ref.c;
     BodyDev& B = *ref.b;
-    __shared__ int shi[2 * kIbThreads + 4];
-    __shared__ double shd[3 * kIbThreads];
     const int tid = threadIdx.x;
-    if (B.nfp < 0) return;
-    const int n = B.n, Sx = B.S, scheme = B.scheme;
+    const int n = B.n, scheme = B.scheme;
     if (!B.cache_valid) {
         if (!build_footprint<R>(C, B, shi)) return;
         if (tid == 0) B.cache_valid = (B.motion == MOT_FIXED) ? 1 : 0;
     }
     __syncthreads();
-    const int bx0 = B.bx0, by0 = B.by0, bw = B.bw, nfp = B.nfp;
+    const int bx0 = B.bx0, bw = B.bw, nfp = B.nfp;
     const R* wts = static_cast<const R*>(B.wts);
     R* fp = static_cast<R*>(B.fpdata);
     R* patch = static_cast<R*>(B.patch);
@@ -739,11 +814,12 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         __syncthreads();
         double best = 0.0;
         for (int k = tid; k < n; k += kIbThreads) {
+            int sl[SS];
+            R D[SS];
+            marker_stencil<SX, R>(B, wts, k, sl, D);
             double row = 0.0;
-            for (int b = 0; b < Sx; ++b)
-                for (int a = 0; a < Sx; ++a)
-                    row += (double)(wts[k * 8 + a] * wts[k * 8 + 4 + b]) *
-                           (double)patch[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9];
+#pragma unroll
+            for (int r = 0; r < SS; ++r) row += (double)D[r] * (double)patch[(size_t)sl[r] * 9];
             best = fmax(best, row * B.ds);
         }
         best = block_max(best, shd);
@@ -759,7 +835,7 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
     if (scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
         for (int q = tid; q < nfp; q += kIbThreads) {
             const int node = B.fp_node[q];
-            const int x = bx0 + node % bw, y = by0 + node / bw;
+            const int x = bx0 + node % bw, y = B.by0 + node / bw;
             R w = R(0);
             for (int ob = 0; ob < C.nbodies; ++ob) {
                 const BodyDev& O = C.bodies[ob];
@@ -778,13 +854,13 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         }
         __syncthreads();
         for (int k = tid; k < n; k += kIbThreads) {
+            int sl[SS];
+            R D[SS];
+            marker_stencil<SX, R>(B, wts, k, sl, D);
             R ws = R(0);
-            for (int b = 0; b < Sx; ++b)
-                for (int a = 0; a < Sx; ++a)
-                    ws += patch[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9] *
-                          (wts[k * 8 + a] * wts[k * 8 + 4 + b]);
-            const double lam = 1.0 / (2.0 * 1.0 * B.ds * (double)ws);
-            B.lam[k] = lam;
+#pragma unroll
+            for (int r = 0; r < SS; ++r) ws += patch[(size_t)sl[r] * 9] * D[r];
+            B.lam[k] = 1.0 / (2.0 * 1.0 * B.ds * (double)ws);
         }
         __syncthreads();
         if (tid == 0) B.lam_valid = 1;
@@ -794,7 +870,7 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
     for (int q = tid; q < nfp; q += kIbThreads) {
         const int node = B.fp_node[q];
-        const int x = bx0 + node % bw, y = by0 + node / bw;
+        const int x = bx0 + node % bw, y = B.by0 + node / bw;
         R s[9];
         post_stream_node<S, R>(C, src, x, y, s);
         R* o = fp + (size_t)q * 9;
@@ -822,15 +898,17 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
     if (scheme == SCH_DF) {
         // Eq. 7 on rho and u_raw, Eq. 11
         for (int k = tid; k < n; k += kIbThreads) {
+            int sl[SS];
+            R D[SS];
+            marker_stencil<SX, R>(B, wts, k, sl, D);
             R rk = R(0), Ux = R(0), Uy = R(0);
-            for (int b = 0; b < Sx; ++b)
-                for (int a = 0; a < Sx; ++a) {
-                    const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
-                    const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
-                    rk += g[0] * D;
-                    Ux += g[1] * D;
-                    Uy += g[2] * D;
-                }
+#pragma unroll
+            for (int r = 0; r < SS; ++r) {
+                const R* g = fp + (size_t)sl[r] * 9;
+                rk += g[0] * D[r];
+                Ux += g[1] * D[r];
+                Uy += g[2] * D[r];
+            }
             const R Fx = R(2) * rk * (R(B.Udx[k]) - Ux), Fy = R(2) * rk * (R(B.Udy[k]) - Uy);
             mk[k * 16 + 0] = Fx;
             mk[k * 16 + 1] = Fy;
@@ -842,10 +920,12 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         // tested on U^(n) before increment n; a diverging iterate is not applied.
         const R om = R(B.st.mdf_omega);
         for (int k = tid; k < n; k += kIbThreads) {
+            int sl[SS];
+            R D[SS];
+            marker_stencil<SX, R>(B, wts, k, sl, D);
             R rk = R(0);
-            for (int b = 0; b < Sx; ++b)
-                for (int a = 0; a < Sx; ++a)
-                    rk += fp[(size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9] * (wts[k * 8 + a] * wts[k * 8 + 4 + b]);
+#pragma unroll
+            for (int r = 0; r < SS; ++r) rk += fp[(size_t)sl[r] * 9] * D[r];
             mk[k * 16 + 2] = rk;
             mk[k * 16 + 3] = R(0);
             mk[k * 16 + 4] = R(0);
@@ -857,14 +937,16 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         for (int it = 1; it <= B.mdf_nmax; ++it) {
             double e = 0.0;
             for (int k = tid; k < n; k += kIbThreads) {
+                int sl[SS];
+                R D[SS];
+                marker_stencil<SX, R>(B, wts, k, sl, D);
                 R Ux = R(0), Uy = R(0);
-                for (int b = 0; b < Sx; ++b)
-                    for (int a = 0; a < Sx; ++a) {
-                        const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
-                        const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
-                        Ux += g[3] * D;
-                        Uy += g[4] * D;
-                    }
+#pragma unroll
+                for (int q = 0; q < SS; ++q) {
+                    const R* g = fp + (size_t)sl[q] * 9;
+                    Ux += g[3] * D[q];
+                    Uy += g[4] * D[q];
+                }
                 const double dx = B.Udx[k] - (double)Ux, dy = B.Udy[k] - (double)Uy;
                 e = fmax(e, sqrt(dx * dx + dy * dy));
                 mk[k * 16 + 5] = R(2) * mk[k * 16 + 2] * (R(B.Udx[k]) - Ux);   // Eq. 13
@@ -875,11 +957,19 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
             if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
             for (int q = tid; q < nfp; q += kIbThreads) {
                 R sx = R(0), sy = R(0);
-                for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-                    const int k = B.csr_ent[o] / (Sx * Sx);
-                    const R D = cw[o];
-                    sx += mk[k * 16 + 5] * D * ds;
-                    sy += mk[k * 16 + 6] * D * ds;
+                const int o1 = B.csr_off[q + 1];
+                for (int o = B.csr_off[q]; o < o1; o += kSpreadChunk) {
+                    int kk[kSpreadChunk];
+                    R dd[kSpreadChunk];
+#pragma unroll
+                    for (int u = 0; u < kSpreadChunk; ++u)
+                        if (o + u < o1) { kk[u] = B.csr_ent[o + u] / SS; dd[u] = cw[o + u]; }
+#pragma unroll
+                    for (int u = 0; u < kSpreadChunk; ++u)
+                        if (o + u < o1) {
+                            sx += mk[kk[u] * 16 + 5] * dd[u] * ds;
+                            sy += mk[kk[u] * 16 + 6] * dd[u] * ds;
+                        }
                 }
                 R* g = fp + (size_t)q * 9;
                 g[3] += om / (R(2) * g[0]) * sx;   // Eq. 14 with the node density
@@ -911,16 +1001,18 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         // DFC, Eqs. 15, 16, 18, 20 on shifted populations: the w_i parts of
         // f*_opp - f*_i cancel, leaving s*_opp - s*_i + 6 w_i e_i.U_d (rho_f = 1).
         for (int k = tid; k < n; k += kIbThreads) {
+            int sl[SS];
+            R D[SS];
+            marker_stencil<SX, R>(B, wts, k, sl, D);
             R st[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) st[i] = R(0);
-            for (int b = 0; b < Sx; ++b)
-                for (int a = 0; a < Sx; ++a) {
-                    const R D = wts[k * 8 + a] * wts[k * 8 + 4 + b];
-                    const R* g = fp + (size_t)slot_of(B, k, a, b, bx0, by0, bw) * 9;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) st[i] += g[i] * D;
-                }
+            for (int r = 0; r < SS; ++r) {
+                const R* g = fp + (size_t)sl[r] * 9;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) st[i] += g[i] * D[r];
+            }
             const R lam = R(B.lam[k]);
             const R udx = R(B.Udx[k]), udy = R(B.Udy[k]);
             R fsx = R(0), fsy = R(0);
@@ -944,15 +1036,27 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         R p[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) p[i] = R(0);
-        for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
-            const int k = B.csr_ent[o] / (Sx * Sx);
-            const R D = cw[o];
+        const int o1 = B.csr_off[q + 1];
+        for (int o = B.csr_off[q]; o < o1; o += kSpreadChunk) {
+            int kk[kSpreadChunk];
+            R dd[kSpreadChunk];
+#pragma unroll
+            for (int u = 0; u < kSpreadChunk; ++u)
+                if (o + u < o1) { kk[u] = B.csr_ent[o + u] / SS; dd[u] = cw[o + u]; }
             if (scheme == SCH_DFC) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) p[i] += mk[k * 16 + 2 + i] * D * ds;
+                for (int u = 0; u < kSpreadChunk; ++u)
+                    if (o + u < o1) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) p[i] += mk[kk[u] * 16 + 2 + i] * dd[u] * ds;
+                    }
             } else {
-                p[0] += mk[k * 16 + 0] * D * ds;
-                p[1] += mk[k * 16 + 1] * D * ds;
+#pragma unroll
+                for (int u = 0; u < kSpreadChunk; ++u)
+                    if (o + u < o1) {
+                        p[0] += mk[kk[u] * 16 + 0] * dd[u] * ds;
+                        p[1] += mk[kk[u] * 16 + 1] * dd[u] * ds;
+                    }
             }
         }
         R* o = patch + (size_t)q * 9;
@@ -983,6 +1087,16 @@ __global__ void __launch_bounds__(kIbThreads) ib_kernel(IbLaunch L) {
         B.hist[3 * h + 2] = Th;
         B.st.hist_n = B.st.hist_n + 1;
     }
+}
+
+template <class S>
+__global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
+    const BodyRef ref = L.refs[blockIdx.x];
+    __shared__ int shi[2 * kIbThreads + 4];
+    __shared__ double shd[3 * kIbThreads];
+    if (ref.b->nfp < 0) return;
+    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd);
+    else ib_run<S, 4>(L, ref, shi, shd);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1153,7 +1267,7 @@ static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, i
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);
         if (attr != cudaSuccess) return attr;
-        IBLBM_LAUNCH_SMEM((sc_kernel_bulk<S, KIND>), grid, kThreads, BulkGeom<S>::SMEM, st, L, jobs);
+        IBLBM_LAUNCH_SMEM((sc_kernel_bulk<S, KIND>), grid, kBulkThreads, BulkGeom<S>::SMEM, st, L, jobs);
     } else IBLBM_LAUNCH((sc_kernel<S, KIND>), grid, kThreads, st, L, jobs);
     return cudaGetLastError();
 }
@@ -1190,7 +1304,7 @@ static int sc_occ_k(int variant) {
     else if (variant == SC_BULK) {
         const void* fn = reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>);
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, BulkGeom<S>::SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBulkThreads, BulkGeom<S>::SMEM);
     } else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel<S, KIND>, kThreads, 0);
     return nb;

@@ -70,6 +70,7 @@ inline T __shfl_down_sync(unsigned, T v, unsigned d) {
     return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src > 31 ? lane : src));
 }
 inline int __any_sync(unsigned, int pred) { return emu::any(pred); }
+inline void __syncwarp(unsigned = 0xffffffffu) { emu::any(0); }
 
 inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
 inline unsigned atomicOr(unsigned* p, unsigned v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }

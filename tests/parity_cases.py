@@ -107,6 +107,39 @@ def check_domain_conditions_f64(name, nx, ny, storage=W.F64, rounds=3, steps=7):
         assert_f64_state(g.populations(), c.populations(), u_ref=0.02)
 
 
+# ---------------------------------------------------------------- rows of many tiles
+def check_wide_rows_f64(collision, scheme, kernel, nx=1600, ny=28, steps=3):
+    """Rows spanning several tiles of every stream-collide variant (the bulk-staged
+    variant's interior tiles need x0 > 0 and x0 + 512 < nx - 1), with a body whose
+    footprint straddles the tile seam at x = 1024."""
+    body = cylinder_body(1024.3, 0.5 * ny + 0.2, 10.0, 31, kernel, scheme, mdf_nmin=2, mdf_nmax=6, mdf_tol=1e-4)
+    spec = channel_spec(nx, ny, collision=collision, tau=0.7, storage=W.F64, u=0.05, bodies=[body])
+    g, c = gpu_case(spec), oracle_case(spec)
+    f0 = W.random_populations(17, nx, ny, amp=0.02)
+    g.set_populations(f0)
+    c.set_populations(f0)
+    stepped(g, c, steps)
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.05)
+    Fg, Fc = g.body_forces(0), c.body_forces(0)
+    assert np.abs(Fg - Fc).max() < 1e-12 * np.abs(Fc[:2]).max()
+
+
+def check_wide_rows_narrow(storage, nx=1600, ny=6):
+    """One step of a wide channel in FP32 / FP16 storage from the stored state,
+    within the storage round-off (as the narrow-type domain-condition check)."""
+    bc, ubc = BC_SETS["channel"]
+    f0 = W.random_populations(18, nx, ny, amp=0.02)
+    spec = W.CaseSpec(name="wide", nx=nx, ny=ny, bc=bc, ubc=ubc, collision=W.TRT, tau=0.7, storage=storage,
+                      trt_lambda=3.0 / 16.0)
+    g, c = gpu_case(spec), oracle_case(spec)
+    g.set_populations(f0)
+    c.set_populations(g.populations())
+    g.step(1)
+    c.step(1)
+    tol = 1e-6 if storage == W.F32 else 2e-3
+    assert rel_l2(dev(g.populations()), dev(c.populations())) < tol
+
+
 # ---------------------------------------------------------------- immersed boundary
 def check_ib_channel_f64(scheme, kernel, collision, nx=150, ny=64, D=16.0, n=47, steps=60):
     body = cylinder_body(0.27 * nx, 0.495 * ny, D, n, kernel, scheme, mdf_nmin=2, mdf_nmax=12, mdf_tol=1e-4)

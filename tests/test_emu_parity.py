@@ -41,6 +41,14 @@ def full_only(L):
         pytest.skip("checked with the one-node-per-lane variant")
 
 
+def bulk_only(L):
+    """Rows of several 512-node tiles matter to the bulk-staged variant (its
+    interior-tile path); the other variants' segments are covered by the
+    narrower lattices."""
+    if L._test_variant != 3:
+        pytest.skip("checked with the bulk-staged variant")
+
+
 SCHEMES = [W.DF, W.MDF, W.DFC]
 KERNELS = [W.HAT, W.PESKIN4]
 COLLS = [W.BGK, W.TRT, W.CMMRT]
@@ -86,6 +94,24 @@ def test_domain_conditions_narrow_types(L, name, storage):
     c.step(1)
     tol = 1e-6 if storage == W.F32 else 2e-3
     assert rel_l2(P.dev(g.populations()), P.dev(c.populations())) < tol
+
+
+@pytest.mark.parametrize("storage,dt", [(W.F64, np.float64), (W.F32, np.float32), (W.F16S, np.float16)])
+def test_wide_streaming_bit_exact(L, storage, dt):
+    bulk_only(L)
+    P.check_streaming_bit_exact(storage, dt, 1600, 3, full_cycle=False)
+
+
+@pytest.mark.parametrize("scheme,kernel,collision", [(W.DF, W.PESKIN4, W.CMMRT), (W.DFC, W.HAT, W.BGK)])
+def test_wide_rows_f64(L, scheme, kernel, collision):
+    bulk_only(L)
+    P.check_wide_rows_f64(collision, scheme, kernel, ny=24, steps=2)
+
+
+@pytest.mark.parametrize("storage", [W.F32, W.F16S])
+def test_wide_rows_narrow(L, storage):
+    bulk_only(L)
+    P.check_wide_rows_narrow(storage, ny=4)
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)

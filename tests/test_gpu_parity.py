@@ -57,6 +57,22 @@ def test_domain_conditions_f64(name, nx, ny):
     P.check_domain_conditions_f64(name, nx, ny)
 
 
+@pytest.mark.parametrize("storage,dt", [(W.F64, np.float64), (W.F32, np.float32), (W.F16S, np.float16)])
+def test_wide_streaming_bit_exact(storage, dt):
+    P.check_streaming_bit_exact(storage, dt, 1600, 7)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kernel,collision", [(W.HAT, W.BGK), (W.PESKIN4, W.TRT), (W.PESKIN4, W.CMMRT)])
+def test_wide_rows_f64(scheme, kernel, collision):
+    P.check_wide_rows_f64(collision, scheme, kernel, steps=20)
+
+
+@pytest.mark.parametrize("storage", [W.F32, W.F16S])
+def test_wide_rows_narrow(storage):
+    P.check_wide_rows_narrow(storage, ny=40)
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("collision", COLLS)
