@@ -429,17 +429,48 @@ __device__ __forceinline__ int bulk_locate(const ScLaunch& L, long long job, int
     return lo;
 }
 
-// Producer side (one thread): describe tile `job` and start its nine row copies.
-template <class S>
-__device__ __forceinline__ void bulk_issue(const ScLaunch& L, long long job, S* st, uint64_t* full, BulkDesc* desc) {
-    using G = BulkGeom<S>;
-    int y, x0;
-    const int c = bulk_locate<G::TW>(L, job, y, x0);
+// Producer's position in the job list with the current case's fields cached, so
+// that a tile costs no global loads beyond its copies.  The IB flag uses the union
+// of the case's body boxes (conservative: add_ib checks each node exactly).
+struct BulkCursor {
+    int c, y, seg, nseg, nx, ny, pitch;
+    long long plane, end;
+    const void* src;
+    int iy0, iy1, ix0, ix1;
+};
+
+template <int TW>
+__device__ __forceinline__ void cursor_load(const ScLaunch& L, BulkCursor& u, int c, long long job) {
     const CaseDev& C = *L.cases[c];
-    const bool staged = y > 0 && y < C.ny - 1;
-    const bool interior = staged && x0 > 0 && x0 + G::TW < C.nx - 1;
-    const bool ib = C.nbodies > 0 && row_has_ib(C, y, x0, x0 + G::TW);
-    desc->c = c;
+    u.c = c;
+    u.nx = C.nx;
+    u.ny = C.ny;
+    u.pitch = C.pitch;
+    u.plane = C.plane;
+    u.nseg = (C.nx + TW - 1) / TW;
+    u.end = L.job_off[c + 1];
+    const long long local = job - L.job_off[c];
+    u.y = (int)(local / u.nseg);
+    u.seg = (int)(local % u.nseg);
+    u.src = C.f[(int)(C.step & 1ull)];
+    u.iy0 = INT_MAX; u.iy1 = INT_MIN; u.ix0 = INT_MAX; u.ix1 = INT_MIN;
+    for (int b = 0; b < C.nbodies; ++b) {
+        const BodyDev& B = C.bodies[b];
+        if (B.nfp <= 0) continue;
+        u.iy0 = min(u.iy0, B.by0); u.iy1 = max(u.iy1, B.by0 + B.bh);
+        u.ix0 = min(u.ix0, B.bx0); u.ix1 = max(u.ix1, B.bx0 + B.bw);
+    }
+}
+
+// Describe the cursor's tile in `desc` and start its nine row copies into `st`.
+template <class S>
+__device__ __forceinline__ void bulk_issue(const BulkCursor& u, S* st, uint64_t* full, BulkDesc* desc) {
+    using G = BulkGeom<S>;
+    const int y = u.y, x0 = u.seg * G::TW;
+    const bool staged = y > 0 && y < u.ny - 1;
+    const bool interior = staged && x0 > 0 && x0 + G::TW < u.nx - 1;
+    const bool ib = y >= u.iy0 && y < u.iy1 && u.ix0 < x0 + G::TW && u.ix1 > x0;
+    desc->c = u.c;
     desc->y = y;
     desc->x0 = x0;
     desc->flags = (staged ? BULK_STAGED : 0) | (interior ? BULK_INTERIOR : 0) | (ib ? BULK_IB : 0);
@@ -447,17 +478,21 @@ __device__ __forceinline__ void bulk_issue(const ScLaunch& L, long long job, S* 
         bar_arrive_tx(full, 0);
         return;
     }
-    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
-    const int xs = max(x0 - G::H, 0), xe = min(x0 + G::TW + G::H, C.pitch);
+    const S* src = static_cast<const S*>(u.src);
+    const int xs = max(x0 - G::H, 0), xe = min(x0 + G::TW + G::H, u.pitch);
     const unsigned bytes = (unsigned)((xe - xs) * (int)sizeof(S));
     bar_arrive_tx(full, 9u * bytes);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        bulk_g2s(st + i * G::RS + (xs - x0 + G::H), src + i * C.plane + (long long)(y - ey(i)) * C.pitch + xs, bytes,
+        bulk_g2s(st + i * G::RS + (xs - x0 + G::H), src + i * u.plane + (long long)(y - ey(i)) * u.pitch + xs, bytes,
                  full);
 }
 
-// One node of a staged tile: pull from the stage, IB patch, collision, store.
+__device__ __forceinline__ void stg1(double* p, double v) { __stcg(p, v); }
+__device__ __forceinline__ void stg1(float* p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void stg1(__half* p, float v) { __stcg(p, __float2half_rn(v)); }
+
+// One node of a staged tile: pull from the stage, IB patch, collision, streaming store.
 template <class S, int KIND, bool FORCED>
 __device__ __forceinline__ bool bulk_node(const ScCase<S>& K, const S* b, S* d, int x, int y, bool ib) {
     using R = typename Traits<S>::R;
@@ -473,15 +508,59 @@ __device__ __forceinline__ bool bulk_node(const ScCase<S>& K, const S* b, S* d, 
         rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+    for (int i = 0; i < 9; ++i) stg1(d + i * K.plane, s[i]);
     return bad_density(rho);
+}
+
+// A node on a lattice edge or edge row: global pulls with the domain conditions.
+template <class S, int KIND>
+__device__ IBLBM_NOINLINE bool bulk_edge_node(const ScCase<S>& K, S* d, int x, int y, bool ib) {
+    using R = typename Traits<S>::R;
+    R s[9];
+    post_stream_node<S, R>(*K.C, K.src, x, y, s);
+    R Fx = K.gfx, Fy = K.gfy;
+    if (ib) add_ib<R>(*K.C, x, y, s, Fx, Fy);
+    const R rho = collide<R, KIND>(K.P, s, Fx, Fy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) stg1(d + i * K.plane, s[i]);
+    return bad_density(rho);
+}
+
+// All nodes of a tile.  Interior tiles take the stage without checks; staged
+// tiles touching a side take it for their inner nodes; edge rows pull globally.
+template <class S, int KIND, bool FORCED>
+__device__ __forceinline__ bool bulk_tile(const ScCase<S>& K, const S* st, S* d, int x0, int y, int flags, int tid) {
+    constexpr int NPT = BulkCfg<S>::NPT;
+    const bool ib = (flags & BULK_IB) != 0;
+    bool unstable = false;
+    if (flags & BULK_INTERIOR) {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+            unstable |= bulk_node<S, KIND, FORCED>(K, st + kBulkConsumers * j, d + kBulkConsumers * j,
+                                                   x0 + tid + kBulkConsumers * j, y, ib);
+    } else if (flags & BULK_STAGED) {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int x = x0 + tid + kBulkConsumers * j;
+            if (x > 0 && x < K.nx - 1)
+                unstable |= bulk_node<S, KIND, FORCED>(K, st + kBulkConsumers * j, d + kBulkConsumers * j, x, y, ib);
+            else if (x < K.nx)
+                unstable |= bulk_edge_node<S, KIND>(K, d + kBulkConsumers * j, x, y, ib);
+        }
+    } else {
+#pragma unroll 1
+        for (int j = 0; j < NPT; ++j) {
+            const int x = x0 + tid + kBulkConsumers * j;
+            if (x < K.nx) unstable |= bulk_edge_node<S, KIND>(K, d + kBulkConsumers * j, x, y, ib);
+        }
+    }
+    return unstable;
 }
 
 template <class S, int KIND>
 __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bulk(ScLaunch L, long long jobs) {
-    using R = typename Traits<S>::R;
     using G = BulkGeom<S>;
-    constexpr int NST = G::NST, NPT = BulkCfg<S>::NPT, TW = G::TW, RS = G::RS, H = G::H;
+    constexpr int NST = G::NST, TW = G::TW, RS = G::RS, H = G::H;
     IBLBM_DYNAMIC_SMEM(smem);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + NST;
@@ -502,7 +581,11 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
 
     if (tid >= kBulkConsumers) {
         // producer warp: lane 0 streams the CTA's tiles through the stages
-        if (tid == kBulkConsumers) {
+        if (tid == kBulkConsumers && j0 < j1) {
+            BulkCursor u;
+            int c0, yy, xx;
+            c0 = bulk_locate<TW>(L, j0, yy, xx);
+            cursor_load<TW>(L, u, c0, j0);
             long long job = j0;
             for (; job < j1 && !abort_flag; ++job) {
                 const long long t = job - j0;
@@ -511,12 +594,16 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
                     abort_flag = 1;
                     break;
                 }
-                bulk_issue<S>(L, job, stages + k * 9 * RS, &full[k], &desc[k]);
+                while (job >= u.end) cursor_load<TW>(L, u, u.c + 1, job);
+                bulk_issue<S>(u, stages + k * 9 * RS, &full[k], &desc[k]);
+                if (++u.seg == u.nseg) {
+                    u.seg = 0;
+                    ++u.y;
+                }
             }
             if (abort_flag) {
                 // report, then wait (bounded) for copies that may still be landing
-                int yy, xx;
-                atomicOr(const_cast<unsigned*>(&L.cases[bulk_locate<TW>(L, j0, yy, xx)]->status), STAT_TIMEOUT);
+                atomicOr(const_cast<unsigned*>(&L.cases[c0]->status), STAT_TIMEOUT);
                 for (long long jj = job - 1; jj >= j0 && jj >= job - NST; --jj)
                     bar_wait(&full[(jj - j0) % NST], (unsigned)(((jj - j0) / NST) & 1), kBulkSpinLimit);
             }
@@ -540,49 +627,11 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
             K.load(L.cases[dk.c]);
             cur = dk.c;
         }
-        const int y = dk.y, x0 = dk.x0;
-        const bool ib = (dk.flags & BULK_IB) != 0;
-        const bool forced = ib || K.has_force;
+        const bool forced = (dk.flags & BULK_IB) || K.has_force;
         const S* st = stages + k * 9 * RS + tid + H;
-        S* d = K.dst + ((long long)y * K.pitch + x0 + tid);
-        bool unstable = false;
-        if (dk.flags & BULK_INTERIOR) {
-            if (forced) {
-#pragma unroll
-                for (int j = 0; j < NPT; ++j)
-                    unstable |= bulk_node<S, KIND, true>(K, st + kBulkConsumers * j, d + kBulkConsumers * j,
-                                                         x0 + tid + kBulkConsumers * j, y, ib);
-            } else {
-#pragma unroll
-                for (int j = 0; j < NPT; ++j)
-                    unstable |= bulk_node<S, KIND, false>(K, st + kBulkConsumers * j, d + kBulkConsumers * j,
-                                                          x0 + tid + kBulkConsumers * j, y, false);
-            }
-        } else {
-            const CaseDev& C = *K.C;
-            const bool staged = (dk.flags & BULK_STAGED) != 0;
-#pragma unroll 1
-            for (int j = 0; j < NPT; ++j) {
-                const int x = x0 + tid + kBulkConsumers * j;
-                if (x >= K.nx) continue;
-                if (staged && x > 0 && x < K.nx - 1) {
-                    unstable |= forced ? bulk_node<S, KIND, true>(K, st + kBulkConsumers * j,
-                                                                  d + kBulkConsumers * j, x, y, ib)
-                                       : bulk_node<S, KIND, false>(K, st + kBulkConsumers * j,
-                                                                   d + kBulkConsumers * j, x, y, false);
-                } else {
-                    R s[9];
-                    post_stream_node<S, R>(C, K.src, x, y, s);
-                    R Fx = K.gfx, Fy = K.gfy;
-                    if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-                    const R rho = collide<R, KIND>(K.P, s, Fx, Fy);
-                    unstable |= bad_density(rho);
-                    S* dd = d + kBulkConsumers * j;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) st1(dd + i * K.plane, s[i]);
-                }
-            }
-        }
+        S* d = K.dst + ((long long)dk.y * K.pitch + dk.x0 + tid);
+        const bool unstable = forced ? bulk_tile<S, KIND, true>(K, st, d, dk.x0, dk.y, dk.flags, tid)
+                                     : bulk_tile<S, KIND, false>(K, st, d, dk.x0, dk.y, dk.flags, tid);
         if (__any_sync(0xffffffffu, unstable) && lane == 0)
             atomicOr(const_cast<unsigned*>(&K.C->status), STAT_UNSTABLE);
         __syncwarp();

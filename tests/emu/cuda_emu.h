@@ -44,6 +44,8 @@ inline void __syncthreads() { emu::syncthreads(); }
 
 template <class T>
 inline T __ldg(const T* p) { return *p; }
+template <class T>
+inline void __stcg(T* p, T v) { *p = v; }
 
 template <class T>
 inline T emu_from_bits(uint64_t b) {
