@@ -182,15 +182,20 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
             k, _, _ = srv.tick(tick)
             done += k
         wall = time.perf_counter() - t0
-        lats, failed = [], 0
-        for i in ids:
+        lats, failed, why = [], 0, {}
+        for i, sp in zip(ids, specs):
             try:
                 lats.append(srv.poll(i, cap=4)[1])
-            except L.IblbmError:       # a request whose case went unstable or did not fit
+            except L.IblbmError as exc:       # a request whose case went unstable or did not fit
                 failed += 1
+                key = "%s %dx%d %s/%s/%s tau<%.2f" % (
+                    str(exc).split(":")[-1].strip(), sp.nx, sp.ny, ("BGK", "TRT", "CM-MRT")[sp.collision],
+                    ("DF", "MDF", "DFC")[sp.bodies[0].scheme], ("hat", "P4")[sp.bodies[0].kernel],
+                    math.ceil(sp.tau * 20) / 20)
+                why[key] = why.get(key, 0) + 1
         srv.close()
         return {"cases_per_s": len(specs) / wall, "p50_s": _pct(lats, 50), "p99_s": _pct(lats, 99),
-                "wall_s": wall, "failed": failed}
+                "wall_s": wall, "failed": failed, "failed_kinds": why}
 
     cap = run_server([0.0] * len(specs))
     rate_cap = cap["cases_per_s"]
