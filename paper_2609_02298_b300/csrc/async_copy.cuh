@@ -41,14 +41,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+// One poll; the thread may be suspended in hardware for up to kBarSuspendNs while
+// the phase is incomplete (woken early when it completes), so waiting warps do
+// not take issue slots from working ones.
+constexpr unsigned kBarSuspendNs = 500;
 __device__ __forceinline__ bool bar_test(uint64_t* bar, unsigned parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kBarSuspendNs)
         : "memory");
     return ok != 0;
 }

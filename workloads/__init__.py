@@ -182,7 +182,9 @@ def serving_requests(seed: int = 0, n: int = 256, rate: float = 100.0, steps: in
     """Seeded request stream: Poisson arrivals (rate per second), grids drawn
     log-uniformly from ``grids``, D = ny/8, round(pi D) markers, uniform
     scheme/kernel/collision, Re uniform in [20, 200], U = 0.1, resampled while
-    tau < 0.55.  Returns (arrival_times, [CaseSpec]), plus the resample count."""
+    tau is below the operator's floor (0.6 for BGK, whose runs below it went
+    unstable on the coarse grids at U = 0.1; 0.55 for TRT and CM-MRT).
+    Returns (arrival_times, [CaseSpec]), plus the resample count."""
     grids = grids or SERVING_GRIDS
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n))
@@ -190,15 +192,16 @@ def serving_requests(seed: int = 0, n: int = 256, rate: float = 100.0, steps: in
     for r in range(n):
         nx, ny = grids[rng.integers(len(grids))]
         d = ny / 8.0
-        while True:
-            re = rng.uniform(20.0, 200.0)
-            tau = tau_for(0.1, d, re)
-            if tau >= 0.55:
-                break
-            resampled += 1
         scheme = int(rng.integers(3))
         kernel = int(rng.integers(2))
         collision = int(rng.integers(3))
+        floor = 0.6 if collision == BGK else 0.55
+        while True:
+            re = rng.uniform(20.0, 200.0)
+            tau = tau_for(0.1, d, re)
+            if tau >= floor:
+                break
+            resampled += 1
         spec = _cylinder_channel("req%d" % r, nx, ny, 0.4 * nx, 0.5 * ny, d,
                                  int(round(math.pi * d)), 0.1, tau, collision, kernel, scheme,
                                  storage, steps)
