@@ -283,7 +283,9 @@ int iblbm_dfc_lambda_noalloc(const double* xy, int n, double ds, int kernel, int
 
 /* ---- timing of the stream-collide kernel ------------------------------------------ */
 /* While enabled, steps launch their kernels one by one (no graph) and bracket
- * each stream-collide launch with CUDA events on the launching stream.
+ * each stream-collide launch (one per collision operator and storage type in
+ * the batch) and each lattice-edge launch (one per storage type) with CUDA
+ * events on the launching stream; together they are the whole lattice sweep.
  * iblbm_kernel_timing returns the summed event time (ms) and the launch count
  * since the last reset, then resets.  Syncs. */
 int iblbm_set_timing(iblbm_ctx* ctx, int enable);

@@ -730,12 +730,22 @@ struct IbGroup {
     BodyRef* drefs = nullptr;
     int nrefs = 0;
 };
+// Lattice-edge nodes of all lattices of one storage type (one launch per step).
+struct EdgeGroup {
+    int storage = 0;
+    int ncases = 0;
+    CaseDev** dcases = nullptr;
+    long long* doff = nullptr;
+    long long total = 0;
+    int grid = 1;
+};
 
 struct BatchPlan {
     std::vector<iblbm_ctx*> ctxs;
     std::vector<int> versions;
     std::vector<BatchGroup> groups;
     std::vector<IbGroup> ib_groups;
+    std::vector<EdgeGroup> edge_groups;
     BodyRef* drefs_all = nullptr;
     CaseDev** dcases_all = nullptr;
     int nrefs_all = 0;
@@ -786,6 +796,20 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
             timer->ev_pending.push_back({a, b});
         }
     }
+    for (auto& g : P->edge_groups) {
+        ScLaunch sl{g.dcases, g.doff, g.ncases, 0};
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timer) {
+            a = pool_event(timer);
+            b = pool_event(timer);
+            cudaEventRecord(a, st);
+        }
+        if ((e = launch_edges(g.storage, sl, g.total, g.grid, st)) != cudaSuccess) return e;
+        if (timer) {
+            cudaEventRecord(b, st);
+            timer->ev_pending.push_back({a, b});
+        }
+    }
     return launch_body(all, 1, st);
 }
 
@@ -824,6 +848,29 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             cudaMemcpyAsync(ig.drefs, refs.data(), sizeof(BodyRef) * refs.size(), cudaMemcpyHostToDevice, P->st);
             P->ib_groups.push_back(ig);
             all_refs.insert(all_refs.end(), refs.begin(), refs.end());
+        }
+        {
+            EdgeGroup eg;
+            eg.storage = st;
+            std::vector<CaseDev*> cs;
+            std::vector<long long> off{0};
+            for (int i = 0; i < n; ++i) {
+                iblbm_ctx* c = ctxs[i];
+                if (c->hc.storage != st) continue;
+                cs.push_back(c->dc);
+                off.push_back(off.back() + lattice_edge_nodes(c->hc.nx, c->hc.ny));
+            }
+            if (!cs.empty()) {
+                eg.ncases = (int)cs.size();
+                eg.total = off.back();
+                eg.grid = (int)std::max<long long>(1, std::min<long long>((eg.total + 255) / 256, (long long)sms * 8));
+                eg.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
+                eg.doff = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
+                if (!eg.dcases || !eg.doff) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+                cudaMemcpyAsync(eg.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
+                cudaMemcpyAsync(eg.doff, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
+                P->edge_groups.push_back(eg);
+            }
         }
         for (int col = 0; col < 4; ++col) {
             BatchGroup g;

@@ -8,9 +8,7 @@
 
 #ifdef IBLBM_EMULATE
 #include "cuda_emu.h"   // host-thread emulation used only by the CPU test suite
-#define IBLBM_NOINLINE
 #else
-#define IBLBM_NOINLINE __noinline__
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #define IBLBM_LAUNCH(kern, grid, block, stream, ...) kern<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__)

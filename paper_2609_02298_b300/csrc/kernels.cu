@@ -97,21 +97,10 @@ __device__ __forceinline__ void sc_row(const ScCase<S>& K, int y, int xseg, int 
     const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * V);
     bool unstable = false;
 
-    if (!yper && (y == 0 || y == ny - 1)) {
-        // boundary row: node by node with the general domain conditions
-#pragma unroll 1
-        for (int k = 0; k < V; ++k) {
-            const int x = x0 + k;
-            if (x >= nx) break;
-            R s[9];
-            post_stream_node<S, R>(C, src, x, y, s);
-            R Fx = gfx, Fy = gfy;
-            if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-            unstable |= bad_density(collide<R, KIND>(P, s, Fx, Fy));
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st1(dst + i * plane + (long long)y * pitch + x, s[i]);
-        }
-    } else {
+    // the first and last rows belong to edge_kernel; side nodes computed here are
+    // rewritten by it after this launch
+    if (y == 0 || y == ny - 1) return;
+    {
         int ym = y - 1, yp = y + 1;
         if (yper) {
             if (ym < 0) ym += ny;
@@ -288,11 +277,12 @@ __global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_ke
 // ------------------------------------------------------------------------------------------
 // Stream-collide, NPT nodes per lane: a warp handles NPT chunks of 32 consecutive
 // nodes of a row (x = xseg + 32 j + lane) and pulls each population with a plain
-// coalesced (possibly one-element unaligned) load.  On B300 the HBM rate allows
-// only ~400 issued instructions per node, so the interior path is lean: 32-bit
-// element offsets with per-population constants, no wrap logic (nodes on any
-// lattice edge take the general path), and the Guo term only on rows that carry
-// a force.
+// coalesced (possibly one-element unaligned) load.  Only interior nodes are
+// computed here (1 <= x <= nx-2, 1 <= y <= ny-2): lattice-edge nodes go to
+// edge_kernel, so the warp path carries no wrap or boundary logic (measured on
+// B300: a boundary branch inside the sweep costs a third of the HBM rate).
+// 32-bit element offsets with per-population constants; the Guo term only on rows
+// that carry a force.
 template <class S, int KIND, int NPT>
 __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane) {
     using R = typename Traits<S>::R;
@@ -300,9 +290,9 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     const S* __restrict__ src = K.src;
     S* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
+    if (y == 0 || y == ny - 1) return;
     const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
     const bool forced = ib || K.has_force;
-    const bool edge_row = y == 0 || y == ny - 1;
     // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
     int koff[9];
 #pragma unroll
@@ -312,15 +302,11 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const int x = xseg + 32 * j + lane;
-        if (x < nx) {
+        if (x >= 1 && x < nx - 1) {
             R s[9];
-            if (edge_row || x == 0 || x == nx - 1) {
-                post_stream_node<S, R>(C, src, x, y, s);
-            } else {
-                const int a = row + x;
+            const int a = row + x;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) s[i] = ld1(src + (a + koff[i]));
-            }
+            for (int i = 0; i < 9; ++i) s[i] = ld1(src + (a + koff[i]));
             R rho;
             if (forced) {
                 R Fx = K.gfx, Fy = K.gfy;
@@ -330,7 +316,6 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
                 rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
             }
             unstable |= bad_density(rho);
-            const int a = row + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) st1(dst + (a + i * plane), s[i]);
         }
@@ -341,17 +326,19 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = NPT == 1 ? 4 : 3; };
 template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
+// Dense job order: warp w takes jobs w, w + W, w + 2W, ... (W warps in the grid),
+// so the warps resident at any moment sweep one compact window of each plane;
+// measured on B300 this beats one contiguous job range per warp by ~10% of HBM.
 template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * kThreads) >> 5;
-    const long long j0 = jobs * gw / nw, j1 = jobs * (gw + 1) / nw;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
-    int nseg = 1, y = 0, seg = 0;
-    for (long long job = j0; job < j1; ++job) {
+    int nseg = 1;
+    for (long long job = gw; job < jobs; job += nw) {
         if (job >= c_hi || job < c_lo) {
             int lo = 0, hi = L.ncases - 1;
             while (lo < hi) {
@@ -362,15 +349,66 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
             c_hi = L.job_off[lo + 1];
             K.load(L.cases[lo]);
             nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
-            const long long local = job - c_lo;
-            y = (int)(local / nseg);
-            seg = (int)(local % nseg);
         }
-        sc_row_scalar<S, KIND, NPT>(K, y, seg * 32 * NPT, lane);
-        if (++seg == nseg) {
-            seg = 0;
-            ++y;
+        const int local = (int)(job - c_lo);   // < ny * nseg
+        const int y = local / nseg;
+        sc_row_scalar<S, KIND, NPT>(K, y, (local - y * nseg) * 32 * NPT, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Lattice-edge nodes (rows 0 and ny-1, columns 0 and nx-1) of every case of one
+// storage type, one node per thread: pull with wrap and domain conditions
+// (post_stream_node), IB patch, collision with the case's own operator, store.
+// Runs after the stream-collide launches of the step and is the only writer of
+// these nodes' results (a variant that also wrote them is overwritten).
+// Edge node e of a case: e < nx -> (e, 0); e < 2nx -> (e - nx, ny - 1) when
+// ny > 1; then columns 0 and nx-1 of rows 1..ny-2, alternating.
+__host__ __device__ inline long long edge_count(int nx, int ny) {
+    const long long rows = (long long)nx * (ny > 1 ? 2 : 1);
+    const long long cols = ny > 2 ? (long long)(ny - 2) * (nx > 1 ? 2 : 1) : 0;
+    return rows + cols;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads) edge_kernel(ScLaunch L, long long total) {
+    using R = typename Traits<S>::R;
+    ScCase<S> K;
+    long long c_lo = 0, c_hi = 0;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < total;
+         q += (long long)gridDim.x * kThreads) {
+        if (q >= c_hi || q < c_lo) {
+            int lo = 0, hi = L.ncases - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.job_off[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            c_lo = L.job_off[lo];
+            c_hi = L.job_off[lo + 1];
+            K.load(L.cases[lo]);
         }
+        const CaseDev& C = *K.C;
+        const int nx = K.nx, ny = K.ny;
+        const int e = (int)(q - c_lo);
+        int x, y;
+        if (e < nx) {
+            x = e; y = 0;
+        } else if (ny > 1 && e < 2 * nx) {
+            x = e - nx; y = ny - 1;
+        } else {
+            const int r = e - (ny > 1 ? 2 * nx : nx);
+            if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
+            else { y = 1 + r; x = 0; }
+        }
+        R s[9];
+        post_stream_node<S, R>(C, K.src, x, y, s);
+        R Fx = K.gfx, Fy = K.gfy;
+        if (K.nbodies > 0) add_ib<R>(C, x, y, s, Fx, Fy);
+        const R rho = collide<R, -1>(K.P, s, Fx, Fy);
+        if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+        S* d = K.dst + ((long long)y * K.pitch + x);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
     }
 }
 
@@ -512,22 +550,9 @@ __device__ __forceinline__ bool bulk_node(const ScCase<S>& K, const S* b, S* d, 
     return bad_density(rho);
 }
 
-// A node on a lattice edge or edge row: global pulls with the domain conditions.
-template <class S, int KIND>
-__device__ IBLBM_NOINLINE bool bulk_edge_node(const ScCase<S>& K, S* d, int x, int y, bool ib) {
-    using R = typename Traits<S>::R;
-    R s[9];
-    post_stream_node<S, R>(*K.C, K.src, x, y, s);
-    R Fx = K.gfx, Fy = K.gfy;
-    if (ib) add_ib<R>(*K.C, x, y, s, Fx, Fy);
-    const R rho = collide<R, KIND>(K.P, s, Fx, Fy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) stg1(d + i * K.plane, s[i]);
-    return bad_density(rho);
-}
-
-// All nodes of a tile.  Interior tiles take the stage without checks; staged
-// tiles touching a side take it for their inner nodes; edge rows pull globally.
+// All interior nodes of a tile: interior tiles take the stage without checks;
+// staged tiles touching a side skip that side's edge node; edge rows hold no
+// interior nodes (edge_kernel computes every lattice-edge node).
 template <class S, int KIND, bool FORCED>
 __device__ __forceinline__ bool bulk_tile(const ScCase<S>& K, const S* st, S* d, int x0, int y, int flags, int tid) {
     constexpr int NPT = BulkCfg<S>::NPT;
@@ -544,14 +569,6 @@ __device__ __forceinline__ bool bulk_tile(const ScCase<S>& K, const S* st, S* d,
             const int x = x0 + tid + kBulkConsumers * j;
             if (x > 0 && x < K.nx - 1)
                 unstable |= bulk_node<S, KIND, FORCED>(K, st + kBulkConsumers * j, d + kBulkConsumers * j, x, y, ib);
-            else if (x < K.nx)
-                unstable |= bulk_edge_node<S, KIND>(K, d + kBulkConsumers * j, x, y, ib);
-        }
-    } else {
-#pragma unroll 1
-        for (int j = 0; j < NPT; ++j) {
-            const int x = x0 + tid + kBulkConsumers * j;
-            if (x < K.nx) unstable |= bulk_edge_node<S, KIND>(K, d + kBulkConsumers * j, x, y, ib);
         }
     }
     return unstable;
@@ -1391,6 +1408,18 @@ bool sc_variant_ok(int variant, const void* f0, const void* f1) {
     // bulk copies need 16-byte aligned population buffers
     return variant != SC_BULK || (((uintptr_t)f0 | (uintptr_t)f1) & 15u) == 0;
 }
+
+cudaError_t launch_edges(int storage, const ScLaunch& L, long long total, int grid, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    switch (storage) {
+    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, grid, kThreads, st, L, total); break;
+    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, grid, kThreads, st, L, total); break;
+    default: IBLBM_LAUNCH(edge_kernel<__half>, grid, kThreads, st, L, total); break;
+    }
+    return cudaGetLastError();
+}
+
+long long lattice_edge_nodes(int nx, int ny) { return edge_count(nx, ny); }
 
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     if (L.nrefs <= 0) return cudaSuccess;
