@@ -212,13 +212,16 @@ int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
  * per lane, 3 stages each tile's source rows in shared memory with bulk
  * asynchronous copies (needs 16-byte aligned population buffers, see
  * iblbm_set_allocator; otherwise variant 1 runs in its place and its tuning
- * time reads 0).  By default the first batch that needs a (storage, collision) pair
- * times all of them in place and keeps the fastest for the rest of the
- * process, so a lattice runs the same kernel alone, batched or served.
- * iblbm_set_kernel_variant fixes the choice (-1 = tune again);
- * iblbm_kernel_variant reports it (-1 = not chosen) and, if ms is not NULL,
- * writes the mean launch time of each variant measured when it was tuned
- * into ms[IBLBM_KERNEL_VARIANTS].  Errors: INVALID_ARG. */
+ * time reads 0).  By default the first batch that needs a (storage, collision)
+ * pair times all of them in place and keeps the fastest for the rest of the
+ * process; groups sweeping fewer than 2^20 nodes per launch (latency-bound) are
+ * tuned apart from larger ones, so a lattice runs the same kernel alone,
+ * batched or served within its size class.
+ * iblbm_set_kernel_variant fixes the choice for both classes (-1 = tune again);
+ * iblbm_kernel_variant reports the large-class choice once tuned, else the small
+ * one (-1 = not chosen) and, if ms is not NULL, writes the mean launch time of
+ * each variant measured when it was tuned into ms[IBLBM_KERNEL_VARIANTS].
+ * Errors: INVALID_ARG. */
 #define IBLBM_KERNEL_VARIANTS 4
 int iblbm_set_kernel_variant(int storage, int collision, int variant);
 int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);

@@ -715,15 +715,21 @@ struct BatchGroup {
     int grid[SC_VARIANTS] = {};
     long long* djob[SC_VARIANTS] = {};
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
+    int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
 };
 
-// Stream-collide variant per (storage, collision), process-wide so that a lattice
-// runs the same kernel alone, in any batch and in the server.  -1: not chosen
-// yet; the first plan that needs it times both variants in place and keeps the
-// faster (the kernel rewrites only its destination buffer from an unchanged
-// source, so repeating it has no effect on the state).
-int g_variant[3][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
-double g_variant_ms[3][5][SC_VARIANTS];
+// Stream-collide variant per (storage, collision, size class), process-wide so
+// that a lattice runs the same kernel alone, in any batch of its class and in the
+// server.  Small groups (< kLargeGroupNodes nodes) are latency-bound and tuned
+// apart from bandwidth-bound large ones.  -1: not chosen yet; the first plan that
+// needs it times every variant in place and keeps the fastest (the kernel
+// rewrites only its destination buffer from an unchanged source, so repeating it
+// has no effect on the state).
+constexpr long long kLargeGroupNodes = 1LL << 20;
+int g_variant[3][5][2] = {{{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}},
+                          {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}},
+                          {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}}};
+double g_variant_ms[3][5][2][SC_VARIANTS];
 static_assert(SC_VARIANTS == IBLBM_KERNEL_VARIANTS, "public variant count must match the kernels");
 struct IbGroup {
     int storage = 0;
@@ -733,11 +739,9 @@ struct IbGroup {
 // Lattice-edge nodes of all lattices of one storage type (one launch per step).
 struct EdgeGroup {
     int storage = 0;
-    int ncases = 0;
     CaseDev** dcases = nullptr;
-    long long* doff = nullptr;
-    long long total = 0;
-    int grid = 1;
+    EdgeChunk* dchunks = nullptr;
+    int nchunks = 0;
 };
 
 struct BatchPlan {
@@ -780,7 +784,8 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         }
     }
     for (auto& g : P->groups) {
-        int v = g_variant[g.storage][g.collision] < 0 ? SC_SCALAR : g_variant[g.storage][g.collision];
+        const int chosen = g_variant[g.storage][g.collision][g.size_class];
+        int v = chosen < 0 ? SC_SCALAR : chosen;
         if (!g.ok[v]) v = SC_SCALAR;
         ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
         cudaEvent_t a = nullptr, b = nullptr;
@@ -797,14 +802,14 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         }
     }
     for (auto& g : P->edge_groups) {
-        ScLaunch sl{g.dcases, g.doff, g.ncases, 0};
+        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, 0};
         cudaEvent_t a = nullptr, b = nullptr;
         if (timer) {
             a = pool_event(timer);
             b = pool_event(timer);
             cudaEventRecord(a, st);
         }
-        if ((e = launch_edges(g.storage, sl, g.total, g.grid, st)) != cudaSuccess) return e;
+        if ((e = launch_edges(g.storage, el, st)) != cudaSuccess) return e;
         if (timer) {
             cudaEventRecord(b, st);
             timer->ev_pending.push_back({a, b});
@@ -853,22 +858,22 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             EdgeGroup eg;
             eg.storage = st;
             std::vector<CaseDev*> cs;
-            std::vector<long long> off{0};
+            std::vector<EdgeChunk> chunks;
             for (int i = 0; i < n; ++i) {
                 iblbm_ctx* c = ctxs[i];
                 if (c->hc.storage != st) continue;
+                const int ne = (int)lattice_edge_nodes(c->hc.nx, c->hc.ny);
+                for (int f = 0; f < ne; f += kThreads) chunks.push_back(EdgeChunk{(int)cs.size(), f, std::min(ne, f + kThreads), 0});
                 cs.push_back(c->dc);
-                off.push_back(off.back() + lattice_edge_nodes(c->hc.nx, c->hc.ny));
             }
             if (!cs.empty()) {
-                eg.ncases = (int)cs.size();
-                eg.total = off.back();
-                eg.grid = (int)std::max<long long>(1, std::min<long long>((eg.total + 255) / 256, (long long)sms * 8));
+                eg.nchunks = (int)chunks.size();
                 eg.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
-                eg.doff = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
-                if (!eg.dcases || !eg.doff) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+                eg.dchunks = static_cast<EdgeChunk*>(plan_alloc(P, sizeof(EdgeChunk) * chunks.size()));
+                if (!eg.dcases || !eg.dchunks) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
                 cudaMemcpyAsync(eg.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
-                cudaMemcpyAsync(eg.doff, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
+                cudaMemcpyAsync(eg.dchunks, chunks.data(), sizeof(EdgeChunk) * chunks.size(), cudaMemcpyHostToDevice,
+                                P->st);
                 P->edge_groups.push_back(eg);
             }
         }
@@ -886,6 +891,11 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             g.dcases = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * cs.size()));
             if (!g.dcases) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
             cudaMemcpyAsync(g.dcases, cs.data(), sizeof(CaseDev*) * cs.size(), cudaMemcpyHostToDevice, P->st);
+            long long group_nodes = 0;
+            for (int i = 0; i < n; ++i)
+                if (ctxs[i]->hc.storage == st && ctxs[i]->hc.collision == col)
+                    group_nodes += (long long)ctxs[i]->hc.nx * ctxs[i]->hc.ny;
+            g.size_class = group_nodes >= kLargeGroupNodes ? 1 : 0;
             for (int v = 0; v < SC_VARIANTS; ++v) {
                 const int seg = sc_segment(st, v);
                 std::vector<long long> off{0};
@@ -923,7 +933,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
     if (*rc) { delete P; return nullptr; }
     // autotune: time each variant of every group whose (storage, collision) has no choice yet
     for (auto& g : P->groups) {
-        if (g_variant[g.storage][g.collision] >= 0) continue;
+        if (g_variant[g.storage][g.collision][g.size_class] >= 0) continue;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -931,7 +941,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         double best_ms = 1e300;
         for (int v = 0; v < SC_VARIANTS; ++v) {
             if (!g.ok[v]) {
-                g_variant_ms[g.storage][g.collision][v] = 0.0;
+                g_variant_ms[g.storage][g.collision][g.size_class][v] = 0.0;
                 continue;
             }
             ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
@@ -945,7 +955,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 cudaEventElapsedTime(&ms, a, b);
                 tot += ms;
             }
-            g_variant_ms[g.storage][g.collision][v] = tot / 3.0;
+            g_variant_ms[g.storage][g.collision][g.size_class][v] = tot / 3.0;
             if (tot / 3.0 < best_ms) {
                 best_ms = tot / 3.0;
                 best = v;
@@ -953,7 +963,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
-        g_variant[g.storage][g.collision] = best;
+        g_variant[g.storage][g.collision][g.size_class] = best;
     }
     *rc = check(cudaStreamSynchronize(P->st));
     if (*rc) { delete P; return nullptr; }
@@ -981,16 +991,17 @@ int batch_capture(BatchPlan* P, int nsteps, cudaGraphExec_t* out) {
 extern "C" int iblbm_set_kernel_variant(int storage, int collision, int variant) {
     if (storage < 0 || storage > 2 || collision < 0 || collision > 3 || variant < -1 || variant >= SC_VARIANTS)
         return IBLBM_ERR_INVALID_ARG;
-    g_variant[storage][collision] = variant;
+    g_variant[storage][collision][0] = g_variant[storage][collision][1] = variant;
     for (auto& kv : g_plans) kv.second->graphs.reset();   // captured graphs hold the old kernel
     return IBLBM_OK;
 }
 
 extern "C" int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms) {
     if (storage < 0 || storage > 2 || collision < 0 || collision > 3) return IBLBM_ERR_INVALID_ARG;
-    if (variant) *variant = g_variant[storage][collision];
+    const int cls = g_variant[storage][collision][1] >= 0 ? 1 : 0;   // the large class when tuned
+    if (variant) *variant = g_variant[storage][collision][cls];
     if (ms)
-        for (int v = 0; v < SC_VARIANTS; ++v) ms[v] = g_variant_ms[storage][collision][v];
+        for (int v = 0; v < SC_VARIANTS; ++v) ms[v] = g_variant_ms[storage][collision][cls][v];
     return IBLBM_OK;
 }
 

@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
 
 // ------------------------------------------------------------------------------------------
 // Lattice-edge nodes (rows 0 and ny-1, columns 0 and nx-1) of every case of one
-// storage type, one node per thread: pull with wrap and domain conditions
+// storage type, one node per thread, one CTA per chunk of 256 edge nodes of one
+// case (chunk table built on the host): pull with wrap and domain conditions
 // (post_stream_node), IB patch, collision with the case's own operator, store.
 // Runs after the stream-collide launches of the step and is the only writer of
 // these nodes' results (a variant that also wrote them is overwritten).
@@ -371,45 +372,34 @@ __host__ __device__ inline long long edge_count(int nx, int ny) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(kThreads) edge_kernel(ScLaunch L, long long total) {
+__global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     using R = typename Traits<S>::R;
+    const EdgeChunk ch = L.chunks[blockIdx.x];   // one CTA per 256 edge nodes of one case
     ScCase<S> K;
-    long long c_lo = 0, c_hi = 0;
-    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < total;
-         q += (long long)gridDim.x * kThreads) {
-        if (q >= c_hi || q < c_lo) {
-            int lo = 0, hi = L.ncases - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (L.job_off[mid] <= q) lo = mid; else hi = mid - 1;
-            }
-            c_lo = L.job_off[lo];
-            c_hi = L.job_off[lo + 1];
-            K.load(L.cases[lo]);
-        }
-        const CaseDev& C = *K.C;
-        const int nx = K.nx, ny = K.ny;
-        const int e = (int)(q - c_lo);
-        int x, y;
-        if (e < nx) {
-            x = e; y = 0;
-        } else if (ny > 1 && e < 2 * nx) {
-            x = e - nx; y = ny - 1;
-        } else {
-            const int r = e - (ny > 1 ? 2 * nx : nx);
-            if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
-            else { y = 1 + r; x = 0; }
-        }
-        R s[9];
-        post_stream_node<S, R>(C, K.src, x, y, s);
-        R Fx = K.gfx, Fy = K.gfy;
-        if (K.nbodies > 0) add_ib<R>(C, x, y, s, Fx, Fy);
-        const R rho = collide<R, -1>(K.P, s, Fx, Fy);
-        if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
-        S* d = K.dst + ((long long)y * K.pitch + x);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+    K.load(L.cases[ch.c]);
+    const CaseDev& C = *K.C;
+    const int nx = K.nx, ny = K.ny;
+    const int e = ch.first + (int)threadIdx.x;
+    if (e >= ch.end) return;
+    int x, y;
+    if (e < nx) {
+        x = e; y = 0;
+    } else if (ny > 1 && e < 2 * nx) {
+        x = e - nx; y = ny - 1;
+    } else {
+        const int r = e - (ny > 1 ? 2 * nx : nx);
+        if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
+        else { y = 1 + r; x = 0; }
     }
+    R s[9];
+    post_stream_node<S, R>(C, K.src, x, y, s);
+    R Fx = K.gfx, Fy = K.gfy;
+    if (K.nbodies > 0) add_ib<R>(C, x, y, s, Fx, Fy);
+    const R rho = collide<R, -1>(K.P, s, Fx, Fy);
+    if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+    S* d = K.dst + ((long long)y * K.pitch + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1409,12 +1399,12 @@ bool sc_variant_ok(int variant, const void* f0, const void* f1) {
     return variant != SC_BULK || (((uintptr_t)f0 | (uintptr_t)f1) & 15u) == 0;
 }
 
-cudaError_t launch_edges(int storage, const ScLaunch& L, long long total, int grid, cudaStream_t st) {
-    if (total <= 0) return cudaSuccess;
+cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st) {
+    if (L.nchunks <= 0) return cudaSuccess;
     switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, grid, kThreads, st, L, total); break;
-    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, grid, kThreads, st, L, total); break;
-    default: IBLBM_LAUNCH(edge_kernel<__half>, grid, kThreads, st, L, total); break;
+    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, L.nchunks, kThreads, st, L); break;
+    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, L.nchunks, kThreads, st, L); break;
+    default: IBLBM_LAUNCH(edge_kernel<__half>, L.nchunks, kThreads, st, L); break;
     }
     return cudaGetLastError();
 }

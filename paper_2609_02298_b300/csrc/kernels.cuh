@@ -46,9 +46,18 @@ cudaError_t launch_stream_collide(int storage, int collision, int variant, const
                                   int grid, cudaStream_t st);
 int sc_segment(int storage, int variant);
 bool sc_variant_ok(int variant, const void* f0, const void* f1);   // alignment a variant needs
-// Lattice-edge nodes of every case in L (job_off = prefix sums of lattice_edge_nodes);
-// launched after the stream-collide launches of the step.
-cudaError_t launch_edges(int storage, const ScLaunch& L, long long total, int grid, cudaStream_t st);
+// Lattice-edge nodes: chunk k covers edge nodes [first, end) of case c (at most
+// kThreads of them); launched after the stream-collide launches of the step.
+struct EdgeChunk {
+    int c, first, end, pad_;
+};
+struct EdgeLaunch {
+    CaseDev** cases;
+    EdgeChunk* chunks;
+    int nchunks;
+    int pad_;
+};
+cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
 cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st);   // 0 prepare, 1 finish
