@@ -374,10 +374,21 @@ __host__ __device__ inline long long edge_count(int nx, int ny) {
 template <class S>
 __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     using R = typename Traits<S>::R;
-    const EdgeChunk ch = L.chunks[blockIdx.x];   // one CTA per 256 edge nodes of one case
+    // one CTA per 256 edge nodes of one case; the case record is staged in shared
+    // memory so the boundary logic reads it without global round trips
+    __shared__ __align__(16) CaseDev sc;
+    const EdgeChunk ch = L.chunks[blockIdx.x];
+    const CaseDev* gc = L.cases[ch.c];
+    {
+        static_assert(sizeof(CaseDev) % 4 == 0, "case record copied as words");
+        const int* from = reinterpret_cast<const int*>(gc);
+        int* to = reinterpret_cast<int*>(&sc);
+        for (int w = threadIdx.x; w < (int)(sizeof(CaseDev) / 4); w += kThreads) to[w] = from[w];
+    }
+    __syncthreads();
     ScCase<S> K;
-    K.load(L.cases[ch.c]);
-    const CaseDev& C = *K.C;
+    K.load(&sc);
+    const CaseDev& C = sc;
     const int nx = K.nx, ny = K.ny;
     const int e = ch.first + (int)threadIdx.x;
     if (e >= ch.end) return;
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     R Fx = K.gfx, Fy = K.gfy;
     if (K.nbodies > 0) add_ib<R>(C, x, y, s, Fx, Fy);
     const R rho = collide<R, -1>(K.P, s, Fx, Fy);
-    if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+    if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
     S* d = K.dst + ((long long)y * K.pitch + x);
 #pragma unroll
     for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
