@@ -35,6 +35,13 @@ import workloads as W  # noqa: E402
 METRIC = "MLUPS & % of HBM peak per IB-LBM step; batched cases/s with p50/p99 latency"
 UNIT = "MLUPS"
 BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
+# DRAM bytes (read + write) per node of one FP32 stream-collide launch, by (variant,
+# operator), and per lattice of the edge launch, from the ncu section captures summarised in
+# profiles/sweep_matrix36_f32.md (12-lattice case, scaled by nodes).  A sweep whose kernels
+# have no entry here (or changed since) reports traffic null.
+SWEEP_DRAM_BYTES_PER_NODE = {(1, W.BGK): 558.71e6 / 8388608, (1, W.TRT): 560.55e6 / 8388608,
+                             (1, W.CMMRT): 560.39e6 / 8388608}
+EDGE_DRAM_BYTES_PER_LATTICE = 29.82e6 / 12
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
 
 
@@ -59,6 +66,21 @@ def sweep_name(L, storage) -> str:
         v = L.kernel_variant(storage, col)[0]
         parts.append("%s:%s" % (name, VARIANT_KERNELS.get(v, "untuned")))
     return "stream-collide sweep (%s) + edge_kernel" % ", ".join(parts)
+
+
+def sweep_traffic(L, specs):
+    """Measured DRAM bytes of one sweep (all stream-collide launches + edge launch) for the
+    tuned kernels, or None when a tuned kernel has no capture."""
+    if any(s.storage != W.F32 for s in specs):
+        return None
+    total = 0.0
+    for s in specs:
+        v = L.kernel_variant(s.storage, s.collision)[0]
+        bpn = SWEEP_DRAM_BYTES_PER_NODE.get((v, s.collision))
+        if bpn is None:
+            return None
+        total += bpn * s.nodes + EDGE_DRAM_BYTES_PER_LATTICE
+    return total
 
 
 def launches_per_step(specs) -> int:
@@ -452,7 +474,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_fraction": (value * 1e6 * BYTES_PER_LU[storage] / (peak * 1e9)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": sweep_traffic(L, specs), "traffic_per": "step (sweep launches)",
                          "peak_kind": peak_kind, "kernel": sweep_name(L, storage),
                          "bytes_per_step": alg_bytes, "launches": sc_n,
                          "launches_per_step": sc_n / args.steps, "avg_launch_ms": sc_avg_s * 1e3,
