@@ -660,35 +660,50 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
 // ------------------------------------------------------------------------------------------
 // Block helpers (fixed-order reductions so results do not depend on timing).
 constexpr int kIbThreads = 512;   // threads of the per-body IB CTA
+// Warp butterflies, then one warp over the warp results: a fixed combination
+// order for any timing, two block barriers instead of one per tree level.
 __device__ __forceinline__ double block_max(double v, double* sh) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0) sh[w] = v;
     __syncthreads();
-    sh[t] = v;
-    __syncthreads();
-    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
-        if (t < s) sh[t] = fmax(sh[t], sh[t + s]);
-        __syncthreads();
+    if (w == 0) {
+        double u = lane < kIbThreads / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+        if (lane == 0) sh[kIbThreads / 32] = u;
     }
-    const double r = sh[0];
     __syncthreads();
-    return r;
+    return sh[kIbThreads / 32];
 }
-// Three sums in one pass of a fixed-order pairwise tree (deterministic).
+// Three sums, same scheme (fixed butterfly order: deterministic).
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
-    const int t = threadIdx.x;
-    __syncthreads();
-    sh[t] = a; sh[kIbThreads + t] = b; sh[2 * kIbThreads + t] = c;
-    __syncthreads();
-    for (int s = kIbThreads / 2; s > 0; s >>= 1) {
-        if (t < s) {
-            sh[t] += sh[t + s];
-            sh[kIbThreads + t] += sh[kIbThreads + t + s];
-            sh[2 * kIbThreads + t] += sh[2 * kIbThreads + t + s];
-        }
-        __syncthreads();
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    constexpr int NW = kIbThreads / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    a = sh[0]; b = sh[kIbThreads]; c = sh[2 * kIbThreads];
     __syncthreads();
+    if (lane == 0) { sh[w] = a; sh[NW + w] = b; sh[2 * NW + w] = c; }
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < NW ? sh[lane] : 0.0, y = lane < NW ? sh[NW + lane] : 0.0,
+               z = lane < NW ? sh[2 * NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) { sh[3 * NW] = x; sh[3 * NW + 1] = y; sh[3 * NW + 2] = z; }
+    }
+    __syncthreads();
+    a = sh[3 * NW]; b = sh[3 * NW + 1]; c = sh[3 * NW + 2];
 }
 __device__ __forceinline__ int block_min_i(int v, int* sh) {
     const int t = threadIdx.x;
@@ -847,10 +862,12 @@ __device__ __forceinline__ void marker_stencil(const BodyDev& B, const R* wts, i
 }
 
 constexpr int kSpreadChunk = 8;   // CSR entries whose loads are issued together
+constexpr int kMdfNodeCap = 2048; // footprint nodes whose MDF iterate fits in shared memory
 
 // Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
 template <class S, int SX>
-__device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd) {
+__device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
+                                       typename Traits<S>::R* sU, typename Traits<S>::R* sF) {
     using R = typename Traits<S>::R;
     constexpr int SS = SX * SX;
     const CaseDev& C = *ref.c;
@@ -982,9 +999,89 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             B.Fx[k] = (double)Fx;
             B.Fy[k] = (double)Fy;
         }
+    } else if (scheme == SCH_MDF && n <= kIbThreads && nfp <= kMdfNodeCap) {
+        // Eqs. 12-14 as below, with each thread holding one marker's stencil, density
+        // and running force in registers, the iterate u^(n) at the footprint nodes in
+        // shared memory (sU) and F^(n) per marker in shared memory (sF): after the first
+        // pass an iteration reads no global memory except L1-resident index data.
+        const R om = R(B.st.mdf_omega);
+        const bool own = tid < n;
+        int sl[SS];
+        R D[SS];
+        R rk = R(0), Fxt = R(0), Fyt = R(0);
+        double udx = 0.0, udy = 0.0;
+        if (own) {
+            marker_stencil<SX, R>(B, wts, tid, sl, D);
+#pragma unroll
+            for (int q = 0; q < SS; ++q) rk += fp[(size_t)sl[q] * 9] * D[q];
+            udx = B.Udx[tid];
+            udy = B.Udy[tid];
+        }
+        for (int q = tid; q < nfp; q += kIbThreads) {
+            sU[2 * q] = fp[(size_t)q * 9 + 3];
+            sU[2 * q + 1] = fp[(size_t)q * 9 + 4];
+        }
+        __syncthreads();
+        int applied = 0;
+        double rprev = 0.0, r = 0.0;
+        bool guard = false, tol_met = false;
+        for (int it = 1; it <= B.mdf_nmax; ++it) {
+            double e = 0.0;
+            R Fx = R(0), Fy = R(0);
+            if (own) {
+                R Ux = R(0), Uy = R(0);
+#pragma unroll
+                for (int q = 0; q < SS; ++q) {
+                    Ux += sU[2 * sl[q]] * D[q];
+                    Uy += sU[2 * sl[q] + 1] * D[q];
+                }
+                const double dx = udx - (double)Ux, dy = udy - (double)Uy;
+                e = sqrt(dx * dx + dy * dy);
+                Fx = R(2) * rk * (R(udx) - Ux);   // Eq. 13
+                Fy = R(2) * rk * (R(udy) - Uy);
+                sF[2 * tid] = Fx;
+                sF[2 * tid + 1] = Fy;
+            }
+            r = block_max(e, shd);   // also publishes sF
+            if (applied >= B.mdf_nmin && r < B.mdf_tol) { tol_met = true; break; }
+            if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
+            for (int q = tid; q < nfp; q += kIbThreads) {
+                R sx = R(0), sy = R(0);
+                const int o1 = B.csr_off[q + 1];
+                for (int o = B.csr_off[q]; o < o1; ++o) {
+                    const int k = B.csr_ent[o] / SS;
+                    const R d = cw[o];
+                    sx += sF[2 * k] * d * ds;
+                    sy += sF[2 * k + 1] * d * ds;
+                }
+                const R rho = fp[(size_t)q * 9];
+                sU[2 * q] += om / (R(2) * rho) * sx;   // Eq. 14 with the node density
+                sU[2 * q + 1] += om / (R(2) * rho) * sy;
+            }
+            Fxt += om * Fx;
+            Fyt += om * Fy;
+            __syncthreads();
+            rprev = r;
+            ++applied;
+        }
+        if (own) {
+            mk[tid * 16 + 0] = Fxt;
+            mk[tid * 16 + 1] = Fyt;
+            B.Fx[tid] = (double)Fxt;
+            B.Fy[tid] = (double)Fyt;
+        }
+        if (tid == 0) {
+            B.st.mdf_iters = applied;
+            B.st.mdf_res = r;
+            if (guard || (!tol_met && B.mdf_nmax > B.mdf_nmin)) {
+                B.status |= STAT_MDF_WARN;
+                atomicOr(const_cast<unsigned*>(&C.status), STAT_MDF_WARN);
+            }
+        }
     } else if (scheme == SCH_MDF) {
         // Eqs. 12-14: at least N_min increments; tolerance and 1.5x guard are
         // tested on U^(n) before increment n; a diverging iterate is not applied.
+        // (Bodies with more markers than threads or footprints above kMdfNodeCap.)
         const R om = R(B.st.mdf_omega);
         for (int k = tid; k < n; k += kIbThreads) {
             int sl[SS];
@@ -1159,11 +1256,14 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
 template <class S>
 __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     const BodyRef ref = L.refs[blockIdx.x];
+    using R = typename Traits<S>::R;
     __shared__ int shi[2 * kIbThreads + 4];
-    __shared__ double shd[3 * kIbThreads];
+    __shared__ double shd[4 * (kIbThreads / 32) + 4];
+    __shared__ R sU[2 * kMdfNodeCap];
+    __shared__ R sF[2 * kIbThreads];
     if (ref.b->nfp < 0) return;
-    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd);
-    else ib_run<S, 4>(L, ref, shi, shd);
+    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF);
+    else ib_run<S, 4>(L, ref, shi, shd, sU, sF);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -71,6 +71,11 @@ inline T __shfl_down_sync(unsigned, T v, unsigned d) {
     const int src = lane + (int)d;
     return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src > 31 ? lane : src));
 }
+template <class T>
+inline T __shfl_xor_sync(unsigned, T v, int mask) {
+    const int lane = (int)(threadIdx.x & 31u);
+    return emu_from_bits<T>(emu::exchange(emu_to_bits(v), lane ^ mask));
+}
 inline int __any_sync(unsigned, int pred) { return emu::any(pred); }
 inline void __syncwarp(unsigned = 0xffffffffu) { emu::any(0); }
 

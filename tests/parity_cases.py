@@ -215,6 +215,19 @@ def check_f16_storage(steps=300, nx=200):
 
 
 # ---------------------------------------------------------------- moving bodies
+def check_mdf_large_body_f64(kernel, nx=260, ny=240, D=180.0, n=566, steps=3):
+    """MDF body with more markers than the IB CTA's threads (and, for Peskin, more
+    footprint nodes than its shared-memory iterate holds): the global-memory MDF path."""
+    body = cylinder_body(0.5 * nx + 0.3, 0.5 * ny + 0.1, D, n, kernel, W.MDF, mdf_nmin=3, mdf_nmax=3)
+    spec = channel_spec(nx, ny, collision=W.BGK, tau=0.8, storage=W.F64, u=0.03, bodies=[body])
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.03)
+    Fg, Fc = g.body_forces(0), c.body_forces(0)
+    assert np.abs(Fg - Fc).max() < 1e-12 * np.abs(Fc[:2]).max()
+    assert g.mdf_info(0)[0] == c.mdf_iterations(0) == 3
+
+
 def check_prescribed_oscillation_f64(nx=128, ny=96, D=16.0, steps=120):
     spec = W.oscillating_cylinder(storage=W.F64, kernel=W.PESKIN4, scheme=W.DF, nx=nx, ny=ny, diameter=D,
                                   kc=5.0, u_max=0.05, re=60.0)

@@ -123,6 +123,12 @@ def test_ib_channel_f64(L, scheme, kernel, collision):
     P.check_ib_channel_f64(scheme, kernel, collision, nx=36, ny=24, D=8.0, n=23, steps=3)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mdf_large_body_f64(L, kernel):
+    full_only(L)
+    P.check_mdf_large_body_f64(kernel, steps=1)
+
+
 def test_prescribed_oscillation_f64(L):
     full_only(L)
     P.check_prescribed_oscillation_f64(nx=40, ny=24, D=8.0, steps=4)

@@ -92,6 +92,11 @@ def test_f16_storage_within_roundoff_bound():
     P.check_f16_storage()
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mdf_large_body_f64(kernel):
+    P.check_mdf_large_body_f64(kernel)
+
+
 def test_prescribed_oscillation_f64():
     P.check_prescribed_oscillation_f64()
 
