@@ -300,6 +300,19 @@ def single_case_report(L, torch, steps=2000):
     return out
 
 
+def workload_config(specs, world=1):
+    """The `config` object both arms print for the same workload."""
+    nx, ny = specs[0].nx, specs[0].ny
+    nodes = sum(s.nodes for s in specs)
+    return {"workload": ("fixed-cylinder matrix %dx%d, D=%g, %d markers: Re {100,200} x "
+                         "{DF, MDF(5), DFC} x {hat, P4} x {BGK, TRT, CM-MRT}" %
+                         (nx, ny, specs[0].bodies[0].radius * 2, len(specs[0].bodies[0].xy))),
+            "lattices": len(specs), "nodes_per_step": nodes, "storage": "f32 shifted",
+            "l2": "populations %.1f GB (A/B buffers) > 126 MB L2, no flush"
+                  % (BYTES_PER_LU[specs[0].storage] * nodes / 1e9),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args, specs):
     """--impl reference: the oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -320,10 +333,11 @@ def run_reference(args, specs):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_time / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": spec.name + " (one lattice of the 2048x1024 matrix)", "lattices": 1,
-                       "scheme": "DF", "kernel": "hat", "collision": "BGK", "storage": "f64"},
+            "config": workload_config(specs),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step = %.0f s of oracle steps on one 2048x1024 lattice" % args.ref_budget},
+                             "sample": "each step = %.1f s of FP64 oracle steps on one %dx%d lattice of the "
+                                       "matrix (%s), scaled to lattice updates per second"
+                                       % (args.ref_budget, spec.nx, spec.ny, spec.name)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -466,12 +480,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
-            "config": {"workload": ("fixed-cylinder matrix %dx%d, D=%g, %d markers: Re {100,200} x "
-                                    "{DF, MDF(5), DFC} x {hat, P4} x {BGK, TRT, CM-MRT}" %
-                                    (nx, ny, specs[0].bodies[0].radius * 2, len(specs[0].bodies[0].xy))),
-                       "lattices": len(specs), "nodes_per_step": nodes, "storage": "f32 shifted",
-                       "l2": "working set %.1f GB > 126 MB L2, no flush" % (2 * alg_bytes / 2 / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(specs, world),
             "hbm_fraction": (value * 1e6 * BYTES_PER_LU[storage] / (peak * 1e9)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,

@@ -52,3 +52,24 @@ def test_single_rank_aggregate():
     import bench
     value, ms = bench.aggregate(2048 * 1024, 100, 50.0)
     assert ms == 50.0 and value == pytest.approx(2048 * 1024 * 100 / 0.05 / 1e6)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """--impl reference: rank 0 times the oracle and prints one line; other ranks exit 0 silently."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--small", "--steps", "1",
+           "--warmup", "1", "--ref-budget", "0.2"]
+    for rank, expect_line in (("1", False), ("0", True)):
+        env = dict(os.environ, RANK=rank, WORLD_SIZE="2")
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
+        assert out.returncode == 0, out.stderr
+        lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+        if expect_line:
+            assert len(lines) == 1
+            rec = json.loads(lines[0])
+            assert rec["impl"] == "reference" and rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
+        else:
+            assert lines == []
