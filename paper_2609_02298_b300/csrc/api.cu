@@ -713,6 +713,7 @@ struct BatchGroup {
     CaseDev** dcases = nullptr;
     long long jobs[SC_VARIANTS] = {};          // per kernel variant (segment widths differ)
     int grid[SC_VARIANTS] = {};
+    int block[SC_VARIANTS] = {};               // scalar variants: threads per CTA (0: default)
     long long* djob[SC_VARIANTS] = {};
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
     int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
@@ -742,6 +743,7 @@ struct EdgeGroup {
     CaseDev** dcases = nullptr;
     EdgeChunk* dchunks = nullptr;
     int nchunks = 0;
+    int block = 0;                             // edge nodes per chunk = threads per CTA
 };
 
 struct BatchPlan {
@@ -787,7 +789,7 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         const int chosen = g_variant[g.storage][g.collision][g.size_class];
         int v = chosen < 0 ? SC_SCALAR : chosen;
         if (!g.ok[v]) v = SC_SCALAR;
-        ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
+        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v]};
         cudaEvent_t a = nullptr, b = nullptr;
         if (timer) {
             a = pool_event(timer);
@@ -802,7 +804,7 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         }
     }
     for (auto& g : P->edge_groups) {
-        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, 0};
+        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block};
         cudaEvent_t a = nullptr, b = nullptr;
         if (timer) {
             a = pool_event(timer);
@@ -859,11 +861,19 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             eg.storage = st;
             std::vector<CaseDev*> cs;
             std::vector<EdgeChunk> chunks;
+            // chunk size: kThreads nodes, smaller when that would leave SMs idle (the edge
+            // work of one small lattice is compute-bound in FP64 and should spread out)
+            long long total = 0;
+            for (int i = 0; i < n; ++i)
+                if (ctxs[i]->hc.storage == st) total += lattice_edge_nodes(ctxs[i]->hc.nx, ctxs[i]->hc.ny);
+            int chunk = (int)std::min<long long>(kThreads, (total + 2LL * sms - 1) / (2LL * sms));
+            chunk = std::max(32, (chunk + 31) / 32 * 32);
+            eg.block = chunk;
             for (int i = 0; i < n; ++i) {
                 iblbm_ctx* c = ctxs[i];
                 if (c->hc.storage != st) continue;
                 const int ne = (int)lattice_edge_nodes(c->hc.nx, c->hc.ny);
-                for (int f = 0; f < ne; f += kThreads) chunks.push_back(EdgeChunk{(int)cs.size(), f, std::min(ne, f + kThreads), 0});
+                for (int f = 0; f < ne; f += chunk) chunks.push_back(EdgeChunk{(int)cs.size(), f, std::min(ne, f + chunk), 0});
                 cs.push_back(c->dc);
             }
             if (!cs.empty()) {
@@ -911,8 +921,13 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 g.djob[v] = static_cast<long long*>(plan_alloc(P, sizeof(long long) * off.size()));
                 if (!g.djob[v]) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
                 cudaMemcpyAsync(g.djob[v], off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
-                g.grid[v] = (int)std::max<long long>(
-                    1, std::min<long long>((g.jobs[v] + 7) / 8, (long long)sms * sc_blocks_per_sm(st, col, v)));
+                const long long cap = (long long)sms * sc_blocks_per_sm(st, col, v);
+                g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 7) / 8, cap));
+                if ((v == SC_SCALAR || v == SC_SCALAR2) && (g.jobs[v] + 7) / 8 < sms) {
+                    // too few jobs to give every SM a 256-thread CTA: spread 64-thread CTAs
+                    g.block[v] = 64;
+                    g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
+                }
             }
             P->groups.push_back(g);
         }
@@ -944,7 +959,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 g_variant_ms[g.storage][g.collision][g.size_class][v] = 0.0;
                 continue;
             }
-            ScLaunch sl{g.dcases, g.djob[v], g.ncases, 0};
+            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v]};
             float ms = 0.f, tot = 0.f;
             launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);   // warm
             for (int r = 0; r < 3; ++r) {

@@ -323,7 +323,7 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
 }
 
-template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = NPT == 1 ? 4 : 3; };
+template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = 4; };
 template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
 // Dense job order: warp w takes jobs w, w + W, w + 2W, ... (W warps in the grid),
@@ -333,8 +333,8 @@ template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * kThreads) >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
     int nseg = 1;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
         static_assert(sizeof(CaseDev) % 4 == 0, "case record copied as words");
         const int* from = reinterpret_cast<const int*>(gc);
         int* to = reinterpret_cast<int*>(&sc);
-        for (int w = threadIdx.x; w < (int)(sizeof(CaseDev) / 4); w += kThreads) to[w] = from[w];
+        for (int w = threadIdx.x; w < (int)(sizeof(CaseDev) / 4); w += blockDim.x) to[w] = from[w];
     }
     __syncthreads();
     ScCase<S> K;
@@ -1427,8 +1427,9 @@ static int grid_for(long long work) {
 
 template <class S, int KIND>
 static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
-    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1>), grid, kThreads, st, L, jobs);
-    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2>), grid, kThreads, st, L, jobs);
+    const int block = L.block > 0 ? L.block : kThreads;
+    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1>), grid, block, st, L, jobs);
+    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2>), grid, block, st, L, jobs);
     else if (variant == SC_BULK) {
         static const cudaError_t attr =
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
@@ -1512,10 +1513,11 @@ bool sc_variant_ok(int variant, const void* f0, const void* f1) {
 
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st) {
     if (L.nchunks <= 0) return cudaSuccess;
+    const int block = L.block > 0 ? L.block : kThreads;
     switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, L.nchunks, kThreads, st, L); break;
-    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, L.nchunks, kThreads, st, L); break;
-    default: IBLBM_LAUNCH(edge_kernel<__half>, L.nchunks, kThreads, st, L); break;
+    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, L.nchunks, block, st, L); break;
+    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, L.nchunks, block, st, L); break;
+    default: IBLBM_LAUNCH(edge_kernel<__half>, L.nchunks, block, st, L); break;
     }
     return cudaGetLastError();
 }

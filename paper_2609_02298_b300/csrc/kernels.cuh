@@ -20,7 +20,7 @@ struct ScLaunch {
     CaseDev** cases;
     long long* job_off;
     int ncases;
-    int pad_;
+    int block;   // threads per CTA for the scalar variants (0: kThreads)
 };
 
 struct IbLaunch {
@@ -47,7 +47,7 @@ cudaError_t launch_stream_collide(int storage, int collision, int variant, const
 int sc_segment(int storage, int variant);
 bool sc_variant_ok(int variant, const void* f0, const void* f1);   // alignment a variant needs
 // Lattice-edge nodes: chunk k covers edge nodes [first, end) of case c (at most
-// kThreads of them); launched after the stream-collide launches of the step.
+// L.block of them); launched after the stream-collide launches of the step.
 struct EdgeChunk {
     int c, first, end, pad_;
 };
@@ -55,7 +55,7 @@ struct EdgeLaunch {
     CaseDev** cases;
     EdgeChunk* chunks;
     int nchunks;
-    int pad_;
+    int block;   // threads per CTA: the chunk size, a multiple of 32 up to kThreads
 };
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
