@@ -111,6 +111,18 @@ def _close_all():
             pass
 
 
+def _host_buffer(obj):
+    """(address, bytes) of a contiguous host buffer: numpy array or CPU torch tensor."""
+    if hasattr(obj, "data_ptr"):
+        if obj.device.type != "cpu" or not obj.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return obj.data_ptr(), obj.numel() * obj.element_size()
+    arr = np.asarray(obj)
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous array")
+    return arr.ctypes.data, arr.nbytes
+
+
 def load_library(path: str = LIB_PATH):
     """Loads libiblbm.so (building it first if the sources are newer); raises if absent."""
     global _lib
@@ -320,17 +332,36 @@ class Lattice:
         _check(load_library().iblbm_get_macro(self._h, _dp(r), _dp(ux), _dp(uy)), "iblbm_get_macro")
         return r, ux, uy
 
-    def snapshot(self) -> bytes:
+    def snapshot_bytes(self) -> int:
+        """Size of a checkpoint of this lattice."""
+        n = C.c_size_t(0)
+        _check(load_library().iblbm_snapshot(self._h, None, 0, C.byref(n)), "iblbm_snapshot")
+        return n.value
+
+    def snapshot(self, out=None):
+        """Checkpoint to host memory: a new ``bytes`` object, or written into ``out``
+        (a uint8 numpy array or CPU torch tensor, e.g. pinned, of at least
+        ``snapshot_bytes()`` bytes), which is then returned."""
         n = C.c_size_t(0)
         lib = load_library()
-        _check(lib.iblbm_snapshot(self._h, None, 0, C.byref(n)), "iblbm_snapshot")
-        buf = C.create_string_buffer(n.value)
-        _check(lib.iblbm_snapshot(self._h, buf, n.value, C.byref(n)), "iblbm_snapshot")
-        return buf.raw
+        if out is None:
+            size = self.snapshot_bytes()
+            buf = C.create_string_buffer(size)
+            _check(lib.iblbm_snapshot(self._h, buf, size, C.byref(n)), "iblbm_snapshot")
+            return buf.raw
+        ptr, size = _host_buffer(out)
+        _check(lib.iblbm_snapshot(self._h, C.c_void_p(ptr), size, C.byref(n)), "iblbm_snapshot")
+        return out
 
-    def restore(self, blob: bytes) -> None:
-        buf = C.create_string_buffer(blob, len(blob))
-        _check(load_library().iblbm_restore(self._h, buf, len(blob)), "iblbm_restore")
+    def restore(self, blob) -> None:
+        """Restore a checkpoint from ``bytes`` or from a host buffer as accepted by
+        ``snapshot(out=...)`` (read in place: a pinned buffer is copied by DMA)."""
+        if isinstance(blob, (bytes, bytearray)):
+            buf = C.create_string_buffer(bytes(blob), len(blob))
+            _check(load_library().iblbm_restore(self._h, buf, len(blob)), "iblbm_restore")
+            return
+        ptr, size = _host_buffer(blob)
+        _check(load_library().iblbm_restore(self._h, C.c_void_p(ptr), size), "iblbm_restore")
 
     def set_timing(self, enable: bool) -> None:
         _check(load_library().iblbm_set_timing(self._h, 1 if enable else 0), "iblbm_set_timing")

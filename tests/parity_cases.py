@@ -319,13 +319,17 @@ def check_snapshot_restore(nx=64, ny=160, D=12.0, steps=(40, 30)):
     a = gpu_case(spec)
     a.step(steps[0])
     blob = a.snapshot()
+    arr = a.snapshot(out=np.empty(a.snapshot_bytes(), dtype=np.uint8))   # caller-owned buffer
+    assert arr.tobytes() == blob
     a.step(steps[1])
-    b = gpu_case(spec)
-    b.restore(blob)
-    b.step(steps[1])
-    np.testing.assert_array_equal(a.populations(shifted=True), b.populations(shifted=True))
-    np.testing.assert_array_equal(a.body_state(0), b.body_state(0))
-    np.testing.assert_array_equal(a.force_history(0), b.force_history(0))
+    for src in (blob, arr):
+        b = gpu_case(spec)
+        b.restore(src)
+        b.step(steps[1])
+        np.testing.assert_array_equal(a.populations(shifted=True), b.populations(shifted=True))
+        np.testing.assert_array_equal(a.body_state(0), b.body_state(0))
+        np.testing.assert_array_equal(a.force_history(0), b.force_history(0))
+        b.close()
 
 
 def check_graph_equals_direct(nx=150, ny=64, steps=33):
