@@ -275,6 +275,35 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
     return out
 
 
+def storage_report(L, torch, steps=20):
+    """The same 36-lattice matrix with FP16 and FP64 shifted storage: graph-replayed
+    steps timed with CUDA events, MLUPS and the fraction of the HBM bound at each
+    storage type's bytes per node (36 B FP16, 144 B FP64)."""
+    out = {}
+    peak, _ = read_peaks()
+    for name, st in (("f16", W.F16S), ("f64", W.F64)):
+        specs = matrix_specs(storage=st)
+        lats = [L.Lattice.from_spec(s) for s in specs]
+        nodes = sum(s.nodes for s in specs)
+        L.step_batch(lats, 3)
+        for l in lats:
+            l.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        L.step_batch(lats, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        rc = max(l.sync() for l in lats)
+        for l in lats:
+            l.close()
+        mlups = nodes * steps / (ms / 1e3) / 1e6
+        out[name] = {"mlups": mlups, "ms_per_step": ms / steps, "steps": steps, "status": rc,
+                     "hbm_fraction": mlups * 1e6 * BYTES_PER_LU[st] / (peak * 1e9)}
+    return out
+
+
 def single_case_report(L, torch, steps=2000):
     """One lattice stepped alone (graph-replayed iblbm_step): the 200x100 Re=20
     cylinder (DF, hat, BGK) in FP64 and FP32, and one 2048x1024 lattice of the
@@ -466,6 +495,12 @@ def main():
             single = single_case_report(L, torch)
         except Exception as exc:
             single = {"error": repr(exc)}
+    storages = None
+    if rank == 0 and args.serving_requests > 0 and not args.small:
+        try:
+            storages = storage_report(L, torch)
+        except Exception as exc:
+            storages = {"error": repr(exc)}
     serving = None
     if rank == 0 and args.serving_requests > 0 and not args.small:
         try:
@@ -502,6 +537,7 @@ def main():
             "clocks": clocks.summary(),
             "device_status": rc,
             "single_lattice": single,
+            "other_storage": storages,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

@@ -86,6 +86,7 @@ inline void fence_bar_init() {}
 inline void bar_arrive_tx(uint64_t* bar, unsigned bytes) { emu_bar_update(bar, 1, (int)bytes); }
 inline void bar_arrive(uint64_t* bar) { emu_bar_update(bar, 1, 0); }
 inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    if (emu::drop_bulk_copies()) return;   // test hook: a copy that never lands
     std::memcpy(dst, src, bytes);
     emu_bar_update(bar, 0, -(int)bytes);
 }

@@ -446,7 +446,11 @@ template <class S> struct BulkGeom {
     static_assert((RS * (int)sizeof(S)) % 16 == 0, "staged rows must stay 16-byte aligned");
     static_assert(SMEM <= 113 * 1024, "two CTAs per SM must fit");
 };
+#ifndef IBLBM_EMULATE
 constexpr long kBulkSpinLimit = 1L << 22;   // polls of an mbarrier before the kernel gives up
+#else
+constexpr long kBulkSpinLimit = 1L << 16;   // host emulation: each poll yields the thread
+#endif
 
 __device__ __forceinline__ double lds1(const double* p) { return *p; }
 __device__ __forceinline__ float lds1(const float* p) { return *p; }

@@ -33,6 +33,7 @@ int any(int pred);
 void launch(dim3 grid, dim3 block, std::function<void()> body, cudaStream_t st);
 unsigned char* dyn_smem();   // dynamic shared memory of the running block (256 KB)
 void yield();
+bool drop_bulk_copies();   // IBLBM_EMU_DROP_BULK_COPIES=1: bulk copies never complete (test hook)
 }  // namespace emu
 
 #define threadIdx (emu::tc.tid)

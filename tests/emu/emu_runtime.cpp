@@ -165,6 +165,11 @@ unsigned char* dyn_smem() {
 
 void yield() { std::this_thread::yield(); }
 
+bool drop_bulk_copies() {
+    const char* v = std::getenv("IBLBM_EMU_DROP_BULK_COPIES");
+    return v && v[0] == '1';
+}
+
 }  // namespace emu
 
 // ---- runtime API --------------------------------------------------------------------------

@@ -169,3 +169,25 @@ def test_marker_out_of_domain_is_reported(L):
 def test_server_alone_vs_mix(L):
     full_only(L)
     P.check_server_alone_vs_mix(L, [(sp, 3) for sp, _ in P.serving_specs(scale=0.2)], max_steps=2)
+
+
+def test_bulk_copy_that_never_lands_reports_timeout(L, monkeypatch):
+    """Failure detection of the bulk-staged sweep, injected on the host: with the
+    emulated bulk copies dropped, every mbarrier wait runs out its bounded poll
+    count, the kernel returns with the timeout status instead of hanging, and the
+    library stays usable once copies land again."""
+    bulk_only(L)
+    spec = W.CaseSpec(name="t", nx=1600, ny=5, bc=(W.PERIODIC,) * 4, ubc=((0, 0),) * 4,
+                      collision=W.BGK, tau=0.8, storage=W.F32)
+    monkeypatch.setenv("IBLBM_EMU_DROP_BULK_COPIES", "1")
+    g = L.Lattice.from_spec(spec)
+    g.step(1)
+    with pytest.raises(L.IblbmError) as err:
+        g.sync()
+    assert err.value.code == -6   # IBLBM_ERR_TIMEOUT
+    g.close()
+    monkeypatch.delenv("IBLBM_EMU_DROP_BULK_COPIES")
+    h = L.Lattice.from_spec(spec)
+    h.step(2)
+    assert h.sync() == 0
+    h.close()
