@@ -60,7 +60,6 @@ struct BodyHost {
     int n = 0;
     int kernel = 0, scheme = 0, motion = 0;
     double xc = 0, yc = 0, reach = 0;   // centre and marker reach for overlap checks
-    double ymin = 0, ymax = 0;          // marker extent in y (rows a fixed body's IB can touch)
 };
 
 struct GraphSet {
@@ -388,11 +387,6 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     BodyHost bh;
     bh.n = n; bh.kernel = kernel; bh.scheme = scheme; bh.motion = bd->motion;
     bh.xc = bd->xc; bh.yc = bd->yc; bh.reach = reach;
-    bh.ymin = bh.ymax = xy[1];
-    for (int k = 1; k < n; ++k) {
-        bh.ymin = std::min(bh.ymin, xy[2 * k + 1]);
-        bh.ymax = std::max(bh.ymax, xy[2 * k + 1]);
-    }
     c->bodies.push_back(bh);
     c->hbodies.push_back(B);
     c->hc.nbodies = (int)c->bodies.size();
@@ -484,9 +478,6 @@ int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3])
         cudaMemcpy(b.Y, Y.data(), 8 * n, cudaMemcpyHostToDevice);
         b.cache_valid = 0;
         b.lam_valid = 0;
-        c->bodies[id].ymin = *std::min_element(Y.begin(), Y.end());
-        c->bodies[id].ymax = *std::max_element(Y.begin(), Y.end());
-        c->version += 1;   // batch plans split their rows by body extent: rebuild them
     }
     if (uvw) {
         b.st.vx = uvw[0];
@@ -726,17 +717,6 @@ struct BatchGroup {
     long long* djob[SC_VARIANTS] = {};
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
     int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
-    // Rows split in two launches (plans whose bodies are all fixed, scalar variants):
-    // `rest` = interior rows no footprint can reach, run while the IB stage runs;
-    // `band` = the remaining interior rows, run after it.
-    struct Part {
-        long long jobs = 0;
-        long long* djob = nullptr;
-        int* drows = nullptr;
-        long long* drowoff = nullptr;
-        int grid = 1, block = 0;
-    } rest, band;
-    int split_variant = -1;                    // variant the parts were built for (-1: none)
 };
 
 // Stream-collide variant per (storage, collision, size class), process-wide so
@@ -780,17 +760,10 @@ struct BatchPlan {
     cudaStream_t st = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> joins;
-    // overlap of the IB stage with the footprint-free rows (all bodies fixed)
-    bool split = false;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_ib = nullptr;
     ~BatchPlan() {
         graphs.reset();
         for (auto p : mem) dev_free(p, st);
         for (auto e : joins) cudaEventDestroy(e);
-        if (ev_fork) cudaEventDestroy(ev_fork);
-        if (ev_ib) cudaEventDestroy(ev_ib);
-        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -802,73 +775,33 @@ void* plan_alloc(BatchPlan* P, size_t b) {
     return p;
 }
 
-// One stream-collide launch, bracketed by timing events when a timer is given.
-cudaError_t timed_sc(int storage, int collision, int v, const ScLaunch& sl, long long jobs, int grid,
-                     cudaStream_t st, iblbm_ctx* timer) {
-    if (jobs <= 0) return cudaSuccess;
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (timer) {
-        a = pool_event(timer);
-        b = pool_event(timer);
-        cudaEventRecord(a, st);
-    }
-    cudaError_t e = launch_stream_collide(storage, collision, v, sl, jobs, grid, st);
-    if (e != cudaSuccess) return e;
-    if (timer) {
-        cudaEventRecord(b, st);
-        timer->ev_pending.push_back({a, b});
-    }
-    return cudaSuccess;
-}
-
-int group_variant(const BatchGroup& g) {
-    const int chosen = g_variant[g.storage][g.collision][g.size_class];
-    const int v = chosen < 0 ? SC_SCALAR : chosen;
-    return g.ok[v] ? v : SC_SCALAR;
-}
-
 cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     cudaError_t e = cudaSuccess;
     FinLaunch all{P->drefs_all, P->nrefs_all, (int)P->ctxs.size(), P->dcases_all};
-    // With every body fixed, rows no footprint can reach do not depend on the IB
-    // stage: they are swept on this stream while the IB stage runs on a side stream
-    // (launch by launch on one stream when timing).
-    const bool split = P->split && P->nrefs_all > 0;
-    cudaStream_t ibs = (split && !timer) ? P->side : st;
-    if (ibs != st) {
-        cudaEventRecord(P->ev_fork, st);
-        cudaStreamWaitEvent(ibs, P->ev_fork, 0);
-    }
     if (P->nrefs_all > 0) {
-        if ((e = launch_body(all, 0, ibs)) != cudaSuccess) return e;
+        if ((e = launch_body(all, 0, st)) != cudaSuccess) return e;
         for (auto& g : P->ib_groups) {
             IbLaunch il{g.drefs, g.nrefs, 0};
-            if ((e = launch_ib(g.storage, il, ibs)) != cudaSuccess) return e;
+            if ((e = launch_ib(g.storage, il, st)) != cudaSuccess) return e;
         }
-    }
-    if (split) {
-        for (auto& g : P->groups) {
-            const int v = group_variant(g);
-            if (g.split_variant != v) continue;
-            ScLaunch sl{g.dcases, g.rest.djob, g.ncases, g.rest.block, g.rest.drows, g.rest.drowoff, 1, 0};
-            if ((e = timed_sc(g.storage, g.collision, v, sl, g.rest.jobs, g.rest.grid, st, timer)) != cudaSuccess)
-                return e;
-        }
-    }
-    if (ibs != st) {
-        cudaEventRecord(P->ev_ib, ibs);
-        cudaStreamWaitEvent(st, P->ev_ib, 0);
     }
     for (auto& g : P->groups) {
-        const int v = group_variant(g);
-        if (split && g.split_variant == v) {
-            ScLaunch sl{g.dcases, g.band.djob, g.ncases, g.band.block, g.band.drows, g.band.drowoff, 0, 0};
-            e = timed_sc(g.storage, g.collision, v, sl, g.band.jobs, g.band.grid, st, timer);
-        } else {
-            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], nullptr, nullptr, 0, 0};
-            e = timed_sc(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st, timer);
+        const int chosen = g_variant[g.storage][g.collision][g.size_class];
+        int v = chosen < 0 ? SC_SCALAR : chosen;
+        if (!g.ok[v]) v = SC_SCALAR;
+        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v]};
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timer) {
+            a = pool_event(timer);
+            b = pool_event(timer);
+            cudaEventRecord(a, st);
         }
-        if (e != cudaSuccess) return e;
+        if ((e = launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st)) != cudaSuccess)
+            return e;
+        if (timer) {
+            cudaEventRecord(b, st);
+            timer->ev_pending.push_back({a, b});
+        }
     }
     for (auto& g : P->edge_groups) {
         EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block};
@@ -885,47 +818,6 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         }
     }
     return launch_body(all, 1, st);
-}
-
-// Row classes of one lattice for the split sweep: interior rows (1..ny-2) within
-// reach of a fixed body's markers form the band, the others the rest.
-void split_rows(const iblbm_ctx* c, std::vector<int>& rest, std::vector<int>& band) {
-    const int ny = c->hc.ny;
-    std::vector<char> in_band(ny, 0);
-    for (const auto& b : c->bodies) {
-        // stencil rows reach floor(Y) - 1 .. floor(Y) + 2; keep a margin of two more
-        const int lo = std::max(1, (int)std::floor(b.ymin) - 3), hi = std::min(ny - 2, (int)std::floor(b.ymax) + 4);
-        for (int y = lo; y <= hi; ++y) in_band[y] = 1;
-    }
-    for (int y = 1; y <= ny - 2; ++y) (in_band[y] ? band : rest).push_back(y);
-}
-
-// Device tables of one part (rows of every case of the group, jobs per row = segs).
-int build_part(BatchPlan* P, const std::vector<std::vector<int>>& rows, const std::vector<int>& nxs, int seg,
-               int cap, int sms, BatchGroup::Part& part) {
-    std::vector<int> flat;
-    std::vector<long long> rowoff{0}, joboff{0};
-    for (size_t i = 0; i < rows.size(); ++i) {
-        flat.insert(flat.end(), rows[i].begin(), rows[i].end());
-        rowoff.push_back((long long)flat.size());
-        joboff.push_back(joboff.back() + (long long)rows[i].size() * ((nxs[i] + seg - 1) / seg));
-    }
-    part.jobs = joboff.back();
-    part.djob = static_cast<long long*>(plan_alloc(P, sizeof(long long) * joboff.size()));
-    part.drowoff = static_cast<long long*>(plan_alloc(P, sizeof(long long) * rowoff.size()));
-    part.drows = static_cast<int*>(plan_alloc(P, sizeof(int) * std::max<size_t>(1, flat.size())));
-    if (!part.djob || !part.drowoff || !part.drows) return IBLBM_ERR_OOM;
-    cudaMemcpyAsync(part.djob, joboff.data(), sizeof(long long) * joboff.size(), cudaMemcpyHostToDevice, P->st);
-    cudaMemcpyAsync(part.drowoff, rowoff.data(), sizeof(long long) * rowoff.size(), cudaMemcpyHostToDevice, P->st);
-    if (!flat.empty())
-        cudaMemcpyAsync(part.drows, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, P->st);
-    part.grid = (int)std::max<long long>(1, std::min<long long>((part.jobs + 7) / 8, cap));
-    part.block = 0;
-    if ((part.jobs + 7) / 8 < sms) {
-        part.block = 64;
-        part.grid = (int)std::max<long long>(1, std::min<long long>((part.jobs + 1) / 2, 4LL * cap));
-    }
-    return IBLBM_OK;
 }
 
 BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
@@ -1087,44 +979,6 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         g_variant[g.storage][g.collision][g.size_class] = best;
-    }
-    // split sweep when every body is fixed: footprint-free rows overlap the IB stage
-    bool all_fixed = P->nrefs_all > 0;
-    for (int i = 0; i < n; ++i)
-        for (const auto& b : ctxs[i]->bodies) all_fixed = all_fixed && b.motion == MOT_FIXED;
-    if (all_fixed) {
-        for (auto& g : P->groups) {
-            const int v = group_variant(g);
-            if (v != SC_SCALAR && v != SC_SCALAR2) continue;
-            std::vector<std::vector<int>> rest, band;
-            std::vector<int> nxs;
-            for (int i = 0; i < n; ++i) {
-                iblbm_ctx* c = ctxs[i];
-                if (c->hc.storage != g.storage || c->hc.collision != g.collision) continue;
-                rest.emplace_back();
-                band.emplace_back();
-                split_rows(c, rest.back(), band.back());
-                nxs.push_back(c->hc.nx);
-            }
-            const int seg = sc_segment(g.storage, v);
-            const int cap = sms * sc_blocks_per_sm(g.storage, g.collision, v);
-            if (build_part(P, rest, nxs, seg, cap, sms, g.rest) || build_part(P, band, nxs, seg, cap, sms, g.band)) {
-                *rc = IBLBM_ERR_OOM;
-                delete P;
-                return nullptr;
-            }
-            g.split_variant = v;
-            P->split = true;
-        }
-        if (P->split) {
-            if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&P->ev_ib, cudaEventDisableTiming) != cudaSuccess) {
-                *rc = IBLBM_ERR_CUDA;
-                delete P;
-                return nullptr;
-            }
-        }
     }
     *rc = check(cudaStreamSynchronize(P->st));
     if (*rc) { delete P; return nullptr; }

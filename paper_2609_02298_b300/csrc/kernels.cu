@@ -284,14 +284,14 @@ __global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_ke
 // 32-bit element offsets with per-population constants; the Guo term only on rows
 // that carry a force.
 template <class S, int KIND, int NPT>
-__device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane, bool noib) {
+__device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane) {
     using R = typename Traits<S>::R;
     const CaseDev& C = *K.C;
     const S* __restrict__ src = K.src;
     S* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
-    const bool ib = !noib && K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
     const bool forced = ib || K.has_force;
     // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
     int koff[9];
@@ -338,7 +338,6 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
     int nseg = 1;
-    const int* rows = nullptr;
     for (long long job = gw; job < jobs; job += nw) {
         if (job >= c_hi || job < c_lo) {
             int lo = 0, hi = L.ncases - 1;
@@ -350,12 +349,10 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
             c_hi = L.job_off[lo + 1];
             K.load(L.cases[lo]);
             nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
-            rows = L.rowmap ? L.rowmap + L.rowoff[lo] : nullptr;
         }
-        const int local = (int)(job - c_lo);   // < rows of the case * nseg
-        const int r = local / nseg;
-        const int y = rows ? rows[r] : r;
-        sc_row_scalar<S, KIND, NPT>(K, y, (local - r * nseg) * 32 * NPT, lane, L.noib != 0);
+        const int local = (int)(job - c_lo);   // < ny * nseg
+        const int y = local / nseg;
+        sc_row_scalar<S, KIND, NPT>(K, y, (local - y * nseg) * 32 * NPT, lane);
     }
 }
 

@@ -21,13 +21,6 @@ struct ScLaunch {
     long long* job_off;
     int ncases;
     int block;   // threads per CTA for the scalar variants (0: kThreads)
-    // scalar variants only: when rowmap is set, case c's jobs cover the rows
-    // rowmap[rowoff[c] ..] in order (instead of rows 0..ny-1), and noib = 1 states
-    // that none of them meets a body footprint (no IB lookup is made)
-    const int* rowmap;
-    const long long* rowoff;
-    int noib;
-    int pad_;
 };
 
 struct IbLaunch {
