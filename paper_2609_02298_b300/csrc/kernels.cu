@@ -867,11 +867,18 @@ __device__ __forceinline__ void marker_stencil(const BodyDev& B, const R* wts, i
 
 constexpr int kSpreadChunk = 8;   // CSR entries whose loads are issued together
 constexpr int kMdfNodeCap = 2048; // footprint nodes whose MDF iterate fits in shared memory
+constexpr int kMdfEntryCap = 4096; // node->marker entries staged in shared memory for MDF
+// Dynamic shared memory of ib_kernel: sU (2 per node), sF (2 per marker), sEw (per
+// entry), then sEk (per entry, int).
+template <class R> struct IbSmem {
+    static constexpr int bytes = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap) * (int)sizeof(R) + kMdfEntryCap * 4;
+};
 
 // Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
 template <class S, int SX>
 __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
-                                       typename Traits<S>::R* sU, typename Traits<S>::R* sF) {
+                                       typename Traits<S>::R* sU, typename Traits<S>::R* sF,
+                                       typename Traits<S>::R* sEw, int* sEk) {
     using R = typename Traits<S>::R;
     constexpr int SS = SX * SX;
     const CaseDev& C = *ref.c;
@@ -956,12 +963,36 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
 
     // gather the post-streaming state at every footprint node
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
-    for (int q = tid; q < nfp; q += kIbThreads) {
-        const int node = B.fp_node[q];
-        const int x = bx0 + node % bw, y = B.by0 + node / bw;
-        R s[9];
-        post_stream_node<S, R>(C, src, x, y, s);
-        R* o = fp + (size_t)q * 9;
+    // GB footprint nodes per thread at a time: their pulls are issued together
+    // (interior nodes pull directly; nodes on a lattice edge take the domain conditions)
+    constexpr int GB = sizeof(R) == 8 ? 2 : 4;
+    const int by0 = B.by0, cnx = C.nx, cny = C.ny, cpitch = C.pitch;
+    const long long cplane = C.plane;
+    for (int q0 = tid; q0 < nfp; q0 += GB * kIbThreads) {
+        int gx[GB], gy[GB];
+        bool live[GB], inner[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const int q = q0 + u * kIbThreads;
+            live[u] = q < nfp;
+            const int node = live[u] ? B.fp_node[q] : 0;
+            gx[u] = bx0 + node % bw;
+            gy[u] = by0 + node / bw;
+            inner[u] = live[u] && gx[u] >= 1 && gx[u] <= cnx - 2 && gy[u] >= 1 && gy[u] <= cny - 2;
+        }
+        R sb[GB][9];
+#pragma unroll
+        for (int u = 0; u < GB; ++u)
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                sb[u][i] = inner[u] ? ld1(src + i * cplane + (long long)(gy[u] - ey(i)) * cpitch + (gx[u] - ex(i)))
+                                    : R(0);
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            if (!live[u]) continue;
+            if (!inner[u]) post_stream_node<S, R>(C, src, gx[u], gy[u], sb[u]);
+            const R* s = sb[u];
+            R* o = fp + (size_t)(q0 + u * kIbThreads) * 9;
         if (scheme == SCH_DFC) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i] = s[i];
@@ -980,9 +1011,20 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             o[3] = o[1];
             o[4] = o[2];
         }
+        }
     }
     __syncthreads();
 
+    // force and torque on the body (Sec. 2.7), accumulated in FP64 by each thread as its
+    // markers' forces are final (ascending k per thread), reduced at the end
+    double gxs = 0.0, gys = 0.0, ts = 0.0;
+    const double bxc = B.st.xc, byc = B.st.yc;
+    auto body_force = [&](int k, double gx, double gy) {
+        const double rx = B.X[k] - bxc, ry = B.Y[k] - byc;
+        gxs += gx;
+        gys += gy;
+        ts += rx * gy - ry * gx;
+    };
     if (scheme == SCH_DF) {
         // Eq. 7 on rho and u_raw, Eq. 11
         for (int k = tid; k < n; k += kIbThreads) {
@@ -1002,12 +1044,14 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             mk[k * 16 + 1] = Fy;
             B.Fx[k] = (double)Fx;
             B.Fy[k] = (double)Fy;
+            body_force(k, -(double)Fx * B.ds, -(double)Fy * B.ds);
         }
-    } else if (scheme == SCH_MDF && n <= kIbThreads && nfp <= kMdfNodeCap) {
+    } else if (scheme == SCH_MDF && n <= kIbThreads && nfp <= kMdfNodeCap && B.csr_off[nfp] <= kMdfEntryCap) {
         // Eqs. 12-14 as below, with each thread holding one marker's stencil, density
-        // and running force in registers, the iterate u^(n) at the footprint nodes in
-        // shared memory (sU) and F^(n) per marker in shared memory (sF): after the first
-        // pass an iteration reads no global memory except L1-resident index data.
+        // and running force in registers, the iterate u^(n) at the footprint nodes (sU),
+        // F^(n) per marker (sF) and the node->marker lists with their weights (sEk, sEw)
+        // in shared memory, and each thread's node list bounds and densities in
+        // registers: an iteration touches no global memory.
         const R om = R(B.st.mdf_omega);
         const bool own = tid < n;
         int sl[SS];
@@ -1024,6 +1068,20 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         for (int q = tid; q < nfp; q += kIbThreads) {
             sU[2 * q] = fp[(size_t)q * 9 + 3];
             sU[2 * q + 1] = fp[(size_t)q * 9 + 4];
+        }
+        for (int o = tid; o < B.csr_off[nfp]; o += kIbThreads) {
+            sEk[o] = B.csr_ent[o] / SS;
+            sEw[o] = cw[o] * ds;
+        }
+        constexpr int NQ = kMdfNodeCap / kIbThreads;   // footprint nodes per thread
+        int qo0[NQ], qo1[NQ];
+        R qc[NQ];                                       // omega / (2 rho(x))
+#pragma unroll
+        for (int u = 0; u < NQ; ++u) {
+            const int q = tid + u * kIbThreads;
+            qo0[u] = q < nfp ? B.csr_off[q] : 0;
+            qo1[u] = q < nfp ? B.csr_off[q + 1] : 0;
+            qc[u] = q < nfp ? om / (R(2) * fp[(size_t)q * 9]) : R(0);
         }
         __syncthreads();
         int applied = 0;
@@ -1049,18 +1107,20 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             r = block_max(e, shd);   // also publishes sF
             if (applied >= B.mdf_nmin && r < B.mdf_tol) { tol_met = true; break; }
             if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
-            for (int q = tid; q < nfp; q += kIbThreads) {
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                const int q = tid + u * kIbThreads;
                 R sx = R(0), sy = R(0);
-                const int o1 = B.csr_off[q + 1];
-                for (int o = B.csr_off[q]; o < o1; ++o) {
-                    const int k = B.csr_ent[o] / SS;
-                    const R d = cw[o];
-                    sx += sF[2 * k] * d * ds;
-                    sy += sF[2 * k + 1] * d * ds;
+                for (int o = qo0[u]; o < qo1[u]; ++o) {
+                    const int k = sEk[o];
+                    const R d = sEw[o];   // D(x - X_k) ds
+                    sx += sF[2 * k] * d;
+                    sy += sF[2 * k + 1] * d;
                 }
-                const R rho = fp[(size_t)q * 9];
-                sU[2 * q] += om / (R(2) * rho) * sx;   // Eq. 14 with the node density
-                sU[2 * q + 1] += om / (R(2) * rho) * sy;
+                if (q < nfp) {
+                    sU[2 * q] += qc[u] * sx;   // Eq. 14 with the node density
+                    sU[2 * q + 1] += qc[u] * sy;
+                }
             }
             Fxt += om * Fx;
             Fyt += om * Fy;
@@ -1073,6 +1133,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             mk[tid * 16 + 1] = Fyt;
             B.Fx[tid] = (double)Fxt;
             B.Fy[tid] = (double)Fyt;
+            body_force(tid, -(double)Fxt * B.ds, -(double)Fyt * B.ds);
         }
         if (tid == 0) {
             B.st.mdf_iters = applied;
@@ -1156,6 +1217,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             mk[k * 16 + 1] = mk[k * 16 + 4];
             B.Fx[k] = (double)mk[k * 16 + 3];
             B.Fy[k] = (double)mk[k * 16 + 4];
+            body_force(k, -(double)mk[k * 16 + 3] * B.ds, -(double)mk[k * 16 + 4] * B.ds);
         }
         if (tid == 0) {
             B.st.mdf_iters = applied;
@@ -1195,6 +1257,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             mk[k * 16 + 1] = -ds * fsy;
             B.Fx[k] = (double)(-ds * fsx);
             B.Fy[k] = (double)(-ds * fsy);
+            body_force(k, (double)(-ds * fsx), (double)(-ds * fsy));
         }
     }
     __syncthreads();
@@ -1232,17 +1295,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         for (int i = 0; i < 9; ++i) o[i] = p[i];
     }
 
-    // force and torque on the body (Sec. 2.7), FP64, fixed-order tree
-    double gxs = 0.0, gys = 0.0, ts = 0.0;
-    for (int k = tid; k < n; k += kIbThreads) {
-        double gx, gy;
-        if (scheme == SCH_DFC) { gx = B.Fx[k]; gy = B.Fy[k]; }
-        else { gx = -B.Fx[k] * B.ds; gy = -B.Fy[k] * B.ds; }
-        const double rx = B.X[k] - B.st.xc, ry = B.Y[k] - B.st.yc;
-        gxs += gx;
-        gys += gy;
-        ts += rx * gy - ry * gx;
-    }
+    // body force and torque: fixed-order reduction of the per-thread sums
     block_sum3(gxs, gys, ts, shd);
     if (tid == 0) {
         const double Fhx = gxs, Fhy = gys, Th = ts;
@@ -1261,13 +1314,17 @@ template <class S>
 __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     const BodyRef ref = L.refs[blockIdx.x];
     using R = typename Traits<S>::R;
+    static_assert(kIbThreads == 512, "IbSmem sizes sF for 512 markers");
     __shared__ int shi[2 * kIbThreads + 4];
     __shared__ double shd[4 * (kIbThreads / 32) + 4];
-    __shared__ R sU[2 * kMdfNodeCap];
-    __shared__ R sF[2 * kIbThreads];
+    IBLBM_DYNAMIC_SMEM(dsm);
+    R* sU = reinterpret_cast<R*>(dsm);
+    R* sF = sU + 2 * kMdfNodeCap;
+    R* sEw = sF + 2 * kIbThreads;
+    int* sEk = reinterpret_cast<int*>(sEw + kMdfEntryCap);
     if (ref.b->nfp < 0) return;
-    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF);
-    else ib_run<S, 4>(L, ref, shi, shd, sU, sF);
+    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk);
+    else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1528,12 +1585,22 @@ cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st) {
 
 long long lattice_edge_nodes(int nx, int ny) { return edge_count(nx, ny); }
 
+template <class S>
+static cudaError_t launch_ib_s(const IbLaunch& L, cudaStream_t st) {
+    constexpr int smem = IbSmem<typename Traits<S>::R>::bytes;
+    static const cudaError_t attr = cudaFuncSetAttribute(reinterpret_cast<const void*>(&ib_kernel<S>),
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    IBLBM_LAUNCH_SMEM(ib_kernel<S>, L.nrefs, kIbThreads, smem, st, L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     if (L.nrefs <= 0) return cudaSuccess;
     switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(ib_kernel<double>, L.nrefs, kIbThreads, st, L); break;
-    case ST_F32: IBLBM_LAUNCH(ib_kernel<float>, L.nrefs, kIbThreads, st, L); break;
-    default: IBLBM_LAUNCH(ib_kernel<__half>, L.nrefs, kIbThreads, st, L); break;
+    case ST_F64: return launch_ib_s<double>(L, st);
+    case ST_F32: return launch_ib_s<float>(L, st);
+    default: return launch_ib_s<__half>(L, st);
     }
     return cudaGetLastError();
 }
