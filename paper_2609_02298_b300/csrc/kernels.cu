@@ -682,32 +682,53 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
     __syncthreads();
     return sh[kIbThreads / 32];
 }
-// Three sums, same scheme (fixed butterfly order: deterministic).
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+// Square root of the largest of the threads' non-negative e2, computed once.  The
+// maximum runs on the integer pipes (the bit patterns of non-negative doubles order
+// as their values), since FP64 arithmetic is scarce on B300.
+__device__ __forceinline__ double block_max_sqrt(double e2, double* sh) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    constexpr int NW = kIbThreads / 32;
+    long long v = __double_as_longlong(e2);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    __syncthreads();
-    if (lane == 0) { sh[w] = a; sh[NW + w] = b; sh[2 * NW + w] = c; }
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    long long* shl = reinterpret_cast<long long*>(sh);
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0) shl[w] = v;
     __syncthreads();
     if (w == 0) {
-        double x = lane < NW ? sh[lane] : 0.0, y = lane < NW ? sh[NW + lane] : 0.0,
-               z = lane < NW ? sh[2 * NW + lane] : 0.0;
+        long long u = lane < kIbThreads / 32 ? shl[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = max(u, __shfl_xor_sync(0xffffffffu, u, o));
+        if (lane == 0) sh[kIbThreads / 32] = sqrt(__longlong_as_double(u));
+    }
+    __syncthreads();
+    return sh[kIbThreads / 32];
+}
+// Three FP64 sums in a fixed order: every thread parks its partials in shared memory
+// and one warp adds them (lane l takes slots l, l + 32, ...), then a butterfly; few
+// FP64 instructions, since FP64 arithmetic is scarce on B300.  sh holds 3 kIbThreads.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    __syncthreads();
+    sh[t] = a; sh[kIbThreads + t] = b; sh[2 * kIbThreads + t] = c;
+    __syncthreads();
+    if (w == 0) {
+        double x = 0.0, y = 0.0, z = 0.0;
+        for (int i = lane; i < kIbThreads; i += 32) {
+            x += sh[i];
+            y += sh[kIbThreads + i];
+            z += sh[2 * kIbThreads + i];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_xor_sync(0xffffffffu, x, o);
             y += __shfl_xor_sync(0xffffffffu, y, o);
             z += __shfl_xor_sync(0xffffffffu, z, o);
         }
-        if (lane == 0) { sh[3 * NW] = x; sh[3 * NW + 1] = y; sh[3 * NW + 2] = z; }
+        __syncwarp();
+        if (lane == 0) { sh[0] = x; sh[1] = y; sh[2] = z; }
     }
     __syncthreads();
-    a = sh[3 * NW]; b = sh[3 * NW + 1]; c = sh[3 * NW + 2];
+    a = sh[0]; b = sh[1]; c = sh[2];
 }
 __device__ __forceinline__ int block_min_i(int v, int* sh) {
     const int t = threadIdx.x;
@@ -871,14 +892,16 @@ constexpr int kMdfEntryCap = 4096; // node->marker entries staged in shared memo
 // Dynamic shared memory of ib_kernel: sU (2 per node), sF (2 per marker), sEw (per
 // entry), then sEk (per entry, int).
 template <class R> struct IbSmem {
-    static constexpr int bytes = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap) * (int)sizeof(R) + kMdfEntryCap * 4;
+    static constexpr int bytes = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap + kMdfNodeCap) * (int)sizeof(R) +
+                                 (kMdfEntryCap + kMdfNodeCap + 1) * 4;
 };
 
 // Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
 template <class S, int SX>
 __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
                                        typename Traits<S>::R* sU, typename Traits<S>::R* sF,
-                                       typename Traits<S>::R* sEw, int* sEk) {
+                                       typename Traits<S>::R* sEw, int* sEk, typename Traits<S>::R* sQc,
+                                       int* sQo) {
     using R = typename Traits<S>::R;
     constexpr int SS = SX * SX;
     const CaseDev& C = *ref.c;
@@ -1073,16 +1096,12 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             sEk[o] = B.csr_ent[o] / SS;
             sEw[o] = cw[o] * ds;
         }
-        constexpr int NQ = kMdfNodeCap / kIbThreads;   // footprint nodes per thread
-        int qo0[NQ], qo1[NQ];
-        R qc[NQ];                                       // omega / (2 rho(x))
-#pragma unroll
-        for (int u = 0; u < NQ; ++u) {
-            const int q = tid + u * kIbThreads;
-            qo0[u] = q < nfp ? B.csr_off[q] : 0;
-            qo1[u] = q < nfp ? B.csr_off[q + 1] : 0;
-            qc[u] = q < nfp ? om / (R(2) * fp[(size_t)q * 9]) : R(0);
+        for (int q = tid; q < nfp; q += kIbThreads) {
+            sQo[q] = B.csr_off[q];
+            sQc[q] = om / (R(2) * fp[(size_t)q * 9]);   // omega / (2 rho(x)), Eq. 14
         }
+        if (tid == 0) sQo[nfp] = B.csr_off[nfp];
+        const R rudx = R(udx), rudy = R(udy);
         __syncthreads();
         int applied = 0;
         double rprev = 0.0, r = 0.0;
@@ -1098,29 +1117,26 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
                     Uy += sU[2 * sl[q] + 1] * D[q];
                 }
                 const double dx = udx - (double)Ux, dy = udy - (double)Uy;
-                e = sqrt(dx * dx + dy * dy);
-                Fx = R(2) * rk * (R(udx) - Ux);   // Eq. 13
-                Fy = R(2) * rk * (R(udy) - Uy);
+                e = dx * dx + dy * dy;            // squared; the root is taken once below
+                Fx = R(2) * rk * (rudx - Ux);     // Eq. 13
+                Fy = R(2) * rk * (rudy - Uy);
                 sF[2 * tid] = Fx;
                 sF[2 * tid + 1] = Fy;
             }
-            r = block_max(e, shd);   // also publishes sF
+            r = block_max_sqrt(e, shd);   // also publishes sF
             if (applied >= B.mdf_nmin && r < B.mdf_tol) { tol_met = true; break; }
             if (it >= 2 && r > 1.5 * rprev) { guard = true; break; }
-#pragma unroll
-            for (int u = 0; u < NQ; ++u) {
-                const int q = tid + u * kIbThreads;
+            for (int q = tid; q < nfp; q += kIbThreads) {
                 R sx = R(0), sy = R(0);
-                for (int o = qo0[u]; o < qo1[u]; ++o) {
+                const int o1 = sQo[q + 1];
+                for (int o = sQo[q]; o < o1; ++o) {
                     const int k = sEk[o];
                     const R d = sEw[o];   // D(x - X_k) ds
                     sx += sF[2 * k] * d;
                     sy += sF[2 * k + 1] * d;
                 }
-                if (q < nfp) {
-                    sU[2 * q] += qc[u] * sx;   // Eq. 14 with the node density
-                    sU[2 * q + 1] += qc[u] * sy;
-                }
+                sU[2 * q] += sQc[q] * sx;   // Eq. 14 with the node density
+                sU[2 * q + 1] += sQc[q] * sy;
             }
             Fxt += om * Fx;
             Fyt += om * Fy;
@@ -1316,15 +1332,17 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     using R = typename Traits<S>::R;
     static_assert(kIbThreads == 512, "IbSmem sizes sF for 512 markers");
     __shared__ int shi[2 * kIbThreads + 4];
-    __shared__ double shd[4 * (kIbThreads / 32) + 4];
+    __shared__ double shd[3 * kIbThreads];
     IBLBM_DYNAMIC_SMEM(dsm);
     R* sU = reinterpret_cast<R*>(dsm);
     R* sF = sU + 2 * kMdfNodeCap;
     R* sEw = sF + 2 * kIbThreads;
-    int* sEk = reinterpret_cast<int*>(sEw + kMdfEntryCap);
+    R* sQc = sEw + kMdfEntryCap;
+    int* sEk = reinterpret_cast<int*>(sQc + kMdfNodeCap);
+    int* sQo = sEk + kMdfEntryCap;
     if (ref.b->nfp < 0) return;
-    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk);
-    else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk);
+    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
+    else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
 }
 
 // ------------------------------------------------------------------------------------------

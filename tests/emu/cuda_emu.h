@@ -45,8 +45,19 @@ inline void __syncthreads() { emu::syncthreads(); }
 
 template <class T>
 inline T __ldg(const T* p) { return *p; }
+inline long long emu_to_bits_ll(double v) {
+    long long b;
+    std::memcpy(&b, &v, sizeof(b));
+    return b;
+}
 template <class T>
 inline void __stcg(T* p, T v) { *p = v; }
+inline long long __double_as_longlong(double v) { return emu_to_bits_ll(v); }
+inline double __longlong_as_double(long long v) {
+    double d;
+    std::memcpy(&d, &v, sizeof(d));
+    return d;
+}
 
 template <class T>
 inline T emu_from_bits(uint64_t b) {
