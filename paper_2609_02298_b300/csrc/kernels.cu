@@ -1088,19 +1088,57 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
             udx = B.Udx[tid];
             udy = B.Udy[tid];
         }
-        for (int q = tid; q < nfp; q += kIbThreads) {
-            sU[2 * q] = fp[(size_t)q * 9 + 3];
-            sU[2 * q + 1] = fp[(size_t)q * 9 + 4];
+        // staging: each thread loads a batch of independent values before storing any,
+        // so one round trip to memory serves the batch
+        {
+            const R* __restrict__ gfp = fp;
+            const int* __restrict__ gent = B.csr_ent;
+            const int* __restrict__ goff = B.csr_off;
+            const R* __restrict__ gcw = cw;
+            constexpr int QB = kMdfNodeCap / kIbThreads;
+            R u0[QB], u1[QB], rh[QB];
+            int of[QB];
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+                const int q = tid + u * kIbThreads;
+                const bool live = q < nfp;
+                u0[u] = live ? gfp[(size_t)q * 9 + 3] : R(0);
+                u1[u] = live ? gfp[(size_t)q * 9 + 4] : R(0);
+                rh[u] = live ? gfp[(size_t)q * 9] : R(1);
+                of[u] = q <= nfp ? goff[q] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+                const int q = tid + u * kIbThreads;
+                if (q < nfp) {
+                    sU[2 * q] = u0[u];
+                    sU[2 * q + 1] = u1[u];
+                    sQc[q] = om / (R(2) * rh[u]);   // omega / (2 rho(x)), Eq. 14
+                }
+                if (q <= nfp) sQo[q] = of[u];
+            }
+            const int ne = goff[nfp];
+            constexpr int EB = 8;
+            for (int o0 = tid; o0 < ne; o0 += EB * kIbThreads) {
+                int ek[EB];
+                R ew[EB];
+#pragma unroll
+                for (int u = 0; u < EB; ++u) {
+                    const int o = o0 + u * kIbThreads;
+                    ek[u] = o < ne ? gent[o] : 0;
+                    ew[u] = o < ne ? gcw[o] : R(0);
+                }
+#pragma unroll
+                for (int u = 0; u < EB; ++u) {
+                    const int o = o0 + u * kIbThreads;
+                    if (o < ne) {
+                        sEk[o] = ek[u] / SS;
+                        sEw[o] = ew[u] * ds;
+                    }
+                }
+            }
+            if (nfp == QB * kIbThreads && tid == 0) sQo[nfp] = goff[nfp];
         }
-        for (int o = tid; o < B.csr_off[nfp]; o += kIbThreads) {
-            sEk[o] = B.csr_ent[o] / SS;
-            sEw[o] = cw[o] * ds;
-        }
-        for (int q = tid; q < nfp; q += kIbThreads) {
-            sQo[q] = B.csr_off[q];
-            sQc[q] = om / (R(2) * fp[(size_t)q * 9]);   // omega / (2 rho(x)), Eq. 14
-        }
-        if (tid == 0) sQo[nfp] = B.csr_off[nfp];
         const R rudx = R(udx), rudy = R(udy);
         __syncthreads();
         int applied = 0;
