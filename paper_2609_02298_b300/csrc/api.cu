@@ -60,6 +60,7 @@ struct BodyHost {
     int n = 0;
     int kernel = 0, scheme = 0, motion = 0;
     double xc = 0, yc = 0, reach = 0;   // centre and marker reach for overlap checks
+    bool moved = false;                 // markers replaced by iblbm_move_body since it was added
 };
 
 struct GraphSet {
@@ -478,6 +479,8 @@ int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3])
         cudaMemcpy(b.Y, Y.data(), 8 * n, cudaMemcpyHostToDevice);
         b.cache_valid = 0;
         b.lam_valid = 0;
+        c->bodies[id].moved = true;
+        c->version += 1;   // batch plans decide launch order from body positions: rebuild them
     }
     if (uvw) {
         b.st.vx = uvw[0];
@@ -760,10 +763,18 @@ struct BatchPlan {
     cudaStream_t st = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> joins;
+    // Lattice-edge launch overlapped with the IB stage on a side stream, when no body
+    // can reach a lattice edge (the edge nodes then need no IB patch).
+    bool edges_early = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_edges = nullptr;
     ~BatchPlan() {
         graphs.reset();
         for (auto p : mem) dev_free(p, st);
         for (auto e : joins) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_edges) cudaEventDestroy(ev_edges);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -775,9 +786,43 @@ void* plan_alloc(BatchPlan* P, size_t b) {
     return p;
 }
 
+cudaError_t launch_edge_groups(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer, int noib) {
+    for (auto& g : P->edge_groups) {
+        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block, noib, 0};
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timer) {
+            a = pool_event(timer);
+            b = pool_event(timer);
+            cudaEventRecord(a, st);
+        }
+        const cudaError_t e = launch_edges(g.storage, el, st);
+        if (e != cudaSuccess) return e;
+        if (timer) {
+            cudaEventRecord(b, st);
+            timer->ev_pending.push_back({a, b});
+        }
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     cudaError_t e = cudaSuccess;
     FinLaunch all{P->drefs_all, P->nrefs_all, (int)P->ctxs.size(), P->dcases_all};
+    // edge nodes first, on a side stream, while the IB stage runs (they read only the
+    // source populations; launch by launch on one stream when timing)
+    // (not with the vector variant, whose launch also writes side nodes that the edge
+    // launch must overwrite afterwards)
+    bool early = P->edges_early && !timer;
+    for (auto& g : P->groups) {
+        const int chosen = g_variant[g.storage][g.collision][g.size_class];
+        if ((chosen < 0 ? SC_SCALAR : chosen) == SC_VECTOR && g.ok[SC_VECTOR]) early = false;
+    }
+    if (early) {
+        cudaEventRecord(P->ev_fork, st);
+        cudaStreamWaitEvent(P->side, P->ev_fork, 0);
+        if ((e = launch_edge_groups(P, P->side, nullptr, 1)) != cudaSuccess) return e;
+        cudaEventRecord(P->ev_edges, P->side);
+    }
     if (P->nrefs_all > 0) {
         if ((e = launch_body(all, 0, st)) != cudaSuccess) return e;
         for (auto& g : P->ib_groups) {
@@ -803,20 +848,8 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
             timer->ev_pending.push_back({a, b});
         }
     }
-    for (auto& g : P->edge_groups) {
-        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block};
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (timer) {
-            a = pool_event(timer);
-            b = pool_event(timer);
-            cudaEventRecord(a, st);
-        }
-        if ((e = launch_edges(g.storage, el, st)) != cudaSuccess) return e;
-        if (timer) {
-            cudaEventRecord(b, st);
-            timer->ev_pending.push_back({a, b});
-        }
-    }
+    if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // join before the step counters advance
+    else if ((e = launch_edge_groups(P, st, timer, 0)) != cudaSuccess) return e;
     return launch_body(all, 1, st);
 }
 
@@ -979,6 +1012,26 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         g_variant[g.storage][g.collision][g.size_class] = best;
+    }
+    // edge launch overlapped with the IB stage when no footprint can reach a lattice
+    // edge: every body fixed where it was added, its markers (within `reach` of the
+    // centre) plus the Peskin stencil and a margin clear of the edge rows and columns
+    bool clear = true;
+    for (int i = 0; i < n; ++i)
+        for (const auto& b : ctxs[i]->bodies) {
+            const double m = b.reach + 4.0;
+            clear = clear && b.motion == MOT_FIXED && !b.moved && b.xc - m > 1.0 && b.yc - m > 1.0 &&
+                    b.xc + m < ctxs[i]->hc.nx - 2.0 && b.yc + m < ctxs[i]->hc.ny - 2.0;
+        }
+    if (clear && !P->edge_groups.empty()) {
+        if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_edges, cudaEventDisableTiming) != cudaSuccess) {
+            *rc = IBLBM_ERR_CUDA;
+            delete P;
+            return nullptr;
+        }
+        P->edges_early = true;
     }
     *rc = check(cudaStreamSynchronize(P->st));
     if (*rc) { delete P; return nullptr; }

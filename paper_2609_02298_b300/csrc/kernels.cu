@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     R s[9];
     post_stream_node<S, R>(C, K.src, x, y, s);
     R Fx = K.gfx, Fy = K.gfy;
-    if (K.nbodies > 0) add_ib<R>(C, x, y, s, Fx, Fy);
+    if (K.nbodies > 0 && !L.noib) add_ib<R>(C, x, y, s, Fx, Fy);
     const R rho = collide<R, -1>(K.P, s, Fx, Fy);
     if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
     S* d = K.dst + ((long long)y * K.pitch + x);

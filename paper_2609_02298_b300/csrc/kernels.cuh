@@ -56,6 +56,8 @@ struct EdgeLaunch {
     EdgeChunk* chunks;
     int nchunks;
     int block;   // threads per CTA: the chunk size, a multiple of 32 up to kThreads
+    int noib;    // 1: no edge node lies in a body footprint (no IB patch lookup)
+    int pad_;
 };
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);

@@ -175,6 +175,7 @@ bool drop_bulk_copies() {
 // ---- runtime API --------------------------------------------------------------------------
 struct EmuEvent {
     std::chrono::steady_clock::time_point t;
+    std::shared_ptr<emu::Capture> cap;   // capture the recording stream was in, if any
 };
 struct EmuGraph {
     std::vector<std::function<void()>> ops;
@@ -239,8 +240,11 @@ cudaError_t cudaEventDestroy(cudaEvent_t e) {
     delete reinterpret_cast<EmuEvent*>(e);
     return cudaSuccess;
 }
-cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
-    reinterpret_cast<EmuEvent*>(e)->t = std::chrono::steady_clock::now();
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) {
+    EmuEvent* ev = reinterpret_cast<EmuEvent*>(e);
+    ev->t = std::chrono::steady_clock::now();
+    auto it = emu::g_capturing.find(s);
+    ev->cap = it != emu::g_capturing.end() ? it->second : nullptr;
     return cudaSuccess;
 }
 cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t a, cudaEvent_t b) {
@@ -248,7 +252,12 @@ cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t a, cudaEvent_t b) {
                                                    reinterpret_cast<EmuEvent*>(a)->t).count();
     return cudaSuccess;
 }
-cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned) { return cudaSuccess; }
+cudaError_t cudaStreamWaitEvent(cudaStream_t s, cudaEvent_t e, unsigned) {
+    // a stream that waits on an event recorded during a capture joins that capture
+    EmuEvent* ev = reinterpret_cast<EmuEvent*>(e);
+    if (ev->cap) emu::g_capturing[s] = ev->cap;
+    return cudaSuccess;
+}
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaGetSymbolAddress(void** p, const void* symbol) {
     *p = const_cast<void*>(symbol);
@@ -263,7 +272,9 @@ cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t* g) {
     if (it == emu::g_capturing.end()) return cudaErrorIllegalState;
     EmuGraph* eg = new EmuGraph();
     eg->ops = it->second->ops;
-    emu::g_capturing.erase(it);
+    const auto cap = it->second;
+    for (auto j = emu::g_capturing.begin(); j != emu::g_capturing.end();)   // joined streams leave too
+        j = j->second == cap ? emu::g_capturing.erase(j) : std::next(j);
     *g = reinterpret_cast<cudaGraph_t>(eg);
     return cudaSuccess;
 }
