@@ -190,7 +190,10 @@ int iblbm_get_macro(iblbm_ctx* ctx, double* rho, double* ux, double* uy);
  * host may be NULL to query the size into *n.  Errors: CAPACITY.  Syncs. */
 int iblbm_snapshot(iblbm_ctx* ctx, void* host, size_t cap, size_t* n);
 /* Restores a checkpoint written by iblbm_snapshot of a context with the same
- * lattice and bodies.  Errors: INVALID_ARG.  Syncs. */
+ * lattice and bodies.  Errors: INVALID_ARG.  Waits for this context's own stream
+ * only (before the copies and after them, so host may be reused on return); work
+ * queued on other contexts keeps running, which lets a caller copy one lattice
+ * in while others step. */
 int iblbm_restore(iblbm_ctx* ctx, const void* host, size_t n);
 
 /* Device bytes held by the context. */

@@ -623,41 +623,46 @@ int iblbm_restore(iblbm_ctx* c, const void* host, size_t n) {
     if (h.magic != 0x49424c4du || h.nx != c->hc.nx || h.ny != c->hc.ny || h.storage != c->hc.storage ||
         h.nbodies != (int)c->bodies.size())
         return IBLBM_ERR_INVALID_ARG;
-    cudaStreamSynchronize(c->work);
+    // every copy goes on the context's own stream and the call waits for that stream
+    // only: restoring one lattice does not wait for work queued on other lattices
+    cudaStream_t w = c->work;
+    cudaStreamSynchronize(w);
     const size_t fb = 9 * (size_t)c->hc.plane * storage_bytes(c->hc.storage);
     const char* p = static_cast<const char*>(host) + sizeof(h);
     size_t need = sizeof(h) + fb;
     std::vector<BodyDev> bs;
     for (int b = 0; b < h.nbodies; ++b) {
-        bs.push_back(fetch_body(c, b));
+        bs.emplace_back();
+        cudaMemcpyAsync(&bs.back(), &c->dbodies[b], sizeof(BodyDev), cudaMemcpyDeviceToHost, w);
+        cudaStreamSynchronize(w);
         need += sizeof(BodyState) + 7 * 8 * (size_t)bs.back().n + 24 * (size_t)bs.back().hist_cap;
     }
     if (n < need) return IBLBM_ERR_INVALID_ARG;
-    cudaMemcpy(c->hc.f[(int)(h.dev_step & 1ull)], p, fb, cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(c->hc.f[(int)(h.dev_step & 1ull)], p, fb, cudaMemcpyHostToDevice, w);
     p += fb;
-    cudaMemcpy(&c->dc->step, &h.dev_step, sizeof(unsigned long long), cudaMemcpyHostToDevice);
-    unsigned zero = 0;
-    cudaMemcpy(&c->dc->status, &zero, sizeof(unsigned), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(&c->dc->step, &h.dev_step, sizeof(unsigned long long), cudaMemcpyHostToDevice, w);
+    const unsigned zero = 0;
+    cudaMemcpyAsync(&c->dc->status, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, w);
     for (int b = 0; b < h.nbodies; ++b) {
         BodyDev& B = bs[b];
         std::memcpy(&B.st, p, sizeof(BodyState));
         p += sizeof(BodyState);
         double* arr[7] = {B.X, B.Y, B.Udx, B.Udy, B.Fx, B.Fy, B.lam};
         for (int j = 0; j < 7; ++j) {
-            cudaMemcpy(arr[j], p, 8 * (size_t)B.n, cudaMemcpyHostToDevice);
+            cudaMemcpyAsync(arr[j], p, 8 * (size_t)B.n, cudaMemcpyHostToDevice, w);
             p += 8 * (size_t)B.n;
         }
-        cudaMemcpy(B.hist, p, 24 * (size_t)B.hist_cap, cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(B.hist, p, 24 * (size_t)B.hist_cap, cudaMemcpyHostToDevice, w);
         p += 24 * (size_t)B.hist_cap;
         B.cache_valid = 0;
         B.lam_valid = 0;
         B.status = 0;
         B.t0 = h.steps - B.st.nstep;   // step at which the body joined the checkpointed run
-        cudaMemcpy(&c->dbodies[b], &B, sizeof(BodyDev), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(&c->dbodies[b], &B, sizeof(BodyDev), cudaMemcpyHostToDevice, w);
     }
     c->steps = h.steps;
     for (int b = 0; b < h.nbodies; ++b) c->hbodies[b].t0 = bs[b].t0;
-    return check(cudaDeviceSynchronize());
+    return check(cudaStreamSynchronize(w));
 }
 
 int iblbm_set_timing(iblbm_ctx* c, int enable) {
