@@ -90,6 +90,8 @@ def lib():
             "orc_dfc_lambda": (None, [i, i, i, pd, i, d, pd]),
             "orc_mdf_norm_A": (d, [i, i, i, pd, i, d]),
             "orc_verlet_free_fall": (None, [d, d, d, d, i, i, pd, pd]),
+            "orc_local_diagnostics_fields": (i, [i, i, i, pd, pd, pd, pd, i, d, pd, d, d, pd, vp]),
+            "orc_local_diagnostics": (i, [vp, i, d, d, pd, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -159,6 +161,22 @@ def dfc_lambda(kernel, xy: np.ndarray, ds: float, nx: int, ny: int) -> np.ndarra
     out = np.zeros(len(xy))
     lib().orc_dfc_lambda(kernel, nx, ny, _dp(xy), len(xy), ds, _dp(out))
     return out
+
+
+def local_diagnostics_fields(kernel, rho, ux, uy, md, ds, body, u_ref, kappa=2.0, per_marker=False):
+    """Sec. 2.8 diagnostics from node fields [ny, nx] and marker data [n, 7]; returns
+    out[8] (and the [n, 5] per-marker table when ``per_marker``)."""
+    rho, ux, uy = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    md = np.ascontiguousarray(md, dtype=np.float64).reshape(-1, 7)
+    body = np.ascontiguousarray(body, dtype=np.float64)
+    out = np.zeros(8)
+    pm = np.zeros((len(md), 5)) if per_marker else None
+    rc = lib().orc_local_diagnostics_fields(kernel, rho.shape[1], rho.shape[0], _dp(rho), _dp(ux), _dp(uy),
+                                            _dp(md), len(md), ds, _dp(body), u_ref, kappa, _dp(out),
+                                            pm.ctypes.data if pm is not None else None)
+    if rc:
+        raise ValueError("stencil or probe node outside the lattice")
+    return (out, pm) if per_marker else out
 
 
 def mdf_norm_A(kernel, xy: np.ndarray, ds: float, nx: int, ny: int) -> float:
@@ -256,3 +274,12 @@ class Case:
 
     def mdf_residual(self, b: int) -> float:
         return lib().orc_mdf_residual(self._h, b)
+
+    def local_diagnostics(self, b: int, u_ref: float, kappa: float = 2.0, per_marker: bool = False):
+        out = np.zeros(8)
+        pm = np.zeros((self.body_n[b], 5)) if per_marker else None
+        rc = lib().orc_local_diagnostics(self._h, b, u_ref, kappa, _dp(out),
+                                         pm.ctypes.data if pm is not None else None)
+        if rc:
+            raise ValueError("stencil or probe node outside the lattice")
+        return (out, pm) if per_marker else out

@@ -825,6 +825,116 @@ int orc_mdf_iterations(const orc_case* c, int b) { return c->bodies[b].mdf_iters
 double orc_mdf_omega(const orc_case* c, int b) { return c->bodies[b].mdf_omega; }
 double orc_mdf_residual(const orc_case* c, int b) { return c->bodies[b].mdf_res; }
 
+/* ---- Sec. 2.8 local diagnostics ------------------------------------------------
+ * Readings (the paper names the three metrics and their normalisations only):
+ *  - slip is |U(X_k) - U_d,k| with U interpolated by the body's own kernel (Eq. 7)
+ *    from the Eq. 4 velocity of the last collision; U_d,k is the marker's desired
+ *    velocity (zero for a fixed body, so this is the paper's |U| / U_inf);
+ *  - the bilinear probe (Sec. 4.2, Fig. 5) interpolates from the four nodes
+ *    around X_k; the pressure residual is (rho - 1) c_s^2 at the probe;
+ *  - leakage is the net flux sum_k rho(X_k) (U - U_d).n_k ds over the marker
+ *    polygon, n_k the outward normal of the chord X_{k+1} - X_{k-1}, normalised by
+ *    U_inf times the polygon length n ds (pi D for a circle); the gross flux with
+ *    |.| is reported beside it;
+ *  - the kappa = 2 buffer keeps the nodes with |x - X_c| < R - kappa (strict);
+ *    inside the solid the residual is taken against the rigid velocity
+ *    v + omega x (x - X_c), which is zero for a fixed body. */
+static double bilinear_at(int nx, const double* g, double X, double Y) {
+    int i0 = (int)floor(X), j0 = (int)floor(Y);
+    double fx = X - i0, fy = Y - j0;
+    return (1.0 - fx) * (1.0 - fy) * g[(size_t)j0 * nx + i0] + fx * (1.0 - fy) * g[(size_t)j0 * nx + i0 + 1]
+         + (1.0 - fx) * fy * g[(size_t)(j0 + 1) * nx + i0] + fx * fy * g[(size_t)(j0 + 1) * nx + i0 + 1];
+}
+
+int orc_local_diagnostics_fields(int kernel, int nx, int ny, const double* rho, const double* ux,
+                                 const double* uy, const double* md, int n, double ds,
+                                 const double body[6], double u_ref, double kappa, double out[8],
+                                 double* pm) {
+    const double xc = body[0], yc = body[1], vx = body[2], vy = body[3], om = body[4], R = body[5];
+    double slip_sum = 0.0, slip_max = 0.0, bl_max = 0.0, net = 0.0, gross = 0.0, fsum = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double X = md[7 * k], Y = md[7 * k + 1], Udx = md[7 * k + 2], Udy = md[7 * k + 3];
+        const double Fkx = md[7 * k + 4], Fky = md[7 * k + 5];
+        int w, i0 = stencil_origin(kernel, X, &w), j0 = stencil_origin(kernel, Y, &w);
+        int b0 = (int)floor(X), c0 = (int)floor(Y);
+        if (i0 < 0 || j0 < 0 || i0 + w > nx || j0 + w > ny || b0 < 0 || c0 < 0 || b0 + 2 > nx || c0 + 2 > ny)
+            return 1;
+        /* Eq. 7 with the body's kernel */
+        const double U = interp_one(kernel, nx, ux, X, Y), V = interp_one(kernel, nx, uy, X, Y);
+        const double rk = interp_one(kernel, nx, rho, X, Y);
+        /* bilinear probe */
+        const double Ub = bilinear_at(nx, ux, X, Y), Vb = bilinear_at(nx, uy, X, Y);
+        const double rb = bilinear_at(nx, rho, X, Y);
+        /* outward normal */
+        double nxk, nyk;
+        if (n >= 3) {
+            const int kp = (k + 1) % n, km = (k + n - 1) % n;
+            const double tx = md[7 * kp] - md[7 * km], ty = md[7 * kp + 1] - md[7 * km + 1];
+            const double t = sqrt(tx * tx + ty * ty);
+            nxk = t > 0.0 ? ty / t : 0.0;
+            nyk = t > 0.0 ? -tx / t : 0.0;
+            if (nxk * (X - xc) + nyk * (Y - yc) < 0.0) { nxk = -nxk; nyk = -nyk; }
+        } else {
+            const double r = sqrt((X - xc) * (X - xc) + (Y - yc) * (Y - yc));
+            nxk = r > 0.0 ? (X - xc) / r : 0.0;
+            nyk = r > 0.0 ? (Y - yc) / r : 0.0;
+        }
+        const double s = sqrt((U - Udx) * (U - Udx) + (V - Udy) * (V - Udy)) / u_ref;
+        const double sb = sqrt((Ub - Udx) * (Ub - Udx) + (Vb - Udy) * (Vb - Udy)) / u_ref;
+        const double un = (U - Udx) * nxk + (V - Udy) * nyk;
+        const double fm = sqrt(Fkx * Fkx + Fky * Fky);
+        slip_sum += s;
+        if (s > slip_max) slip_max = s;
+        if (sb > bl_max) bl_max = sb;
+        net += rk * un * ds;
+        gross += rk * fabs(un) * ds;
+        fsum += fm;
+        if (pm) {
+            pm[5 * k + 0] = s;
+            pm[5 * k + 1] = sb;
+            pm[5 * k + 2] = un / u_ref;
+            pm[5 * k + 3] = (rb - 1.0) / 3.0;
+            pm[5 * k + 4] = fm;
+        }
+    }
+    /* interior nodes beyond the kappa buffer */
+    double in_sum = 0.0;
+    long cnt = 0;
+    const double ri = R - kappa;
+    if (ri > 0.0) {
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const double dx = x - xc, dy = y - yc;
+                if (dx * dx + dy * dy < ri * ri) {
+                    const size_t q = (size_t)y * nx + x;
+                    const double ex_ = ux[q] - (vx - om * dy), ey_ = uy[q] - (vy + om * dx);
+                    in_sum += sqrt(ex_ * ex_ + ey_ * ey_);
+                    ++cnt;
+                }
+            }
+    }
+    out[0] = n > 0 ? slip_sum / n : 0.0;
+    out[1] = slip_max;
+    out[2] = bl_max;
+    out[3] = n > 0 ? net / (u_ref * n * ds) : 0.0;
+    out[4] = n > 0 ? gross / (u_ref * n * ds) : 0.0;
+    out[5] = cnt > 0 ? in_sum / cnt / u_ref : 0.0;
+    out[6] = (double)cnt;
+    out[7] = fsum;
+    return 0;
+}
+
+int orc_local_diagnostics(const orc_case* c, int b, double u_ref, double kappa, double out[8], double* pm) {
+    const orc_body* B = &c->bodies[b];
+    double* md = (double*)malloc(sizeof(double) * 7 * (size_t)(B->n > 0 ? B->n : 1));
+    orc_marker_data(c, b, md);
+    const double body[6] = {B->xc, B->yc, B->vx, B->vy, B->om, B->p.radius};
+    int rc = orc_local_diagnostics_fields(B->kernel, c->nx, c->ny, c->mrho, c->mux, c->muy, md, B->n,
+                                          B->ds, body, u_ref, kappa, out, pm);
+    free(md);
+    return rc;
+}
+
 /* Verlet of Eq. 23 with F_hydro = 0 (no fluid): gravity and internal mass only. */
 void orc_verlet_free_fall(double rho_ratio, double radius, double gx, double gy, int internal_mass,
                           int nsteps, double* out_v, double* out_x) {

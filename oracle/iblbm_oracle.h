@@ -75,6 +75,26 @@ int       orc_mdf_iterations(const orc_case* c, int b);
 double    orc_mdf_omega(const orc_case* c, int b);
 double    orc_mdf_residual(const orc_case* c, int b);
 
+/* Local boundary-fidelity diagnostics of Sec. 2.8 (with the bilinear probe of
+ * Sec. 4.2) from node fields rho, ux, uy [ny*nx] and one body:
+ *   md[7*n]   marker data as orc_marker_data writes it (X, Y, U_d, force, lambda)
+ *   body[6]   centre xc, yc, rigid velocity vx, vy, omega, radius R
+ * out[8]: mean and max over markers of |U(X_k) - U_d,k| / u_ref (U interpolated
+ * with the body's kernel, Eq. 7); max of the same with a bilinear probe; net and
+ * gross leakage sum_k rho(X_k) (U - U_d).n_k ds (resp. its absolute value) over
+ * u_ref * n * ds; mean |u(x) - U_rigid(x)| / u_ref over nodes with
+ * |x - X_c| < R - kappa, and their count; sum_k |F_k|.
+ * pm[5*n] (may be NULL): per marker kernel slip, bilinear slip, (U - U_d).n_k /
+ * u_ref, (rho_bilinear - 1) c_s^2, |F_k|.  Returns 0, or 1 if a stencil or probe
+ * node lies outside the lattice. */
+int orc_local_diagnostics_fields(int kernel, int nx, int ny, const double* rho, const double* ux,
+                                 const double* uy, const double* md, int n, double ds,
+                                 const double body[6], double u_ref, double kappa, double out[8],
+                                 double* pm);
+/* The same on the case's macro fields of the last collision and body b. */
+int orc_local_diagnostics(const orc_case* c, int b, double u_ref, double kappa, double out[8],
+                          double* pm);
+
 /* primitives exposed for the pin tests */
 double orc_phi(int kernel, double r);
 void   orc_feq(double rho, double ux, double uy, double feq[9]);

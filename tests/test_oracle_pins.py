@@ -502,3 +502,117 @@ def test_free_body_torque_free_symmetric_flow():
     F = c.body_forces(0)
     assert abs(F[1]) < 1e-12 * abs(F[0]) + 1e-15
     assert abs(F[2]) < 1e-10 * abs(F[0])
+
+
+# ------------------------------------------------------ Sec. 2.8 local diagnostics
+def _diag_markers(xc, yc, R, n, clockwise=False, U_d=(0.0, 0.0)):
+    th = 2.0 * math.pi * np.arange(n) / n
+    if clockwise:
+        th = -th
+    md = np.zeros((n, 7))
+    md[:, 0] = xc + R * np.cos(th)
+    md[:, 1] = yc + R * np.sin(th)
+    md[:, 2], md[:, 3] = U_d
+    return md, th
+
+
+def _grid(nx, ny):
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    return x, y
+
+
+@pytest.mark.parametrize("kernel", [oracle.HAT, oracle.PESKIN4])
+def test_diagnostics_uniform_flow_closed_form(kernel):
+    """Uniform flow past a fixed circle: every interpolant reproduces the constant
+    (partition of unity), so slip = U/u_ref at every marker; the net flux through
+    equispaced markers vanishes (sum of cos over the n-th roots of unity) and the
+    gross flux is U mean|cos theta_k| / u_ref; the interior mean is U/u_ref."""
+    nx, ny, U, u_ref = 72, 64, 0.037, 0.1
+    x, y = _grid(nx, ny)
+    rho, ux, uy = np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx))
+    xc, yc, R, n = 33.3, 31.6, 10.0, 63
+    md, th = _diag_markers(xc, yc, R, n)
+    ds = 2 * math.pi * R / n
+    out, pm = oracle.local_diagnostics_fields(kernel, rho, ux, uy, md, ds, [xc, yc, 0, 0, 0, R], u_ref,
+                                              per_marker=True)
+    r = U / u_ref
+    assert out[0] == pytest.approx(r, rel=1e-13) and out[1] == pytest.approx(r, rel=1e-13)
+    assert out[2] == pytest.approx(r, rel=1e-13)
+    assert abs(out[3]) < 1e-14
+    assert out[4] == pytest.approx(r * np.abs(np.cos(th)).mean(), rel=1e-12)
+    assert out[5] == pytest.approx(r, rel=1e-13)
+    np.testing.assert_allclose(pm[:, 2], r * np.cos(th), atol=1e-13)
+    np.testing.assert_allclose(pm[:, 3], 0.0, atol=1e-16)
+
+
+def test_diagnostics_buffer_count_gauss_circle():
+    """kappa buffer: nodes with |x - X_c| < R - kappa.  Centred on a node with
+    R - kappa = 8 that is the Gauss circle count N(8) = 197 (points with
+    x^2 + y^2 <= 64) less the four lattice points on the circle itself."""
+    nx = ny = 64
+    rho, ux, uy = np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
+    md, _ = _diag_markers(32.0, 32.0, 10.0, 60)
+    out = oracle.local_diagnostics_fields(oracle.HAT, rho, ux, uy, md, 1.0, [32, 32, 0, 0, 0, 10.0], 0.1,
+                                          kappa=2.0)
+    assert out[6] == 193
+    out = oracle.local_diagnostics_fields(oracle.HAT, rho, ux, uy, md, 1.0, [32, 32, 0, 0, 0, 10.0], 0.1,
+                                          kappa=1.0)
+    assert out[6] == 253 - 4     # N(9) = 253; x^2 + y^2 = 81 holds only (+-9, 0) and (0, +-9)
+
+
+@pytest.mark.parametrize("kernel", [oracle.HAT, oracle.PESKIN4])
+def test_diagnostics_linear_field_is_exact(kernel):
+    """Both kernels and the bilinear probe reproduce linear fields (first-moment
+    condition), so with u = (a + b (y - y0), c (x - x0)) and rho = 1 + g x the
+    marker values are known in closed form; b != c catches a transposed axis."""
+    nx, ny = 70, 66
+    x, y = _grid(nx, ny)
+    a, b, c, g, x0, y0 = 0.02, 0.003, -0.0011, 0.0007, 30.0, 31.0
+    ux, uy, rho = a + b * (y - y0), c * (x - x0), 1.0 + g * x
+    xc, yc, R, n, u_ref = 35.25, 32.75, 9.5, 57, 0.05
+    md, th = _diag_markers(xc, yc, R, n, U_d=(0.004, -0.002))
+    X, Y = md[:, 0], md[:, 1]
+    out, pm = oracle.local_diagnostics_fields(kernel, rho, ux, uy, md, 0.9, [xc, yc, 0, 0, 0, R], u_ref,
+                                              per_marker=True)
+    U, V = a + b * (Y - y0) - 0.004, c * (X - x0) + 0.002
+    np.testing.assert_allclose(pm[:, 0], np.hypot(U, V) / u_ref, rtol=1e-11)
+    np.testing.assert_allclose(pm[:, 1], np.hypot(U, V) / u_ref, rtol=1e-11)
+    np.testing.assert_allclose(pm[:, 2], (U * np.cos(th) + V * np.sin(th)) / u_ref, atol=1e-12)
+    np.testing.assert_allclose(pm[:, 3], g * X / 3.0, rtol=1e-10)
+    assert out[0] == pytest.approx(np.hypot(U, V).mean() / u_ref, rel=1e-11)
+
+
+def test_diagnostics_rigid_rotation_has_no_residual():
+    """A fluid in rigid motion with the body (translation plus rotation) leaves no
+    slip, no flux and no interior residual; a sign slip in v + omega x r would
+    leave 2 omega r."""
+    nx, ny = 64, 64
+    x, y = _grid(nx, ny)
+    xc, yc, R, vx, vy, om = 31.4, 32.9, 11.0, 0.01, -0.02, 0.003
+    ux, uy = vx - om * (y - yc), vy + om * (x - xc)
+    md, th = _diag_markers(xc, yc, R, 70)
+    md[:, 2] = vx - om * (md[:, 1] - yc)
+    md[:, 3] = vy + om * (md[:, 0] - xc)
+    for kernel in (oracle.HAT, oracle.PESKIN4):
+        out = oracle.local_diagnostics_fields(kernel, np.ones((ny, nx)), ux, uy, md, 1.0,
+                                              [xc, yc, vx, vy, om, R], 0.1)
+        assert out[0] < 1e-12 and out[2] < 1e-12 and abs(out[3]) < 1e-13 and out[5] < 1e-12
+        assert out[6] > 200
+
+
+@pytest.mark.parametrize("clockwise", [False, True])
+def test_diagnostics_radial_source_flux(clockwise):
+    """Radial expansion u = s (x - X_c) through markers on a circle of radius R
+    crosses it at s R everywhere; with rho = 1 + g x the net flux over u_ref n ds
+    is s R (1 + g X_c) / u_ref.  The outward normal must not depend on the marker
+    order, and the marker forces give sum |F_k|."""
+    nx = ny = 60
+    x, y = _grid(nx, ny)
+    xc, yc, R, s, g, u_ref = 29.6, 30.2, 8.0, 0.002, 0.001, 0.1
+    ux, uy, rho = s * (x - xc), s * (y - yc), 1.0 + g * x
+    md, th = _diag_markers(xc, yc, R, 48, clockwise=clockwise)
+    md[:, 4], md[:, 5] = 3.0 * np.cos(th), 4.0 * np.sin(th)
+    out = oracle.local_diagnostics_fields(oracle.PESKIN4, rho, ux, uy, md, 1.05, [xc, yc, 0, 0, 0, R], u_ref)
+    assert out[3] == pytest.approx(s * R * (1 + g * xc) / u_ref, rel=1e-11)
+    assert out[4] == pytest.approx(out[3], rel=1e-12)
+    assert out[7] == pytest.approx(np.hypot(3.0 * np.cos(th), 4.0 * np.sin(th)).sum(), rel=1e-13)
