@@ -171,6 +171,30 @@ int iblbm_marker_data(iblbm_ctx* ctx, int body_id, double* out);
 /* Stencil origin (i0, j0) of each marker for the last step into ij[2*n]: the
  * footprint is i0..i0+S-1 x j0..j0+S-1, S = 2 (hat) or 4 (Peskin).  Syncs. */
 int iblbm_marker_stencils(iblbm_ctx* ctx, int body_id, int* ij);
+/* Local boundary-fidelity diagnostics of Sec. 2.8 for body body_id on the state
+ * after the last step, with the bilinear probe of Sec. 4.2.  The fluid fields
+ * are the density and Eq. 4 velocity of the last collision (as iblbm_get_macro);
+ * X_k, U_d,k and F_k are the marker data of iblbm_marker_data; u_ref > 0 is the
+ * reference speed (U_inf), kappa >= 0 the buffer width in lattice units (the
+ * paper takes 2).  out[8]:
+ *   [0] mean over markers of |U(X_k) - U_d,k| / u_ref, U interpolated with the
+ *       body's kernel (Eq. 7): the slip error eps_slip
+ *   [1] max over markers of the same
+ *   [2] max over markers of the same with U from the bilinear probe
+ *   [3] leakage Phi_leak: sum_k rho(X_k) (U - U_d,k).n_k ds / (u_ref n ds), n_k the
+ *       outward unit normal of the chord X_{k+1} - X_{k-1} (radial when n < 3);
+ *       n ds is pi D for a circle
+ *   [4] the same with |(U - U_d,k).n_k| (gross flux)
+ *   [5] mean over nodes with |x - X_c| < R - kappa (strict; R the body radius) of
+ *       |u(x) - (v + omega x (x - X_c))| / u_ref: the internal residual velocity
+ *   [6] the number of those nodes
+ *   [7] sum_k |F_k|
+ * per_marker[5*n] (host, may be NULL): per marker [0] and the bilinear slip,
+ * (U - U_d,k).n_k / u_ref, (rho_bilinear(X_k) - 1) c_s^2 and |F_k|.  Sums are
+ * FP64.  Errors: INVALID_ARG, MARKER_OUT_OF_DOMAIN (a stencil or probe node
+ * outside the lattice), OOM.  Syncs. */
+int iblbm_local_diagnostics(iblbm_ctx* ctx, int body_id, double u_ref, double kappa, double out[8],
+                            double* per_marker);
 /* MDF diagnostics of the last step: increments applied, last L_inf residual
  * (FP64) and omega_MDF.  Syncs. */
 int iblbm_mdf_info(iblbm_ctx* ctx, int body_id, int* iterations, double* residual, double* omega);

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("iblbm_marker_data", _i, [_vp, _i, _pd]),
     ("iblbm_marker_stencils", _i, [_vp, _i, _pi]),
     ("iblbm_mdf_info", _i, [_vp, _i, _pi, _pd, _pd]),
+    ("iblbm_local_diagnostics", _i, [_vp, _i, C.c_double, C.c_double, _pd, _vp]),
     ("iblbm_get_populations", _i, [_vp, _pd, _i]),
     ("iblbm_set_populations", _i, [_vp, _pd]),
     ("iblbm_get_macro", _i, [_vp, _pd, _pd, _pd]),
@@ -315,6 +316,19 @@ class Lattice:
         _check(load_library().iblbm_mdf_info(self._h, b, C.byref(it), C.byref(res), C.byref(om)),
                "iblbm_mdf_info")
         return it.value, res.value, om.value
+
+    def local_diagnostics(self, b: int = 0, u_ref: float = 0.1, kappa: float = 2.0, per_marker: bool = False):
+        """Sec. 2.8 diagnostics of body ``b`` (iblbm_local_diagnostics): out[8] =
+        slip mean, slip max, bilinear slip max, net and gross leakage, interior
+        residual, interior node count, sum |F_k|; with ``per_marker`` also the
+        [n, 5] table (kernel slip, bilinear slip, normal velocity, pressure
+        residual, |F_k|)."""
+        out = np.zeros(8)
+        pm = np.zeros((self.body_n[b], 5)) if per_marker else None
+        _check(load_library().iblbm_local_diagnostics(self._h, b, u_ref, kappa, _dp(out),
+                                                       pm.ctypes.data if pm is not None else None),
+               "iblbm_local_diagnostics")
+        return (out, pm) if per_marker else out
 
     def populations(self, shifted: bool = False) -> np.ndarray:
         out = np.zeros((9, self.ny, self.nx))

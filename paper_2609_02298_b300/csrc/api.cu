@@ -511,6 +511,27 @@ int iblbm_marker_data(iblbm_ctx* c, int id, double* out) {
     return check(cudaGetLastError()) ? IBLBM_ERR_CUDA : rc;
 }
 
+int iblbm_local_diagnostics(iblbm_ctx* c, int id, double u_ref, double kappa, double out[8], double* per_marker) {
+    if (!body_index_ok(c, id) || !out || !(u_ref > 0.0) || !(kappa >= 0.0) || !(u_ref < 1e300) || !(kappa < 1e300))
+        return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    const int n = fetch_body(c, id).n;
+    const size_t words = 9 + (per_marker ? 5 * (size_t)n : 0);
+    double* d = static_cast<double*>(dev_alloc(8 * words, c->work));
+    if (!d) return IBLBM_ERR_OOM;
+    std::vector<double> h(words);
+    int e = check(launch_diagnostics(&c->hc, c->dc, id, u_ref, kappa, d, per_marker ? d + 9 : nullptr, c->work));
+    if (!e) e = check(cudaMemcpyAsync(h.data(), d, 8 * words, cudaMemcpyDeviceToHost, c->work));
+    if (!e) e = check(cudaStreamSynchronize(c->work));
+    dev_free(d, c->work);
+    if (e) return e;
+    if (h[8] != 0.0) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
+    std::memcpy(out, h.data(), 8 * sizeof(double));
+    if (per_marker) std::memcpy(per_marker, h.data() + 9, 5 * (size_t)n * sizeof(double));
+    return rc;
+}
+
 int iblbm_marker_stencils(iblbm_ctx* c, int id, int* ij) {
     if (!body_index_ok(c, id) || !ij) return IBLBM_ERR_INVALID_ARG;
     int rc = sync_status(c);

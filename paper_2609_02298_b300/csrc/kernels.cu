@@ -1508,30 +1508,204 @@ __global__ void fill_eq_kernel(const CaseDev* __restrict__ Cp, double rho, doubl
     }
 }
 
+// Density and Eq. 4 velocity of the last collision at node (x, y), from the stored
+// post-collision state: its first moment is rho u + F/2 for the force F of that step.
+template <class S>
+__device__ __forceinline__ void node_macro(const CaseDev& C, const S* src, int x, int y, double& r, double& u,
+                                           double& v) {
+    using R = typename Traits<S>::R;
+    double drho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        const double f = (double)ld1(src + i * C.plane + (long long)y * C.pitch + x);
+        drho += f;
+        jx += ex(i) * f;
+        jy += ey(i) * f;
+    }
+    R s[9];
+    for (int i = 0; i < 9; ++i) s[i] = R(0);
+    R Fx = R(C.gfx), Fy = R(C.gfy);
+    add_ib<R>(C, x, y, s, Fx, Fy);
+    r = 1.0 + drho;
+    u = (jx - 0.5 * (double)Fx) / r;
+    v = (jy - 0.5 * (double)Fy) / r;
+}
+
 template <class S>
 __global__ void macro_kernel(const CaseDev* __restrict__ Cp, double* rho, double* ux, double* uy) {
-    using R = typename Traits<S>::R;
     const CaseDev& C = *Cp;
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
     const long long N = (long long)C.nx * C.ny;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(q / C.nx), x = (int)(q % C.nx);
-        double drho = 0.0, jx = 0.0, jy = 0.0;
-        for (int i = 0; i < 9; ++i) {
-            const double v = (double)ld1(src + i * C.plane + (long long)y * C.pitch + x);
-            drho += v;
-            jx += ex(i) * v;
-            jy += ey(i) * v;
-        }
-        R s[9];
-        for (int i = 0; i < 9; ++i) s[i] = R(0);
-        R Fx = R(C.gfx), Fy = R(C.gfy);
-        add_ib<R>(C, x, y, s, Fx, Fy);
-        const double r = 1.0 + drho;
-        rho[q] = r;
-        ux[q] = (jx - 0.5 * (double)Fx) / r;
-        uy[q] = (jy - 0.5 * (double)Fy) / r;
+        node_macro<S>(C, src, x, y, rho[q], ux[q], uy[q]);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Local boundary-fidelity diagnostics of one body (Sec. 2.8; bilinear probe of Sec. 4.2),
+// one CTA.  Per marker: the fluid velocity and density interpolated with the body's own
+// kernel (Eq. 7) and with the bilinear probe from node_macro, the slip against the
+// marker's desired velocity, the normal velocity through the marker polygon (outward
+// normal of the chord X_{k+1} - X_{k-1}; radial below three markers) and |F_k|.  Inside
+// the body the nodes with |x - X_c| < R - kappa give the residual against the rigid
+// velocity v + omega x (x - X_c).  out[0..7] as the C-ABI documents, out[8] = 1 when a
+// stencil or probe node lies outside the lattice; pm[5n] (or null) per marker.
+constexpr int kDiagThreads = 256;
+
+template <class S>
+__global__ void __launch_bounds__(kDiagThreads) diag_kernel(const CaseDev* __restrict__ Cp, int body, double u_ref,
+                                                          double kappa, double* __restrict__ out,
+                                                          double* __restrict__ pm) {
+    __shared__ double red[7][kDiagThreads];
+    __shared__ long long cnt_s[kDiagThreads];
+    __shared__ int bad_s[kDiagThreads];
+    const CaseDev& C = *Cp;
+    const BodyDev& B = C.bodies[body];
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    const int tid = threadIdx.x, n = B.n, kern = B.kernel, SW = kern == K_HAT ? 2 : 4;
+    const double xc = B.st.xc, yc = B.st.yc, ds = B.ds;
+    double slip_sum = 0.0, slip_max = 0.0, bl_max = 0.0, net = 0.0, gross = 0.0, fsum = 0.0;
+    int bad = 0;
+    for (int k = tid; k < n; k += kDiagThreads) {
+        const double X = B.X[k], Y = B.Y[k], Udx = B.Udx[k], Udy = B.Udy[k];
+        const int b0 = (int)floor(X), c0 = (int)floor(Y);
+        const int i0 = b0 - (kern == K_HAT ? 0 : 1), j0 = c0 - (kern == K_HAT ? 0 : 1);
+        if (!(X == X) || !(Y == Y) || i0 < 0 || j0 < 0 || i0 + SW > C.nx || j0 + SW > C.ny || b0 < 0 || c0 < 0 ||
+            b0 + 2 > C.nx || c0 + 2 > C.ny) {
+            bad = 1;
+            continue;
+        }
+        double U = 0.0, V = 0.0, rk = 0.0;
+        for (int b = 0; b < SW; ++b) {
+            const double py = phi<double>(kern, (double)(j0 + b) - Y);
+            for (int a = 0; a < SW; ++a) {
+                const double D = phi<double>(kern, (double)(i0 + a) - X) * py;
+                double r, u, v;
+                node_macro<S>(C, src, i0 + a, j0 + b, r, u, v);
+                U += u * D;
+                V += v * D;
+                rk += r * D;
+            }
+        }
+        const double fx = X - b0, fy = Y - c0;
+        double Ub = 0.0, Vb = 0.0, rb = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            const int a = c & 1, b = c >> 1;
+            const double w = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+            double r, u, v;
+            node_macro<S>(C, src, b0 + a, c0 + b, r, u, v);
+            Ub += u * w;
+            Vb += v * w;
+            rb += r * w;
+        }
+        double nxk = 0.0, nyk = 0.0;
+        if (n >= 3) {
+            const int kp = k + 1 == n ? 0 : k + 1, km = k == 0 ? n - 1 : k - 1;
+            const double tx = B.X[kp] - B.X[km], ty = B.Y[kp] - B.Y[km];
+            const double t = sqrt(tx * tx + ty * ty);
+            if (t > 0.0) {
+                nxk = ty / t;
+                nyk = -tx / t;
+            }
+            if (nxk * (X - xc) + nyk * (Y - yc) < 0.0) {
+                nxk = -nxk;
+                nyk = -nyk;
+            }
+        } else {
+            const double r = sqrt((X - xc) * (X - xc) + (Y - yc) * (Y - yc));
+            if (r > 0.0) {
+                nxk = (X - xc) / r;
+                nyk = (Y - yc) / r;
+            }
+        }
+        const double s = sqrt((U - Udx) * (U - Udx) + (V - Udy) * (V - Udy)) / u_ref;
+        const double sb = sqrt((Ub - Udx) * (Ub - Udx) + (Vb - Udy) * (Vb - Udy)) / u_ref;
+        const double un = (U - Udx) * nxk + (V - Udy) * nyk;
+        const double fm = sqrt(B.Fx[k] * B.Fx[k] + B.Fy[k] * B.Fy[k]);
+        slip_sum += s;
+        slip_max = fmax(slip_max, s);
+        bl_max = fmax(bl_max, sb);
+        net += rk * un * ds;
+        gross += rk * fabs(un) * ds;
+        fsum += fm;
+        if (pm) {
+            pm[5 * k + 0] = s;
+            pm[5 * k + 1] = sb;
+            pm[5 * k + 2] = un / u_ref;
+            pm[5 * k + 3] = (rb - 1.0) / 3.0;
+            pm[5 * k + 4] = fm;
+        }
+    }
+    // interior nodes beyond the buffer; the strict test is taken with single roundings
+    // (no fused multiply-add) so that it decides every node as a plain FP64 evaluation does
+    double in_sum = 0.0;
+    long long cnt = 0;
+    const double ri = B.radius - kappa;
+    if (ri > 0.0) {
+        const double rr = __dmul_rn(ri, ri);
+        const int x0 = max(0, (int)floor(xc - ri)), x1 = min(C.nx - 1, (int)ceil(xc + ri));
+        const int y0 = max(0, (int)floor(yc - ri)), y1 = min(C.ny - 1, (int)ceil(yc + ri));
+        const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
+        if (bw > 0 && bh > 0) {
+            for (long long q = tid; q < (long long)bw * bh; q += kDiagThreads) {
+                const int x = x0 + (int)(q % bw), y = y0 + (int)(q / bw);
+                const double dx = (double)x - xc, dy = (double)y - yc;
+                if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < rr) {
+                    double r, u, v;
+                    node_macro<S>(C, src, x, y, r, u, v);
+                    const double eu = u - (B.st.vx - B.st.om * dy), ev = v - (B.st.vy + B.st.om * dx);
+                    in_sum += sqrt(eu * eu + ev * ev);
+                    ++cnt;
+                }
+            }
+        }
+    }
+    red[0][tid] = slip_sum;
+    red[1][tid] = slip_max;
+    red[2][tid] = bl_max;
+    red[3][tid] = net;
+    red[4][tid] = gross;
+    red[5][tid] = fsum;
+    red[6][tid] = in_sum;
+    cnt_s[tid] = cnt;
+    bad_s[tid] = bad;
+    __syncthreads();
+    if (tid == 0) {
+        double a[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        long long c = 0;
+        int anybad = 0;
+        for (int t = 0; t < kDiagThreads; ++t) {
+            a[0] += red[0][t];
+            a[1] = fmax(a[1], red[1][t]);
+            a[2] = fmax(a[2], red[2][t]);
+            a[3] += red[3][t];
+            a[4] += red[4][t];
+            a[5] += red[5][t];
+            a[6] += red[6][t];
+            c += cnt_s[t];
+            anybad |= bad_s[t];
+        }
+        const double norm = u_ref * n * ds;
+        out[0] = n > 0 ? a[0] / n : 0.0;
+        out[1] = a[1];
+        out[2] = a[2];
+        out[3] = n > 0 ? a[3] / norm : 0.0;
+        out[4] = n > 0 ? a[4] / norm : 0.0;
+        out[5] = c > 0 ? a[6] / (double)c / u_ref : 0.0;
+        out[6] = (double)c;
+        out[7] = a[5];
+        out[8] = anybad ? 1.0 : 0.0;
+    }
+}
+
+cudaError_t launch_diagnostics(const CaseDev* hc, CaseDev* dc, int body, double u_ref, double kappa, double* out,
+                               double* pm, cudaStream_t st) {
+    switch (hc->storage) {
+    case ST_F64: IBLBM_LAUNCH(diag_kernel<double>, 1, kDiagThreads, st, dc, body, u_ref, kappa, out, pm); break;
+    case ST_F32: IBLBM_LAUNCH(diag_kernel<float>, 1, kDiagThreads, st, dc, body, u_ref, kappa, out, pm); break;
+    default: IBLBM_LAUNCH(diag_kernel<__half>, 1, kDiagThreads, st, dc, body, u_ref, kappa, out, pm); break;
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------

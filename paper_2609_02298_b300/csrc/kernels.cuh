@@ -67,6 +67,9 @@ cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shift
 cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st);
 cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st);
 cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux, double* uy, cudaStream_t st);
+// Sec. 2.8 local diagnostics of one body into out[9] (and pm[5n] unless null), one CTA.
+cudaError_t launch_diagnostics(const CaseDev* hc, CaseDev* dc, int body, double u_ref, double kappa, double* out,
+                               double* pm, cudaStream_t st);
 int sc_blocks_per_sm(int storage, int collision, int variant);
 
 }  // namespace iblbm

@@ -53,6 +53,10 @@ inline long long emu_to_bits_ll(double v) {
 template <class T>
 inline void __stcg(T* p, T v) { *p = v; }
 inline long long __double_as_longlong(double v) { return emu_to_bits_ll(v); }
+// round-to-nearest FP64 product and sum (the host build targets x86-64 without FMA,
+// so these are single roundings as on the device)
+inline double __dmul_rn(double a, double b) { return a * b; }
+inline double __dadd_rn(double a, double b) { return a + b; }
 inline double __longlong_as_double(long long v) {
     double d;
     std::memcpy(&d, &v, sizeof(d));

@@ -1,0 +1,160 @@
+"""Paper-scale fixed-cylinder runs (Sec. 2.9.1, Table I) through the library,
+for comparison with the paper's Table II (drag) and Table III (slip).
+
+Setup as Sec. 2.9.1 states it: a [0, 1.25] x [0, 1] domain, the cylinder centre
+at (0.4 Lx, 0.5 Ly), Dirichlet inflow on the west side and on the south and
+north sides (u = (u_inf, 0), u_inf = 0.1), zero-gradient outflow on the east
+side; 2001 x 1601 nodes with D = 40 for Re <= 100 and 3001 x 2401 with D = 60
+for Re = 200; n = round(pi D) markers (ds ~ 1); tau = 1/2 + 3 u_inf D / Re;
+BGK; adaptive MDF with N in [5, 20] and tol 1e-4.  C_d = 2 F_x / (u_inf^2 D)
+with the force history sampled every 200 steps and averaged over steps
+70,200-100,000 (Re <= 100) or 30,200-60,000 (Re = 200); the slip is taken
+at the last step with ``iblbm_local_diagnostics``.
+
+The paper does not say how its shedding starts.  A perfectly symmetric start
+sheds late on a lattice this large (at Re = 200 the shedding is still growing
+at step 30,000), so ``trigger_steps > 0`` spins the cylinder at
+omega = u_inf / R for that many steps first (a start-up rotation, the usual
+symmetry breaker), then holds it fixed for the rest of the run.  The script
+applies it to the unsteady rows (Re >= 100) only: at Re = 20 and 40 the same
+rotation excites a lift oscillation with the period of a sound wave crossing
+between the south and north sides (Ly / c_s ~ 2,770 steps) that is still
+growing at step 100,000, while the symmetric start settles to a steady state.
+
+Run as a script it writes one JSON record per case:
+    python tests/paper_scale.py --re 20,40,100,200 --trigger 2000 --out results.json
+"""
+import argparse
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fixed_cylinder_tables.txt")
+U_INF = 0.1
+SCHEME_NAMES = {W.DF: "DF", W.MDF: "MDF", W.DFC: "DFC"}
+KERNEL_NAMES = {W.HAT: "hat", W.PESKIN4: "P4"}
+
+
+def paper_tables():
+    """{(re, kernel name): {"cd": {scheme: value}, "slip": {scheme: value}}} from the golden file."""
+    out = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            v = [float(x) for x in t[2:]]
+            out[(int(t[0]), t[1])] = {"cd": dict(zip(("DF", "MDF", "DFC"), v[:3])),
+                                      "slip": dict(zip(("DF", "MDF", "DFC"), v[3:]))}
+    return out
+
+
+def protocol(re):
+    """(nx, ny, D, steps, first averaged step) of Table I for one Reynolds number."""
+    if re <= 100:
+        return 2001, 1601, 40.0, 100000, 70200
+    return 3001, 2401, 60.0, 60000, 30200
+
+
+def build_row(L, re, storage=W.F32, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W.MDF, W.DFC)):
+    """The lattices of one Table II row: one per (kernel, scheme)."""
+    nx, ny, D, steps, _ = protocol(re)
+    xc, yc = 0.4 * (nx - 1), 0.5 * (ny - 1)
+    nb = int(round(math.pi * D))
+    tau = W.tau_for(U_INF, D, re)
+    xy, ds = W.circle_markers(xc, yc, D, nb)
+    bc = (W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY)
+    ubc = ((U_INF, 0.0), (0.0, 0.0), (U_INF, 0.0), (U_INF, 0.0))
+    cases = []
+    for kern in kernels:
+        for sch in schemes:
+            lat = L.Lattice(nx, ny, W.BGK, tau, storage, bc, ubc, init_u=(U_INF, 0.0))
+            lat.add_body(xy, ds, kern, sch, xc=xc, yc=yc, radius=0.5 * D, mdf_nmin=5, mdf_nmax=20,
+                         mdf_tol=1e-4, history_cap=steps)
+            cases.append({"re": re, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch], "lat": lat})
+    return cases
+
+
+def run_row(L, re, storage=W.F32, trigger_steps=0, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W.MDF, W.DFC),
+            chunk=5000):
+    """Runs one row as one batch and returns a record per case (the lattices are closed)."""
+    nx, ny, D, steps, avg_from = protocol(re)
+    cases = build_row(L, re, storage, kernels, schemes)
+    lats = [c["lat"] for c in cases]
+    left = steps
+    if trigger_steps > 0:
+        om = U_INF / (0.5 * D)
+        for lat in lats:
+            lat.move_body(0, None, (0.0, 0.0, om))
+        L.step_batch(lats, trigger_steps)
+        for lat in lats:
+            lat.move_body(0, None, (0.0, 0.0, 0.0))
+        left -= trigger_steps
+    while left > 0:
+        n = min(left, chunk)
+        L.step_batch(lats, n)
+        left -= n
+    out = []
+    for c in cases:
+        lat = c.pop("lat")
+        status = lat.sync()
+        h = lat.force_history(0, cap=steps)
+        stepno = np.arange(steps - len(h) + 1, steps + 1)
+        sample = stepno % 200 == 0
+        cd = 2.0 * h[:, 0] / (U_INF * U_INF * D)
+        cl = 2.0 * h[:, 1] / (U_INF * U_INF * D)
+        win = sample & (stepno >= avg_from)
+        tail = cl[stepno >= avg_from]
+        x = tail - tail.mean()
+        spec = np.abs(np.fft.rfft(x * np.hanning(len(x))))
+        st = float(np.fft.rfftfreq(len(x))[int(np.argmax(spec[1:])) + 1] * D / U_INF) if re >= 100 else None
+        d = lat.local_diagnostics(0, U_INF, 2.0)
+        c.update(cd=float(cd[win].mean()), cl_rms=float(np.sqrt((x * x).mean())),
+                 cl_amp=float(0.5 * (tail.max() - tail.min())), st=st, slip=float(d[0]), slip_max=float(d[1]),
+                 bilinear_slip_max=float(d[2]), leakage=float(d[3]), leakage_gross=float(d[4]),
+                 u_inside=float(d[5]), n_inside=int(d[6]), status=int(status), steps=steps,
+                 cd_series=[float(v) for v in cd[sample]])
+        if c["scheme"] == "MDF":
+            c["mdf_iterations"], c["mdf_residual"], c["mdf_omega"] = lat.mdf_info(0)
+        lat.close()
+        out.append(c)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--re", default="20,40,100,200")
+    ap.add_argument("--trigger", type=int, default=2000,
+                    help="start-up rotation steps for the rows with Re >= 100 (0: symmetric start everywhere)")
+    ap.add_argument("--storage", default="f32", choices=sorted(W.STORAGES))
+    ap.add_argument("--out", default="fixed_cylinder_tables.json")
+    args = ap.parse_args()
+    import torch
+    import paper_2609_02298_b300 as L
+    torch.cuda.set_device(0)
+    L.use_torch_allocator()
+    paper = paper_tables()
+    rows = []
+    for re in [int(v) for v in args.re.split(",")]:
+        trigger = args.trigger if re >= 100 else 0
+        for r in run_row(L, re, W.STORAGES[args.storage], trigger):
+            p = paper[(re, r["kernel"])]
+            r["paper_cd"], r["paper_slip"] = p["cd"][r["scheme"]], p["slip"][r["scheme"]]
+            r["trigger_steps"] = trigger
+            rows.append(r)
+            print(json.dumps({k: v for k, v in r.items() if k != "cd_series"}), flush=True)
+    with open(args.out, "w") as fh:
+        json.dump(rows, fh)
+
+
+if __name__ == "__main__":
+    main()

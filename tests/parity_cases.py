@@ -424,3 +424,44 @@ def check_server_alone_vs_mix(L, cases, budget_lattices=2.5, max_steps=8):
     else:
         raise AssertionError("oversized request was not rejected")
     srv.close()
+
+
+# ---------------------------------------------------------------- Sec. 2.8 diagnostics
+def _assert_diagnostics(dg, dc, pg, pc, tol):
+    """Slip, leakage and interior values are normalised by u_ref (O(1) at most);
+    the interior count is decided in FP64 on both sides and must be equal."""
+    assert dg[6] == dc[6] and dc[6] > 0
+    np.testing.assert_allclose(dg[[0, 1, 2, 3, 4, 5]], dc[[0, 1, 2, 3, 4, 5]], rtol=tol, atol=tol * 1e-2)
+    np.testing.assert_allclose(dg[7], dc[7], rtol=tol)
+    np.testing.assert_allclose(pg[:, :3], pc[:, :3], rtol=tol, atol=tol * 1e-2)
+    np.testing.assert_allclose(pg[:, 3], pc[:, 3], rtol=tol, atol=tol * 1e-4)
+    np.testing.assert_allclose(pg[:, 4], pc[:, 4], rtol=tol, atol=tol * 1e-3 * pc[:, 4].max())
+
+
+def check_local_diagnostics(scheme, kernel, storage=W.F64, nx=150, ny=64, D=16.0, n=47, steps=60):
+    """Fixed cylinder in the channel: the device diagnostics of the device state
+    against the oracle's diagnostics of its own state.  FP64: 1e-9 relative (the
+    slip is a small difference of interpolated velocities, so it carries the
+    state's 1e-12 at up to 1e3 times the weight); FP32 shifted storage 2e-3."""
+    body = cylinder_body(0.27 * nx, 0.495 * ny, D, n, kernel, scheme, mdf_nmin=2, mdf_nmax=12, mdf_tol=1e-4)
+    spec = channel_spec(nx, ny, collision=W.BGK, tau=0.68, storage=storage, u=0.06, bodies=[body])
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    dg, pg = g.local_diagnostics(0, 0.06, 2.0, per_marker=True)
+    dc, pc = c.local_diagnostics(0, 0.06, 2.0, per_marker=True)
+    _assert_diagnostics(dg, dc, pg, pc, 1e-9 if storage == W.F64 else 2e-3)
+    # a wider buffer keeps fewer interior nodes
+    assert g.local_diagnostics(0, 0.06, 4.0)[6] == c.local_diagnostics(0, 0.06, 4.0)[6] < dc[6]
+
+
+def check_local_diagnostics_free_body(scheme=W.DF, steps=60):
+    """Settling disk: the interior residual is taken against the rigid velocity of
+    the moving body and the slip against the markers' desired velocity."""
+    spec = W.sedimentation(two_particles=False, storage=W.F64, internal_mass=1, kernel=W.PESKIN4, scheme=scheme,
+                           nx=64, ny=160, diameter=12.0, tau=0.7, g=1e-4)
+    g, c = gpu_case(spec), oracle_case(spec)
+    stepped(g, c, steps)
+    dg, pg = g.local_diagnostics(0, 0.01, 2.0, per_marker=True)
+    dc, pc = c.local_diagnostics(0, 0.01, 2.0, per_marker=True)
+    assert abs(g.body_state(0)[3]) > 1e-5
+    _assert_diagnostics(dg, dc, pg, pc, 1e-9)

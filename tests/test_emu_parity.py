@@ -191,3 +191,15 @@ def test_bulk_copy_that_never_lands_reports_timeout(L, monkeypatch):
     h.step(2)
     assert h.sync() == 0
     h.close()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_local_diagnostics(L, scheme, kernel):
+    full_only(L)
+    P.check_local_diagnostics(scheme, kernel, nx=70, ny=40, D=12.0, n=37, steps=12)
+
+
+def test_local_diagnostics_free_body(L):
+    full_only(L)
+    P.check_local_diagnostics_free_body(steps=10)

@@ -146,3 +146,14 @@ def test_full_size_2048x1024_f32_window():
     assert rel_l2(np.stack(ug), np.stack(uc)) < 1e-5
     hg, hc = g.force_history(0), c.force_history(0)
     assert np.abs(hg[:, 0] - hc[:, 0]).max() < 1e-4 * np.abs(hc[:, 0]).max()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("storage", [W.F64, W.F32])
+def test_local_diagnostics(scheme, kernel, storage):
+    P.check_local_diagnostics(scheme, kernel, storage=storage)
+
+
+def test_local_diagnostics_free_body():
+    P.check_local_diagnostics_free_body()
