@@ -165,6 +165,14 @@ int iblbm_force_history(iblbm_ctx* ctx, int body_id, double* out, int cap, int* 
  * U_d = v + omega x (X - X_c).  Errors: INVALID_ARG (not FIXED), MARKER_OUT_OF_DOMAIN. */
 int iblbm_move_body(iblbm_ctx* ctx, int body_id, const double* xy, const double uvw[3]);
 
+/* FIXED bodies only: sets the desired velocity U_d,k of every marker, ud[2*n] =
+ * (U_d,x, U_d,y) per marker in lattice units (|component| < 1), used by the IB
+ * stage (Eq. 13) from the next step on instead of v + omega x (X - X_c), until
+ * the next call, iblbm_move_body with uvw, or ud = NULL (back to the rigid
+ * velocity).  App. D.1 drives markers this way with the analytical Taylor-Green
+ * field.  The setting is not part of a checkpoint.  Errors: INVALID_ARG (bad
+ * body, not FIXED, a component out of range).  Syncs. */
+int iblbm_set_marker_velocity(iblbm_ctx* ctx, int body_id, const double* ud);
 /* Per-marker data of the last step into out[7*n]: X, Y, U_d,x, U_d,y, force x,
  * force y (DF: F_L, MDF: F_total, DFC: F_s), lambda_k (DFC, else 0).  Syncs. */
 int iblbm_marker_data(iblbm_ctx* ctx, int body_id, double* out);

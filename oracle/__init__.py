@@ -92,6 +92,7 @@ def lib():
             "orc_verlet_free_fall": (None, [d, d, d, d, i, i, pd, pd]),
             "orc_local_diagnostics_fields": (i, [i, i, i, pd, pd, pd, pd, i, d, pd, d, d, pd, vp]),
             "orc_local_diagnostics": (i, [vp, i, d, d, pd, vp]),
+            "orc_set_marker_velocity": (i, [vp, i, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -274,6 +275,15 @@ class Case:
 
     def mdf_residual(self, b: int) -> float:
         return lib().orc_mdf_residual(self._h, b)
+
+    def set_marker_velocity(self, b: int, ud=None) -> None:
+        if ud is None:
+            rc = lib().orc_set_marker_velocity(self._h, b, None)
+        else:
+            ud = np.ascontiguousarray(ud, dtype=np.float64).reshape(-1, 2)
+            rc = lib().orc_set_marker_velocity(self._h, b, ud.ctypes.data)
+        if rc:
+            raise ValueError("orc_set_marker_velocity: bad body or moving body")
 
     def local_diagnostics(self, b: int, u_ref: float, kappa: float = 2.0, per_marker: bool = False):
         out = np.zeros(8)

@@ -34,6 +34,7 @@ typedef struct {
     double *X, *Y;      /* marker positions for the current step */
     double *r0x, *r0y;  /* marker offsets from the centre at theta = 0 */
     double *Udx, *Udy;  /* desired marker velocity */
+    int ud_given;       /* fixed body whose U_d was set per marker (orc_set_marker_velocity) */
     double *Fx, *Fy;    /* DF/MDF: Lagrangian force F_L (MDF: F_total); DFC: F_s */
     double *lambda;     /* DFC scaling factor, Eq. 17 */
     /* rigid-body state, Sec. 2.7 */
@@ -543,9 +544,23 @@ static void prepare_body(orc_case* c, orc_body* B) {
             B->Udx[k] = vx;
             B->Udy[k] = 0.0;
         }
-    } else {
+    } else if (!B->ud_given) {
         for (int k = 0; k < B->n; ++k) { B->Udx[k] = 0.0; B->Udy[k] = 0.0; }
     }
+}
+
+/* Desired velocity per marker of a fixed body (App. D.1 drives the markers with
+ * the analytical Taylor-Green field); NULL returns to U_d = 0. */
+int orc_set_marker_velocity(orc_case* c, int b, const double* ud) {
+    if (b < 0 || b >= c->nbodies) return 1;
+    orc_body* B = &c->bodies[b];
+    if (B->p.motion != ORC_FIXED) return 1;
+    B->ud_given = ud != NULL;
+    for (int k = 0; k < B->n; ++k) {
+        B->Udx[k] = ud ? ud[2 * k] : 0.0;
+        B->Udy[k] = ud ? ud[2 * k + 1] : 0.0;
+    }
+    return 0;
 }
 
 /* Second half of Eq. 23 and the internal-mass increment of Eq. A3. */

@@ -75,6 +75,10 @@ int       orc_mdf_iterations(const orc_case* c, int b);
 double    orc_mdf_omega(const orc_case* c, int b);
 double    orc_mdf_residual(const orc_case* c, int b);
 
+/* Fixed bodies: desired velocity of every marker (ud[2*n]) from the next step on,
+ * or NULL for U_d = 0.  Returns 0, or 1 for a bad index or a moving body. */
+int orc_set_marker_velocity(orc_case* c, int b, const double* ud);
+
 /* Local boundary-fidelity diagnostics of Sec. 2.8 (with the bilinear probe of
  * Sec. 4.2) from node fields rho, ux, uy [ny*nx] and one body:
  *   md[7*n]   marker data as orc_marker_data writes it (X, Y, U_d, force, lambda)

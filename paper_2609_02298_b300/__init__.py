@@ -74,6 +74,7 @@ SIGNATURES = [
     ("iblbm_marker_stencils", _i, [_vp, _i, _pi]),
     ("iblbm_mdf_info", _i, [_vp, _i, _pi, _pd, _pd]),
     ("iblbm_local_diagnostics", _i, [_vp, _i, C.c_double, C.c_double, _pd, _vp]),
+    ("iblbm_set_marker_velocity", _i, [_vp, _i, _vp]),
     ("iblbm_get_populations", _i, [_vp, _pd, _i]),
     ("iblbm_set_populations", _i, [_vp, _pd]),
     ("iblbm_get_macro", _i, [_vp, _pd, _pd, _pd]),
@@ -316,6 +317,17 @@ class Lattice:
         _check(load_library().iblbm_mdf_info(self._h, b, C.byref(it), C.byref(res), C.byref(om)),
                "iblbm_mdf_info")
         return it.value, res.value, om.value
+
+    def set_marker_velocity(self, b: int, ud=None) -> None:
+        """Desired velocity per marker of a fixed body (``[n, 2]``), or None for the
+        rigid velocity again (iblbm_set_marker_velocity)."""
+        if ud is None:
+            _check(load_library().iblbm_set_marker_velocity(self._h, b, None), "iblbm_set_marker_velocity")
+            return
+        ud = np.ascontiguousarray(ud, dtype=np.float64).reshape(-1, 2)
+        if len(ud) != self.body_n[b]:
+            raise ValueError("expected %d marker velocities" % self.body_n[b])
+        _check(load_library().iblbm_set_marker_velocity(self._h, b, ud.ctypes.data), "iblbm_set_marker_velocity")
 
     def local_diagnostics(self, b: int = 0, u_ref: float = 0.1, kappa: float = 2.0, per_marker: bool = False):
         """Sec. 2.8 diagnostics of body ``b`` (iblbm_local_diagnostics): out[8] =

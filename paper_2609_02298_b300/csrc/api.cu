@@ -486,6 +486,7 @@ int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3])
         b.st.vx = uvw[0];
         b.st.vy = uvw[1];
         b.st.om = uvw[2];
+        b.ud_given = 0;
     }
     cudaMemcpy(&c->dbodies[id], &b, sizeof(BodyDev), cudaMemcpyHostToDevice);
     if (xy)
@@ -493,6 +494,28 @@ int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3])
             int zero = 0;
             cudaMemcpy(&c->dbodies[o].lam_valid, &zero, sizeof(int), cudaMemcpyHostToDevice);
         }
+    return check(cudaGetLastError());
+}
+
+int iblbm_set_marker_velocity(iblbm_ctx* c, int id, const double* ud) {
+    if (!body_index_ok(c, id)) return IBLBM_ERR_INVALID_ARG;
+    if (c->bodies[id].motion != MOT_FIXED) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    const int n = b.n;
+    if (ud) {
+        std::vector<double> U(n), V(n);
+        for (int k = 0; k < n; ++k) {
+            U[k] = ud[2 * k];
+            V[k] = ud[2 * k + 1];
+            if (!(std::fabs(U[k]) < 1.0) || !(std::fabs(V[k]) < 1.0)) return IBLBM_ERR_INVALID_ARG;
+        }
+        cudaMemcpy(b.Udx, U.data(), 8 * (size_t)n, cudaMemcpyHostToDevice);
+        cudaMemcpy(b.Udy, V.data(), 8 * (size_t)n, cudaMemcpyHostToDevice);
+    }
+    const int flag = ud ? 1 : 0;
+    cudaMemcpy(&c->dbodies[id].ud_given, &flag, sizeof(int), cudaMemcpyHostToDevice);
     return check(cudaGetLastError());
 }
 

@@ -79,7 +79,8 @@ struct BodyDev {
     // markers
     double *X, *Y, *r0x, *r0y, *Udx, *Udy, *Fx, *Fy, *lam;
     // footprint: bounding box, box-local node -> slot map, node CSR over markers
-    int bx0, by0, bw, bh, box_cap, nfp, nent, cache_valid, lam_valid, pad0_;
+    int bx0, by0, bw, bh, box_cap, nfp, nent, cache_valid, lam_valid;
+    int ud_given;                 // FIXED: U_d set per marker by the caller, not v + omega x r
     int* node_map;                // [box_cap]
     int* fp_node;                 // [nent] slot -> box-local node
     int* csr_off;                 // [nent + 1]

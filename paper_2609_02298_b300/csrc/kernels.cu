@@ -1387,6 +1387,7 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
 // Body motion at the start of a step (mode PREPARE): first half of Eq. 23 with
 // F_total^n = F_h^n + F_g + dF_IM^n and the torque-only rotation (FREE), x_c(t)
 // at t = n + 1 (PRESCRIBED), then marker positions and U_d = v + omega x (X - X_c).
+// A FIXED body whose desired velocity was set per marker keeps it.
 // At the end of a step (mode FINISH): second half of Eq. 23 and Eq. A3 (FREE),
 // the body and case step counters.
 __global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
@@ -1457,6 +1458,7 @@ __global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
             B.X[k] = xc + rx;
             B.Y[k] = B.yc0 + ry;
         } else {
+            if (B.ud_given) continue;   // desired velocity set per marker by the caller
             rx = B.X[k] - xc;
             ry = B.Y[k] - yc;
         }

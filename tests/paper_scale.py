@@ -130,6 +130,77 @@ def run_row(L, re, storage=W.F32, trigger_steps=0, kernels=(W.HAT, W.PESKIN4), s
     return out
 
 
+# ---- single-particle sedimentation (Sec. 2.9.3, Table IV) ----------------------------
+SED_TAU = {1.01: 0.95, 1.1: 0.64, 1.5: 0.56}
+
+
+def sedimentation_protocol(rho_ratio):
+    """Sec. 2.9.3 in lattice units: W x L = 2 x 6 cm on 1281 x 3841 nodes (dx = W / 1280),
+    d = 0.25 cm (D = 160), released at rest at (1, 4) cm, g = 980 cm/s^2,
+    nu = 0.01 cm^2/s and the paper's tau per density ratio, so dt = nu_lat dx^2 / nu
+    and g_lat = g dt^2 / dx; u_g = sqrt(|rho_r - 1| g_lat D)."""
+    dx = 2.0 / 1280.0
+    tau = SED_TAU[rho_ratio]
+    dt = (tau - 0.5) / 3.0 * dx * dx / 0.01
+    g = 980.0 * dt * dt / dx
+    D = 160.0
+    return {"nx": 1281, "ny": 3841, "D": D, "xc": 640.0, "yc": 2560.0, "tau": tau, "g": g,
+            "u_g": math.sqrt(abs(rho_ratio - 1.0) * g * D)}
+
+
+def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.HAT, W.PESKIN4),
+                      schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000):
+    """All cases as one batch until every particle is within one diameter of the
+    bottom wall (or max_steps); v* = max |v_y| / u_g over the samples taken every
+    ``sample`` steps, with the height where it occurred."""
+    cases = []
+    for rr in rho_ratios:
+        p = sedimentation_protocol(rr)
+        nb = int(round(math.pi * p["D"]))
+        xy, ds = W.circle_markers(p["xc"], p["yc"], p["D"], nb)
+        for kern in kernels:
+            for sch in schemes:
+                lat = L.Lattice(p["nx"], p["ny"], W.BGK, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
+                lat.add_body(xy, ds, kern, sch, xc=p["xc"], yc=p["yc"], radius=0.5 * p["D"], rho_ratio=rr,
+                             motion=W.FREE, gx=0.0, gy=-p["g"], internal_mass=1, mdf_nmin=5, mdf_nmax=20,
+                             mdf_tol=1e-4)
+                cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
+                              "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
+    lats = [c["lat"] for c in cases]
+    steps = 0
+    while steps < max_steps and not all(c["done"] for c in cases):
+        L.step_batch(lats, sample)
+        steps += sample
+        for c in cases:
+            if c["done"]:
+                continue
+            try:
+                st = c["lat"].body_state(0)
+            except Exception as exc:      # a diverged case is recorded, the others go on
+                c["done"], c["error"], c["error_step"] = True, str(exc), steps
+                continue
+            c["vy"].append(float(st[3]))
+            if not c["done"]:
+                if abs(st[3]) > c["vmax"]:
+                    c["vmax"], c["y_at_vmax"] = abs(st[3]), float(st[1])
+                if st[1] < 1.5 * c["p"]["D"] or not np.isfinite(st[1]):
+                    c["done"] = True
+    out = []
+    for c in cases:
+        lat = c.pop("lat")
+        p = c.pop("p")
+        try:
+            status = lat.sync()
+        except Exception as exc:
+            status = str(exc)
+        c.update(v_star=c.pop("vmax") / p["u_g"], u_g=p["u_g"], g=p["g"], tau=p["tau"], steps=steps,
+                 status=status, vy_series=c.pop("vy"))
+        del c["done"]
+        lat.close()
+        out.append(c)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--re", default="20,40,100,200")
@@ -137,11 +208,20 @@ def main():
                     help="start-up rotation steps for the rows with Re >= 100 (0: symmetric start everywhere)")
     ap.add_argument("--storage", default="f32", choices=sorted(W.STORAGES))
     ap.add_argument("--out", default="fixed_cylinder_tables.json")
+    ap.add_argument("--sedimentation", action="store_true",
+                    help="run the Table IV settling matrix instead of the fixed-cylinder rows")
     args = ap.parse_args()
     import torch
     import paper_2609_02298_b300 as L
     torch.cuda.set_device(0)
     L.use_torch_allocator()
+    if args.sedimentation:
+        rows = run_sedimentation(L, storage=W.STORAGES[args.storage])
+        for r in rows:
+            print(json.dumps({k: v for k, v in r.items() if k != "vy_series"}), flush=True)
+        with open(args.out, "w") as fh:
+            json.dump(rows, fh)
+        return
     paper = paper_tables()
     rows = []
     for re in [int(v) for v in args.re.split(",")]:

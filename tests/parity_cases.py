@@ -465,3 +465,25 @@ def check_local_diagnostics_free_body(scheme=W.DF, steps=60):
     dc, pc = c.local_diagnostics(0, 0.01, 2.0, per_marker=True)
     assert abs(g.body_state(0)[3]) > 1e-5
     _assert_diagnostics(dg, dc, pg, pc, 1e-9)
+
+
+# ---------------------------------------------------------------- App. D.1 Taylor-Green, IB mode
+def check_taylor_green_ib(kernel, scheme, D=10, storage=W.F64):
+    """Markers driven per step through iblbm_set_marker_velocity with the analytical
+    field: device and oracle velocity fields and errors after t = D / u0.  FP64
+    within 1e-12 (relative to the field); FP32 storage within 1e-5."""
+    from harness import taylor_green_ib_run, taylor_green_ib_spec
+    spec = taylor_green_ib_spec(D, kernel, scheme, storage=storage)
+    g, c = gpu_case(spec), oracle_case(spec)
+    eg = taylor_green_ib_run(g, spec, D)
+    ec = taylor_green_ib_run(c, spec, D)
+    assert g.sync() >= 0
+    _, gx, gy = g.macro()
+    _, cx, cy = c.macro()
+    tol = F64_TOL if storage == W.F64 else 1e-5
+    assert rel_l2(np.stack([gx, gy]), np.stack([cx, cy])) < tol
+    # the error is a small difference of fields that agree to tol relative to |u|
+    assert abs(eg - ec) < 10 * tol
+    mg, mc = g.marker_data(0), c.marker_data(0)
+    np.testing.assert_allclose(mg[:, 2:4], mc[:, 2:4], rtol=0, atol=1e-15)   # the U_d that was set
+    return eg

@@ -47,3 +47,45 @@ def test_fixed_cylinder_steady_rows_match_tables(re):
         if kern == "P4":
             assert abs(slip["DFC"] / p["slip"]["DFC"] - 1.0) < 0.15
             assert abs(slip["MDF"] / p["slip"]["MDF"] - 1.0) < 0.30
+
+
+KERNEL_OF = {"P4": W.PESKIN4, "hat": W.HAT}
+SCHEME_OF = {"DF": W.DF, "MDF": W.MDF, "DFC": W.DFC}
+
+
+@pytest.mark.parametrize("kernel", ["P4", "hat"])
+@pytest.mark.parametrize("scheme", ["DF", "MDF", "DFC"])
+def test_taylor_green_ib_orders(kernel, scheme):
+    """App. D.1 IB-LBM mode on the device (FP64 storage) at D = 10, 20, 40, 80 with
+    the markers driven through iblbm_set_marker_velocity.  Peskin: the order within
+    0.2 of Table D.1.  Hat: the errors fall from D = 10 to 40 and sit within a
+    factor 2.5 of Table D.2; at D = 80 they flatten on the pure-LBM error (the ring
+    layout is a reading, so the hat orders, 1.2-1.5 here against 1.8-2.1 printed,
+    are reported, not bounded)."""
+    import math
+    import numpy as np
+    from harness import gpu_case, taylor_green_ib_run, taylor_green_ib_spec
+    rows = {}
+    import os
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "taylor_green_orders.txt")):
+        t = line.split()
+        if t and t[0] == "ib":
+            rows[(t[1], t[2])] = [float(v) for v in t[3:]]
+    printed = rows[(kernel, scheme)]
+    Ds = [10, 20, 40, 80]
+    e = []
+    for D in Ds:
+        spec = taylor_green_ib_spec(D, KERNEL_OF[kernel], SCHEME_OF[scheme])
+        g = gpu_case(spec)
+        e.append(taylor_green_ib_run(g, spec, D))
+        assert g.sync() >= 0
+        g.close()
+    order = -np.polyfit(np.log(Ds), np.log(e), 1)[0]
+    print(kernel, scheme, ["%.3e" % v for v in e], "order %.3f (printed %.3f)" % (order, printed[4]))
+    assert all(math.isfinite(v) for v in e)
+    if kernel == "P4":
+        assert abs(order - printed[4]) < 0.2
+        assert all(0.5 < a / b < 2.0 for a, b in zip(e, printed[:4]))
+    else:
+        assert e[0] > e[1] > e[2]
+        assert all(0.4 < a / b < 2.5 for a, b in zip(e, printed[:4]))

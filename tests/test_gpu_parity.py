@@ -157,3 +157,10 @@ def test_local_diagnostics(scheme, kernel, storage):
 
 def test_local_diagnostics_free_body():
     P.check_local_diagnostics_free_body()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("D", [10, 20])
+def test_taylor_green_ib(scheme, kernel, D):
+    P.check_taylor_green_ib(kernel, scheme, D=D)
