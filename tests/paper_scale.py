@@ -184,15 +184,14 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
                 if abs(st[3]) > c["vmax"]:
                     c["vmax"], c["y_at_vmax"] = abs(st[3]), float(st[1])
                 if st[1] < 1.5 * c["p"]["D"] or not np.isfinite(st[1]):
-                    c["done"] = True
+                    c["done"], c["done_step"] = True, steps
     out = []
     for c in cases:
         lat = c.pop("lat")
         p = c.pop("p")
-        try:
-            status = lat.sync()
-        except Exception as exc:
-            status = str(exc)
+        # a case that reached the bottom keeps being stepped with the others and
+        # eventually meets the wall; its record is the one taken when it arrived
+        status = c.get("error", 0)
         c.update(v_star=c.pop("vmax") / p["u_g"], u_g=p["u_g"], g=p["g"], tau=p["tau"], steps=steps,
                  status=status, vy_series=c.pop("vy"))
         del c["done"]
