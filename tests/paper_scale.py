@@ -132,6 +132,19 @@ def run_row(L, re, storage=W.F32, trigger_steps=0, kernels=(W.HAT, W.PESKIN4), s
 
 # ---- single-particle sedimentation (Sec. 2.9.3, Table IV) ----------------------------
 SED_TAU = {1.01: 0.95, 1.1: 0.64, 1.5: 0.56}
+GOLDEN_T4 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sedimentation_table4.txt")
+
+
+def paper_table4():
+    """{(rho_ratio, kernel name): {scheme: v*}} from the golden file."""
+    out = {}
+    with open(GOLDEN_T4) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            out[(float(t[0]), t[1])] = dict(zip(("DF", "MDF", "DFC"), (float(v) for v in t[2:5])))
+    return out
 
 
 def sedimentation_protocol(rho_ratio):
@@ -216,7 +229,9 @@ def main():
     L.use_torch_allocator()
     if args.sedimentation:
         rows = run_sedimentation(L, storage=W.STORAGES[args.storage])
+        t4 = paper_table4()
         for r in rows:
+            r["paper_v_star"] = t4[(r["rho_ratio"], r["kernel"])][r["scheme"]]
             print(json.dumps({k: v for k, v in r.items() if k != "vy_series"}), flush=True)
         with open(args.out, "w") as fh:
             json.dump(rows, fh)

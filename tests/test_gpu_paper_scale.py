@@ -89,3 +89,24 @@ def test_taylor_green_ib_orders(kernel, scheme):
     else:
         assert e[0] > e[1] > e[2]
         assert all(0.4 < a / b < 2.5 for a, b in zip(e, printed[:4]))
+
+
+def test_sedimentation_rho_1_1_matches_table4():
+    """Table IV row rho_s/rho_f = 1.1 at the paper's scale (1281 x 3841, D = 160,
+    tests/paper_scale.py): every v* within 0.3 % of the printed value and the
+    scheme-to-scheme spread per kernel within 0.15 points of the printed one."""
+    t4 = PS.paper_table4()
+    rows = PS.run_sedimentation(L, rho_ratios=(1.1,), storage=W.F32)
+    for kern in ("hat", "P4"):
+        vals = {}
+        for r in rows:
+            if r["kernel"] != kern:
+                continue
+            assert "error" not in r, r.get("error")
+            p = t4[(1.1, kern)][r["scheme"]]
+            assert abs(r["v_star"] / p - 1.0) < 0.003, (kern, r["scheme"], r["v_star"], p)
+            vals[r["scheme"]] = r["v_star"]
+        ours = 100.0 * (max(vals.values()) - min(vals.values())) / (sum(vals.values()) / 3.0)
+        printed = t4[(1.1, kern)]
+        theirs = 100.0 * (max(printed.values()) - min(printed.values())) / (sum(printed.values()) / 3.0)
+        assert abs(ours - theirs) < 0.15, (kern, ours, theirs)
