@@ -213,6 +213,85 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
     return out
 
 
+# ---- two-particle wake interaction (Sec. 2.9.4, Tables V and C.3) ---------------------
+GOLDEN_T5 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "wake_interaction_table5.txt")
+
+
+def paper_table5():
+    """{(scheme, "B-2" | "A"): (heavy Re_f peak, light Re_f peak)} and
+    {("peak", "B-2" | "A"): (heavy step, heavy distance [D], light step, light distance)}
+    (DF) from the golden file."""
+    out = {}
+    with open(GOLDEN_T5) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            if t[0] == "peak":
+                out[("peak", t[1])] = tuple(float(v) for v in t[2:6])
+            else:
+                out[(t[0], t[1])] = (float(t[2]), float(t[3]))
+    return out
+
+
+def run_wake_interaction(L, schemes=(W.DF, W.DFC), internal=(1, 0), kernel=W.PESKIN4, storage=W.F32,
+                         steps=40000, sample=100):
+    """Sec. 2.9.4 in lattice units: Omega = [0, 10] x [-1, 1] on 4001 x 801 nodes
+    (dx = 0.0025), d = 0.2 (D = 80, 251 markers), heavy disk (rho_r 1.5) at
+    (0.8, -0.13), light disk (1.25) at (1.2, 0.13), gravity g_lat = 2.156e-4 along
+    +x, tau = 0.59 (nu = 0.03).  Reading of the boundaries (the paper defers to
+    the reference configuration): zero-velocity Zou-He walls at y = -1, 1 and at
+    x = 0, zero-gradient outlet at x = 10.  Re_f = |U| D / nu of each particle is
+    sampled every ``sample`` steps until a particle comes within 3 D of the
+    outlet.  Reading of the peaks: the light particle's is the maximum of its
+    series (the paper's falls at step 35,000), the heavy particle's the maximum
+    over the first 20,000 steps (the paper's falls at 8,500-9,500, long before
+    the heavy disk nears the outlet and speeds up again)."""
+    dx, D, nu, g = 0.0025, 80.0, (0.59 - 0.5) / 3.0, 2.156e-4
+    nb = int(round(math.pi * D))
+    places = [(0.8, -0.13, 1.5), (1.2, 0.13, 1.25)]
+    cases = []
+    for sch in schemes:
+        for im in internal:
+            lat = L.Lattice(4001, 801, W.BGK, 0.59, storage, (W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY),
+                            ((0.0, 0.0),) * 4)
+            for X, Y, rr in places:
+                xc, yc = X / dx, (Y + 1.0) / dx
+                xy, ds = W.circle_markers(xc, yc, D, nb)
+                lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr, motion=W.FREE,
+                             gx=g, gy=0.0, internal_mass=im)
+            cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
+                          "re": [[], []], "x": [[], []], "stopped": False})
+    lats = [c["lat"] for c in cases]
+    done = 0
+    while done < steps and not all(c["stopped"] for c in cases):
+        L.step_batch(lats, sample)
+        done += sample
+        for c in cases:
+            if c["stopped"]:
+                continue
+            try:
+                for b in range(2):
+                    st = c["lat"].body_state(b)
+                    c["re"][b].append(math.hypot(st[2], st[3]) * D / nu)
+                    c["x"][b].append(float(st[0]))
+                if max(c["x"][0][-1], c["x"][1][-1]) > 4000.0 - 3.0 * D:
+                    c["stopped"], c["stop_step"] = True, done
+            except Exception as exc:
+                c["stopped"], c["error"], c["error_step"] = True, str(exc), done
+    for c in cases:
+        c.pop("lat").close()
+        del c["stopped"]
+        heavy, light = np.array(c["re"][0]), np.array(c["re"][1])
+        early = heavy[: 20000 // sample]
+        c["heavy_re"], c["heavy_step"] = float(early.max()), int((early.argmax() + 1) * sample)
+        c["light_re"], c["light_step"] = float(light.max()), int((light.argmax() + 1) * sample)
+        c["heavy_x_at_peak_D"] = (c["x"][0][c["heavy_step"] // sample - 1] - 320.0) / D
+        c["light_x_at_peak_D"] = (c["x"][1][c["light_step"] // sample - 1] - 480.0) / D
+        del c["x"]
+    return cases
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--re", default="20,40,100,200")
@@ -222,11 +301,22 @@ def main():
     ap.add_argument("--out", default="fixed_cylinder_tables.json")
     ap.add_argument("--sedimentation", action="store_true",
                     help="run the Table IV settling matrix instead of the fixed-cylinder rows")
+    ap.add_argument("--wake", action="store_true",
+                    help="run the two-particle wake interaction of Tables V and C.3")
     args = ap.parse_args()
     import torch
     import paper_2609_02298_b300 as L
     torch.cuda.set_device(0)
     L.use_torch_allocator()
+    if args.wake:
+        rows = run_wake_interaction(L, storage=W.STORAGES[args.storage])
+        t5 = paper_table5()
+        for r in rows:
+            r["paper_heavy_re"], r["paper_light_re"] = t5[(r["scheme"], r["internal_mass"])]
+            print(json.dumps({k: v for k, v in r.items() if k != "re"}), flush=True)
+        with open(args.out, "w") as fh:
+            json.dump(rows, fh)
+        return
     if args.sedimentation:
         rows = run_sedimentation(L, storage=W.STORAGES[args.storage])
         t4 = paper_table4()

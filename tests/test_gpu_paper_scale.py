@@ -110,3 +110,21 @@ def test_sedimentation_rho_1_1_matches_table4():
         printed = t4[(1.1, kern)]
         theirs = 100.0 * (max(printed.values()) - min(printed.values())) / (sum(printed.values()) / 3.0)
         assert abs(ours - theirs) < 0.15, (kern, ours, theirs)
+
+
+def test_wake_interaction_matches_tables():
+    """Two-particle wake interaction at the paper's scale (4001 x 801, D = 80,
+    DF and DFC, internal-mass schemes B-2 and A; tests/paper_scale.py): heavy-disk
+    peak Re_f within 0.3 % of Tables V / C.3, light-disk peak within 1 %, and (DF)
+    the peak steps within 1,000 steps and the distances within 0.5 D of Table C.2."""
+    t5 = PS.paper_table5()
+    rows = PS.run_wake_interaction(L)
+    for r in rows:
+        assert "error" not in r, r.get("error")
+        heavy, light = t5[(r["scheme"], r["internal_mass"])]
+        assert abs(r["heavy_re"] / heavy - 1.0) < 0.003, r
+        assert abs(r["light_re"] / light - 1.0) < 0.01, r
+        if r["scheme"] == "DF":
+            hs, hd, ls, ld = t5[("peak", r["internal_mass"])]
+            assert abs(r["heavy_step"] - hs) <= 1000 and abs(r["light_step"] - ls) <= 1000, r
+            assert abs(r["heavy_x_at_peak_D"] - hd) < 0.5 and abs(r["light_x_at_peak_D"] - ld) < 0.5, r
