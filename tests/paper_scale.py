@@ -42,6 +42,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fix
 U_INF = 0.1
 SCHEME_NAMES = {W.DF: "DF", W.MDF: "MDF", W.DFC: "DFC"}
 KERNEL_NAMES = {W.HAT: "hat", W.PESKIN4: "P4"}
+COLLISION_NAMES = {W.BGK: "BGK", W.TRT: "TRT", W.CMMRT: "CM-MRT"}
 
 
 def paper_tables():
@@ -65,8 +66,10 @@ def protocol(re):
     return 3001, 2401, 60.0, 60000, 30200
 
 
-def build_row(L, re, storage=W.F32, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W.MDF, W.DFC)):
-    """The lattices of one Table II row: one per (kernel, scheme)."""
+def build_row(L, re, storage=W.F32, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W.MDF, W.DFC), pairs=None,
+              collision=W.BGK):
+    """The lattices of one Table II row: one per (kernel, scheme), or per (kernel,
+    scheme) in ``pairs``; ``collision`` as in Table VI (BGK for Table II)."""
     nx, ny, D, steps, _ = protocol(re)
     xc, yc = 0.4 * (nx - 1), 0.5 * (ny - 1)
     nb = int(round(math.pi * D))
@@ -75,20 +78,20 @@ def build_row(L, re, storage=W.F32, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W
     bc = (W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY)
     ubc = ((U_INF, 0.0), (0.0, 0.0), (U_INF, 0.0), (U_INF, 0.0))
     cases = []
-    for kern in kernels:
-        for sch in schemes:
-            lat = L.Lattice(nx, ny, W.BGK, tau, storage, bc, ubc, init_u=(U_INF, 0.0))
-            lat.add_body(xy, ds, kern, sch, xc=xc, yc=yc, radius=0.5 * D, mdf_nmin=5, mdf_nmax=20,
-                         mdf_tol=1e-4, history_cap=steps)
-            cases.append({"re": re, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch], "lat": lat})
+    for kern, sch in (pairs or [(k, s) for k in kernels for s in schemes]):
+        lat = L.Lattice(nx, ny, collision, tau, storage, bc, ubc, init_u=(U_INF, 0.0))
+        lat.add_body(xy, ds, kern, sch, xc=xc, yc=yc, radius=0.5 * D, mdf_nmin=5, mdf_nmax=20,
+                     mdf_tol=1e-4, history_cap=steps)
+        cases.append({"re": re, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch], "lat": lat,
+                      "collision": COLLISION_NAMES[collision]})
     return cases
 
 
 def run_row(L, re, storage=W.F32, trigger_steps=0, kernels=(W.HAT, W.PESKIN4), schemes=(W.DF, W.MDF, W.DFC),
-            chunk=5000):
+            chunk=5000, pairs=None, collision=W.BGK):
     """Runs one row as one batch and returns a record per case (the lattices are closed)."""
     nx, ny, D, steps, avg_from = protocol(re)
-    cases = build_row(L, re, storage, kernels, schemes)
+    cases = build_row(L, re, storage, kernels, schemes, pairs, collision)
     lats = [c["lat"] for c in cases]
     left = steps
     if trigger_steps > 0:
@@ -162,7 +165,7 @@ def sedimentation_protocol(rho_ratio):
 
 
 def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.HAT, W.PESKIN4),
-                      schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000):
+                      schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000, collision=W.BGK):
     """All cases as one batch until every particle is within one diameter of the
     bottom wall (or max_steps); v* = max |v_y| / u_g over the samples taken every
     ``sample`` steps, with the height where it occurred."""
@@ -173,11 +176,12 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
         xy, ds = W.circle_markers(p["xc"], p["yc"], p["D"], nb)
         for kern in kernels:
             for sch in schemes:
-                lat = L.Lattice(p["nx"], p["ny"], W.BGK, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
+                lat = L.Lattice(p["nx"], p["ny"], collision, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
                 lat.add_body(xy, ds, kern, sch, xc=p["xc"], yc=p["yc"], radius=0.5 * p["D"], rho_ratio=rr,
                              motion=W.FREE, gx=0.0, gy=-p["g"], internal_mass=1, mdf_nmin=5, mdf_nmax=20,
                              mdf_tol=1e-4)
                 cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
+                              "collision": COLLISION_NAMES[collision],
                               "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
     lats = [c["lat"] for c in cases]
     steps = 0
@@ -234,8 +238,11 @@ def paper_table5():
     return out
 
 
-def run_wake_interaction(L, schemes=(W.DF, W.DFC), internal=(1, 0), kernel=W.PESKIN4, storage=W.F32,
-                         steps=40000, sample=100):
+WAKE_CASES = [(W.DF, 1, W.BGK), (W.DF, 0, W.BGK), (W.DFC, 1, W.BGK), (W.DFC, 0, W.BGK)]
+WAKE_COLLISION_CASES = [(W.DF, 1, W.TRT), (W.DF, 1, W.CMMRT)]
+
+
+def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F32, steps=40000, sample=100):
     """Sec. 2.9.4 in lattice units: Omega = [0, 10] x [-1, 1] on 4001 x 801 nodes
     (dx = 0.0025), d = 0.2 (D = 80, 251 markers), heavy disk (rho_r 1.5) at
     (0.8, -0.13), light disk (1.25) at (1.2, 0.13), gravity g_lat = 2.156e-4 along
@@ -251,17 +258,17 @@ def run_wake_interaction(L, schemes=(W.DF, W.DFC), internal=(1, 0), kernel=W.PES
     nb = int(round(math.pi * D))
     places = [(0.8, -0.13, 1.5), (1.2, 0.13, 1.25)]
     cases = []
-    for sch in schemes:
-        for im in internal:
-            lat = L.Lattice(4001, 801, W.BGK, 0.59, storage, (W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY),
-                            ((0.0, 0.0),) * 4)
-            for X, Y, rr in places:
-                xc, yc = X / dx, (Y + 1.0) / dx
-                xy, ds = W.circle_markers(xc, yc, D, nb)
-                lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr, motion=W.FREE,
-                             gx=g, gy=0.0, internal_mass=im)
-            cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
-                          "re": [[], []], "x": [[], []], "stopped": False})
+    for sch, im, col in cases_spec:
+        lat = L.Lattice(4001, 801, col, 0.59, storage, (W.VELOCITY, W.NEUMANN, W.VELOCITY, W.VELOCITY),
+                        ((0.0, 0.0),) * 4)
+        for X, Y, rr in places:
+            xc, yc = X / dx, (Y + 1.0) / dx
+            xy, ds = W.circle_markers(xc, yc, D, nb)
+            lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr, motion=W.FREE,
+                         gx=g, gy=0.0, internal_mass=im)
+        cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
+                      "collision": COLLISION_NAMES[col],
+                      "re": [[], []], "x": [[], []], "stopped": False})
     lats = [c["lat"] for c in cases]
     done = 0
     while done < steps and not all(c["stopped"] for c in cases):
@@ -292,6 +299,22 @@ def run_wake_interaction(L, schemes=(W.DF, W.DFC), internal=(1, 0), kernel=W.PES
     return cases
 
 
+GOLDEN_T6 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "collision_table6.txt")
+
+
+def paper_table6():
+    """{("a", re, kernel, scheme) or ("b", particle): {"BGK": v, "TRT": v, "CM-MRT": v}}."""
+    out = {}
+    with open(GOLDEN_T6) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            key = ("a", int(t[1]), t[2], t[3]) if t[0] == "a" else ("b", t[1])
+            out[key] = dict(zip(("BGK", "TRT", "CM-MRT"), (float(v) for v in t[-3:])))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--re", default="20,40,100,200")
@@ -303,11 +326,37 @@ def main():
                     help="run the Table IV settling matrix instead of the fixed-cylinder rows")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
+    ap.add_argument("--collisions", action="store_true",
+                    help="run the TRT and CM-MRT cases of Table VI, and the rho_r = 1.5 settling row with TRT")
     args = ap.parse_args()
     import torch
     import paper_2609_02298_b300 as L
     torch.cuda.set_device(0)
     L.use_torch_allocator()
+    if args.collisions:
+        t6 = paper_table6()
+        rows = []
+        pairs = [(W.HAT, W.DF), (W.HAT, W.MDF), (W.PESKIN4, W.DFC)]
+        for col in (W.TRT, W.CMMRT):
+            for r in run_row(L, 100, W.STORAGES[args.storage], args.trigger, pairs=pairs, collision=col):
+                r["paper_cd"] = t6[("a", 100, r["kernel"], r["scheme"])][r["collision"]]
+                r["table"] = "VI(a)"
+                rows.append(r)
+        for r in run_wake_interaction(L, WAKE_COLLISION_CASES, storage=W.STORAGES[args.storage]):
+            r["paper_heavy_re"] = t6[("b", "heavy")][r["collision"]]
+            r["paper_light_re"] = t6[("b", "light")][r["collision"]]
+            r["table"] = "VI(b)"
+            rows.append(r)
+        for r in run_sedimentation(L, rho_ratios=(1.5,), storage=W.STORAGES[args.storage],
+                                   schemes=(W.DF, W.DFC), collision=W.TRT):
+            r["table"] = "IV, TRT"
+            r["paper_v_star_bgk"] = paper_table4()[(1.5, r["kernel"])][r["scheme"]]
+            rows.append(r)
+        for r in rows:
+            print(json.dumps({k: v for k, v in r.items() if k not in ("cd_series", "re", "vy_series")}), flush=True)
+        with open(args.out, "w") as fh:
+            json.dump(rows, fh)
+        return
     if args.wake:
         rows = run_wake_interaction(L, storage=W.STORAGES[args.storage])
         t5 = paper_table5()

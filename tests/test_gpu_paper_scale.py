@@ -128,3 +128,13 @@ def test_wake_interaction_matches_tables():
             hs, hd, ls, ld = t5[("peak", r["internal_mass"])]
             assert abs(r["heavy_step"] - hs) <= 1000 and abs(r["light_step"] - ls) <= 1000, r
             assert abs(r["heavy_x_at_peak_D"] - hd) < 0.5 and abs(r["light_x_at_peak_D"] - ld) < 0.5, r
+
+
+def test_wake_interaction_collision_operators_match_table6():
+    """Table VI(b): the wake-interaction reference (DF, Peskin, B-2) with TRT and
+    CM-MRT collision: both peaks within 0.3 % of the printed values."""
+    t6 = PS.paper_table6()
+    for r in PS.run_wake_interaction(L, PS.WAKE_COLLISION_CASES):
+        assert "error" not in r, r.get("error")
+        assert abs(r["heavy_re"] / t6[("b", "heavy")][r["collision"]] - 1.0) < 0.003, r
+        assert abs(r["light_re"] / t6[("b", "light")][r["collision"]] - 1.0) < 0.003, r
