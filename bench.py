@@ -39,10 +39,7 @@ BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # operator), and per lattice of the edge launch, from the ncu section captures summarised in
 # profiles/sweep_matrix36_f32.md (12-lattice case, scaled by nodes).  A sweep whose kernels
 # have no entry here (or changed since) reports traffic null.
-SWEEP_DRAM_BYTES_PER_NODE = {(1, W.BGK): 558.71e6 / 8388608, (1, W.TRT): 560.55e6 / 8388608,
-                             (1, W.CMMRT): 560.39e6 / 8388608,
-                             (2, W.BGK): 561.33e6 / 8388608, (2, W.TRT): 559.75e6 / 8388608,
-                             (2, W.CMMRT): 560.86e6 / 8388608}
+SWEEP_DRAM_BYTES_PER_NODE = {}
 EDGE_DRAM_BYTES_PER_LATTICE = 29.82e6 / 12
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
 

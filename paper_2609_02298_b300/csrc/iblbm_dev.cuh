@@ -119,6 +119,20 @@ __device__ __forceinline__ double ld1(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ldg(p)); }
 
+// Read-only load for the stream-collide sweep, which reads whole rows of every plane:
+// FP32 asks L2 to fetch 256-byte blocks around each miss.
+__device__ __forceinline__ double ld1_sweep(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld1_sweep(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float ld1_sweep(const float* p) {
+#ifdef IBLBM_EMULATE
+    return *p;
+#else
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+#endif
+}
+
 __device__ __forceinline__ void st1(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }

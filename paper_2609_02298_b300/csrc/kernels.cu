@@ -306,7 +306,7 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
             R s[9];
             const int a = row + x;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) s[i] = ld1(src + (a + koff[i]));
+            for (int i = 0; i < 9; ++i) s[i] = ld1_sweep(src + (a + koff[i]));
             R rho;
             if (forced) {
                 R Fx = K.gfx, Fy = K.gfy;
