@@ -39,8 +39,9 @@ BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # operator), and per lattice of the edge launch, from the ncu section captures summarised in
 # profiles/sweep_matrix36_f32.md (12-lattice case, scaled by nodes).  A sweep whose kernels
 # have no entry here (or changed since) reports traffic null.
-SWEEP_DRAM_BYTES_PER_NODE = {}
-EDGE_DRAM_BYTES_PER_LATTICE = 29.82e6 / 12
+SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): 564.13e6 / 8388608, (2, W.TRT): 563.61e6 / 8388608,
+                             (2, W.CMMRT): 564.38e6 / 8388608}
+EDGE_DRAM_BYTES_PER_LATTICE = 29.69e6 / 12
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
 
 
