@@ -136,6 +136,10 @@ __device__ __forceinline__ float ld1_sweep(const float* p) {
 __device__ __forceinline__ void st1(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }
+// Store of the stream-collide sweep (the destination is not read again this step).
+__device__ __forceinline__ void st1_sweep(double* p, double v) { st1(p, v); }
+__device__ __forceinline__ void st1_sweep(__half* p, float v) { st1(p, v); }
+__device__ __forceinline__ void st1_sweep(float* p, float v) { *p = v; }
 // One correctly rounded conversion from double (no double rounding through float).
 __device__ __forceinline__ void st1_from_double(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1_from_double(float* p, double v) { *p = (float)v; }

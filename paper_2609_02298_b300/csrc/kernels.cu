@@ -317,7 +317,7 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
             }
             unstable |= bad_density(rho);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) st1(dst + (a + i * plane), s[i]);
+            for (int i = 0; i < 9; ++i) st1_sweep(dst + (a + i * plane), s[i]);
         }
     }
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
