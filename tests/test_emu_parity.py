@@ -205,7 +205,7 @@ def test_local_diagnostics_free_body(L):
     P.check_local_diagnostics_free_body(steps=10)
 
 
-@pytest.mark.parametrize("kernel,scheme", [(W.PESKIN4, W.DF), (W.HAT, W.MDF), (W.PESKIN4, W.DFC)])
+@pytest.mark.parametrize("kernel,scheme", [(W.PESKIN4, W.DF), (W.HAT, W.DF), (W.PESKIN4, W.DFC)])
 def test_taylor_green_ib(L, kernel, scheme):
     full_only(L)
     P.check_taylor_green_ib(kernel, scheme, D=8)
