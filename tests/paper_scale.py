@@ -165,24 +165,27 @@ def sedimentation_protocol(rho_ratio):
 
 
 def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.HAT, W.PESKIN4),
-                      schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000, collision=W.BGK):
+                      schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000, collision=W.BGK,
+                      retractions=(0.0,)):
     """All cases as one batch until every particle is within one diameter of the
     bottom wall (or max_steps); v* = max |v_y| / u_g over the samples taken every
-    ``sample`` steps, with the height where it occurred."""
+    ``sample`` steps, with the height where it occurred.  ``retractions`` moves
+    the markers inward by that many lattice units (Table VII; reading: the same
+    n markers on the circle of radius R - delta, ds = 2 pi (R - delta) / n, the
+    body's mass and inertia still those of radius R)."""
     cases = []
     for rr in rho_ratios:
         p = sedimentation_protocol(rr)
         nb = int(round(math.pi * p["D"]))
-        xy, ds = W.circle_markers(p["xc"], p["yc"], p["D"], nb)
-        for kern in kernels:
-            for sch in schemes:
-                lat = L.Lattice(p["nx"], p["ny"], collision, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
-                lat.add_body(xy, ds, kern, sch, xc=p["xc"], yc=p["yc"], radius=0.5 * p["D"], rho_ratio=rr,
-                             motion=W.FREE, gx=0.0, gy=-p["g"], internal_mass=1, mdf_nmin=5, mdf_nmax=20,
-                             mdf_tol=1e-4)
-                cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
-                              "collision": COLLISION_NAMES[collision],
-                              "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
+        for kern, sch, dr in [(k, s_, d) for k in kernels for s_ in schemes for d in retractions]:
+            xy, ds = W.circle_markers(p["xc"], p["yc"], p["D"] - 2.0 * dr, nb)
+            lat = L.Lattice(p["nx"], p["ny"], collision, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
+            lat.add_body(xy, ds, kern, sch, xc=p["xc"], yc=p["yc"], radius=0.5 * p["D"], rho_ratio=rr,
+                         motion=W.FREE, gx=0.0, gy=-p["g"], internal_mass=1, mdf_nmin=5, mdf_nmax=20,
+                         mdf_tol=1e-4)
+            cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
+                          "collision": COLLISION_NAMES[collision], "retraction": dr,
+                          "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
     lats = [c["lat"] for c in cases]
     steps = 0
     while steps < max_steps and not all(c["done"] for c in cases):
@@ -326,6 +329,8 @@ def main():
                     help="run the Table IV settling matrix instead of the fixed-cylinder rows")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
+    ap.add_argument("--retraction", action="store_true",
+                    help="run the marker-retraction row of Table VII (rho_r = 1.5, Peskin DF, TRT)")
     ap.add_argument("--collisions", action="store_true",
                     help="run the TRT and CM-MRT cases of Table VI, and the rho_r = 1.5 settling row with TRT")
     args = ap.parse_args()
@@ -333,6 +338,23 @@ def main():
     import paper_2609_02298_b300 as L
     torch.cuda.set_device(0)
     L.use_torch_allocator()
+    if args.retraction:
+        shifts = {}
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "retraction_table7.txt")) as fh:
+            for line in fh:
+                if line.strip() and not line.startswith("#"):
+                    t = line.split()
+                    shifts[float(t[0])] = float(t[2])
+        rows = run_sedimentation(L, rho_ratios=(1.5,), storage=W.STORAGES[args.storage], kernels=(W.PESKIN4,),
+                                 schemes=(W.DF,), collision=W.TRT, retractions=(0.0, 0.3, 0.5, 1.0))
+        base = next(r["v_star"] for r in rows if r["retraction"] == 0.0)
+        for r in rows:
+            r["shift_percent"] = 100.0 * (r["v_star"] / base - 1.0)
+            r["paper_shift_percent"] = shifts.get(r["retraction"], 0.0)
+            print(json.dumps({k: v for k, v in r.items() if k != "vy_series"}), flush=True)
+        with open(args.out, "w") as fh:
+            json.dump(rows, fh)
+        return
     if args.collisions:
         t6 = paper_table6()
         rows = []
