@@ -329,6 +329,8 @@ def main():
                     help="run the Table IV settling matrix instead of the fixed-cylinder rows")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
+    ap.add_argument("--table-b4", action="store_true",
+                    help="the Re = 100 half of Table B.4: every kernel/scheme pair with TRT and CM-MRT")
     ap.add_argument("--precision", action="store_true",
                     help="FP32 against FP64 storage at paper scale: Re = 100 cylinder and rho_r = 1.1 settling")
     ap.add_argument("--retraction", action="store_true",
@@ -340,6 +342,19 @@ def main():
     import paper_2609_02298_b300 as L
     torch.cuda.set_device(0)
     L.use_torch_allocator()
+    if args.table_b4:
+        t6 = paper_table6()
+        rows = []
+        pairs = [(k, s_) for k in (W.HAT, W.PESKIN4) for s_ in (W.DF, W.MDF, W.DFC)]
+        for col in (W.TRT, W.CMMRT):
+            for r in run_row(L, 100, W.STORAGES[args.storage], args.trigger, pairs=pairs, collision=col):
+                r["paper_cd"] = t6[("a", 100, r["kernel"], r["scheme"])][r["collision"]]
+                rows.append(r)
+                print(json.dumps({k: r[k] for k in ("kernel", "scheme", "collision", "cd", "paper_cd", "st")}),
+                      flush=True)
+        with open(args.out, "w") as fh:
+            json.dump(rows, fh)
+        return
     if args.precision:
         # the FP64 device mode matches the FP64 oracle to 1e-12 (parity tests), so it stands in
         # for the oracle at sizes the oracle cannot run
