@@ -346,6 +346,29 @@ def test_df_force_is_eq11():
     assert Fb[0] == pytest.approx(2.0 * u[0] * ds * len(xy), rel=1e-13)
 
 
+def test_df_force_with_marker_velocity():
+    """Per-marker desired velocity (App. D.1 drive) in Eq. 11: on a uniform stream,
+    markers driven with the stream's own velocity feel no force, and markers
+    driven with a different velocity per marker feel 2 rho (U_d,k - U) each."""
+    u = (0.05, -0.02)
+    c = _periodic_case(30, 30, u=u)
+    xy, ds = W.circle_markers(15.2, 14.7, 8.0, 25)
+    c.add_body(xy, ds, W.HAT, W.DF, _body(xy, ds, W.HAT, W.DF, 15.2, 14.7, 4.0))
+    c.set_marker_velocity(0, np.tile(u, (len(xy), 1)))
+    c.step(1)
+    m = c.marker_data(0)
+    np.testing.assert_allclose(m[:, 2:4], np.tile(u, (len(xy), 1)), rtol=0, atol=0)
+    np.testing.assert_allclose(m[:, 4:6], 0.0, atol=1e-15)
+    c2 = _periodic_case(30, 30, u=u)
+    c2.add_body(xy, ds, W.HAT, W.DF, _body(xy, ds, W.HAT, W.DF, 15.2, 14.7, 4.0))
+    ud = np.stack([0.01 * np.arange(len(xy)) / len(xy), -0.005 * np.ones(len(xy))], axis=1)
+    c2.set_marker_velocity(0, ud)
+    c2.step(1)
+    m2 = c2.marker_data(0)
+    np.testing.assert_allclose(m2[:, 4], 2.0 * (ud[:, 0] - u[0]), rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(m2[:, 5], 2.0 * (ud[:, 1] - u[1]), rtol=1e-12, atol=1e-16)
+
+
 @pytest.mark.parametrize("kernel", [W.HAT, W.PESKIN4])
 def test_mdf_is_richardson(kernel):
     """Sec. 2.5.2: on a uniform field (rho = 1) the MDF residual obeys
