@@ -72,3 +72,13 @@ def test_create_rejects_bad_arguments_without_device_work():
     assert lib.iblbm_create(None, L.BGK, 0.8, C.byref(h)) == -1
     assert lib.iblbm_step(None, 1) == -1
     assert lib.iblbm_step_batch(None, 0, 1) == -1
+
+
+def test_diagnostics_and_marker_velocity_reject_bad_arguments():
+    """The Sec. 2.8 diagnostics and the per-marker velocity call validate their
+    arguments before any CUDA call (null context, null output)."""
+    import paper_2609_02298_b300 as L
+    lib = L.load_library()
+    out = (C.c_double * 8)()
+    assert lib.iblbm_local_diagnostics(None, 0, 0.1, 2.0, out, None) == -1
+    assert lib.iblbm_set_marker_velocity(None, 0, None) == -1
