@@ -90,6 +90,11 @@ typedef struct {
     double force[2];            /* uniform body-force density on the fluid (usually 0) */
     double init_rho, init_u[2]; /* initial state: equilibrium at this density/velocity */
     void* cuda_stream;          /* cudaStream_t, NULL = legacy default stream */
+    int wall_closure;           /* IBLBM_BC_VELOCITY sides with zero velocity: 0 = the Zou-He
+                                   closure with its tangential correction (Sec. 2.9.3 names Zou
+                                   and He); 1 = on-node bounce-back of the unknown populations,
+                                   the same closure at u = 0 without the tangential correction,
+                                   which stays stable with BGK below tau ~ 0.6 */
 } iblbm_lattice_desc;
 
 typedef struct {

@@ -46,7 +46,7 @@ class LatticeParams(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc", C.c_int * 4),
                 ("ubc", (C.c_double * 2) * 4), ("collision", C.c_int), ("tau", C.c_double),
                 ("trt_lambda", C.c_double), ("cm_sq", C.c_double), ("cm_se", C.c_double),
-                ("gfx", C.c_double), ("gfy", C.c_double)]
+                ("gfx", C.c_double), ("gfy", C.c_double), ("wall_closure", C.c_int)]
 
 
 class BodyParams(C.Structure):
@@ -107,7 +107,7 @@ def _dp(a: np.ndarray):
 
 
 def lattice_params(nx, ny, bc=(PERIODIC,) * 4, ubc=((0.0, 0.0),) * 4, collision=BGK, tau=0.8,
-                   trt_lambda=0.25, cm_sq=1.2, cm_se=1.4, force=(0.0, 0.0)) -> LatticeParams:
+                   trt_lambda=0.25, cm_sq=1.2, cm_se=1.4, force=(0.0, 0.0), wall_closure=0) -> LatticeParams:
     p = LatticeParams()
     p.nx, p.ny = nx, ny
     for s in range(4):
@@ -115,6 +115,7 @@ def lattice_params(nx, ny, bc=(PERIODIC,) * 4, ubc=((0.0, 0.0),) * 4, collision=
         p.ubc[s][0], p.ubc[s][1] = ubc[s]
     p.collision, p.tau, p.trt_lambda, p.cm_sq, p.cm_se = collision, tau, trt_lambda, cm_sq, cm_se
     p.gfx, p.gfy = force
+    p.wall_closure = wall_closure
     return p
 
 

@@ -317,6 +317,24 @@ static void zou_he(int side, double f[9], double ux, double uy) {
     }
 }
 
+/* A velocity side: the Zou-He closure, or (wall_closure = 1, zero wall velocity) the
+ * populations pointing into the lattice equal to their opposites (on-node bounce-back):
+ * W: 1, 5, 8 from 3, 7, 6;  E: 3, 7, 6 from 1, 5, 8;  S: 2, 5, 6 from 4, 7, 8;
+ * N: 4, 7, 8 from 2, 5, 6. */
+static void apply_velocity_side(const orc_case* c, int side, double f[9]) {
+    const double ux = c->p.ubc[side][0], uy = c->p.ubc[side][1];
+    if (c->p.wall_closure == 1 && ux == 0.0 && uy == 0.0) {
+        switch (side) {
+        case SIDE_W: f[1] = f[3]; f[5] = f[7]; f[8] = f[6]; break;
+        case SIDE_E: f[3] = f[1]; f[7] = f[5]; f[6] = f[8]; break;
+        case SIDE_S: f[2] = f[4]; f[5] = f[7]; f[6] = f[8]; break;
+        default:     f[4] = f[2]; f[7] = f[5]; f[8] = f[6]; break;
+        }
+        return;
+    }
+    zou_he(side, f, ux, uy);
+}
+
 static void load9(const orc_case* c, const double* a, int x, int y, double v[9]) {
     for (int i = 0; i < 9; ++i) v[i] = a[IDX(c, i, x, y)];
 }
@@ -344,7 +362,7 @@ static void apply_bcs(orc_case* c) {
                     load9(c, c->fs, xin, y, v);
                 } else {
                     load9(c, c->fs, x, y, v);
-                    zou_he(s, v, c->p.ubc[s][0], c->p.ubc[s][1]);
+                    apply_velocity_side(c, s, v);
                 }
                 store9(c, c->fs, x, y, v);
             }
@@ -358,7 +376,7 @@ static void apply_bcs(orc_case* c) {
                     load9(c, c->fs, x, yin, v);
                 } else {
                     load9(c, c->fs, x, y, v);
-                    zou_he(s, v, c->p.ubc[s][0], c->p.ubc[s][1]);
+                    apply_velocity_side(c, s, v);
                 }
                 store9(c, c->fs, x, y, v);
             }

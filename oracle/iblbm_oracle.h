@@ -41,6 +41,7 @@ typedef struct {
     double trt_lambda;  /* TRT magic parameter Lambda_eo */
     double cm_sq, cm_se;/* CM-MRT third/fourth-order rates */
     double gfx, gfy;    /* uniform body-force density on the fluid (0 for IB cases) */
+    int wall_closure;   /* 1: zero-velocity ORC_VELOCITY sides by on-node bounce-back */
 } orc_lattice_params;
 
 typedef struct {

@@ -40,7 +40,7 @@ class LatticeDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("storage", C.c_int), ("bc", C.c_int * 4),
                 ("u_bc", (C.c_double * 2) * 4), ("trt_lambda", C.c_double), ("cm_sq", C.c_double),
                 ("cm_se", C.c_double), ("force", C.c_double * 2), ("init_rho", C.c_double),
-                ("init_u", C.c_double * 2), ("cuda_stream", C.c_void_p)]
+                ("init_u", C.c_double * 2), ("cuda_stream", C.c_void_p), ("wall_closure", C.c_int)]
 
 
 class BodyDesc(C.Structure):
@@ -184,7 +184,7 @@ class Lattice:
                  bc: Sequence[int] = (BC_PERIODIC,) * 4,
                  u_bc: Sequence[Sequence[float]] = ((0.0, 0.0),) * 4, trt_lambda: float = 3.0 / 16.0,
                  cm_sq: float = 1.2, cm_se: float = 1.4, force=(0.0, 0.0), init_rho: float = 1.0,
-                 init_u=(0.0, 0.0), stream: Optional[int] = None):
+                 init_u=(0.0, 0.0), stream: Optional[int] = None, wall_closure: int = 0):
         lib = load_library()
         d = LatticeDesc()
         d.nx, d.ny, d.storage = nx, ny, storage
@@ -202,6 +202,7 @@ class Lattice:
             except Exception:
                 stream = 0
         d.cuda_stream = stream
+        d.wall_closure = wall_closure
         h = C.c_void_p()
         _check(lib.iblbm_create(C.byref(d), collision, tau, C.byref(h)), "iblbm_create")
         self._h = h
@@ -217,7 +218,8 @@ class Lattice:
         yc, radius, rho_ratio, motion, gx, gy, internal_mass, mdf_*, osc_*)."""
         lat = cls(spec.nx, spec.ny, spec.collision, spec.tau,
                   spec.storage if storage is None else storage, spec.bc, spec.ubc, spec.trt_lambda,
-                  spec.cm_sq, spec.cm_se, spec.force, 1.0, spec.init_u, stream)
+                  spec.cm_sq, spec.cm_se, spec.force, 1.0, spec.init_u, stream,
+                  getattr(spec, "wall_closure", 0))
         for b in spec.bodies:
             lat.add_body(b.xy, b.ds, b.kernel, b.scheme, xc=b.xc, yc=b.yc, radius=b.radius,
                          rho_ratio=b.rho_ratio, motion=b.motion, gx=b.gx, gy=b.gy,

@@ -253,6 +253,7 @@ int iblbm_create(const iblbm_lattice_desc* d, int collision, double tau, iblbm_c
         h.ubc[s][0] = d->u_bc[s][0];
         h.ubc[s][1] = d->u_bc[s][1];
     }
+    h.wall_closure = d->wall_closure;
     h.tau = tau;
     h.omega = 1.0 / tau;
     h.s_e = 1.0 / tau;

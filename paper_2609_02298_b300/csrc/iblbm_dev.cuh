@@ -57,7 +57,7 @@ struct CaseDev {
     BodyDev* bodies;              // device array [kMaxBodies]
     unsigned long long step;
     unsigned int status;
-    int pad_;
+    int wall_closure;             // 1: zero-velocity walls by on-node bounce-back of the unknowns
 };
 
 // Dynamic FP64 state of a rigid body (what a checkpoint carries besides arrays).
@@ -383,11 +383,19 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
 // tangent t: rho = (1 + sum_{e.n=0} s + 2 sum_{e.n<0} s) / (1 - u.n) and for every
 // unknown population (e.n > 0):
 //   s_i = s_opp + 6 w_i rho (e_i.u) + (e_i.t)/2 [ (2/3) rho (u.t) - sum_{e.n=0} s_j (e_j.t) ].
+// wall_closure = 1 reads a zero-velocity side as on-node bounce-back of the unknowns,
+// s_i = s_opp: the closure above at u = 0 without its tangential correction.
 template <class R>
-__device__ __forceinline__ void zou_he(int side, R (&s)[9], R ux, R uy) {
+__device__ __forceinline__ void zou_he(int side, R (&s)[9], R ux, R uy, int wall_closure = 0) {
     const int nnx = side == SIDE_W ? 1 : (side == SIDE_E ? -1 : 0);
     const int nny = side == SIDE_S ? 1 : (side == SIDE_N ? -1 : 0);
     const int ttx = nnx == 0 ? 1 : 0, tty = nnx == 0 ? 0 : 1;
+    if (wall_closure == 1 && ux == R(0) && uy == R(0)) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if (ex(i) * nnx + ey(i) * nny > 0) s[i] = s[opp(i)];
+        return;
+    }
     R a = R(0), b = R(0), Qt = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -468,7 +476,7 @@ __device__ void post_stream_node(const CaseDev& C, const S* __restrict__ src, in
         return;
     }
     pull_node<S, R>(C, src, x, y, s);
-    zou_he<R>(side, s, R(C.ubc[side][0]), R(C.ubc[side][1]));
+    zou_he<R>(side, s, R(C.ubc[side][0]), R(C.ubc[side][1]), C.wall_closure);
 }
 
 // ---- regularised delta kernels (Eq. 9, Eq. 10) --------------------------------------------

@@ -15,7 +15,7 @@ EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 def oracle_case(spec: W.CaseSpec) -> oracle.Case:
     p = oracle.lattice_params(spec.nx, spec.ny, bc=spec.bc, ubc=spec.ubc, collision=spec.collision,
                               tau=spec.tau, trt_lambda=spec.trt_lambda, cm_sq=spec.cm_sq,
-                              cm_se=spec.cm_se, force=spec.force)
+                              cm_se=spec.cm_se, force=spec.force, wall_closure=spec.wall_closure)
     c = oracle.Case(p)
     c.set_uniform(1.0, *spec.init_u)
     for b in spec.bodies:

@@ -166,7 +166,7 @@ def sedimentation_protocol(rho_ratio):
 
 def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.HAT, W.PESKIN4),
                       schemes=(W.DF, W.MDF, W.DFC), sample=200, max_steps=150000, collision=W.BGK,
-                      retractions=(0.0,)):
+                      retractions=(0.0,), wall_closure=0):
     """All cases as one batch until every particle is within one diameter of the
     bottom wall (or max_steps); v* = max |v_y| / u_g over the samples taken every
     ``sample`` steps, with the height where it occurred.  ``retractions`` moves
@@ -179,12 +179,13 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
         nb = int(round(math.pi * p["D"]))
         for kern, sch, dr in [(k, s_, d) for k in kernels for s_ in schemes for d in retractions]:
             xy, ds = W.circle_markers(p["xc"], p["yc"], p["D"] - 2.0 * dr, nb)
-            lat = L.Lattice(p["nx"], p["ny"], collision, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4)
+            lat = L.Lattice(p["nx"], p["ny"], collision, p["tau"], storage, (W.VELOCITY,) * 4, ((0.0, 0.0),) * 4,
+                            wall_closure=wall_closure)
             lat.add_body(xy, ds, kern, sch, xc=p["xc"], yc=p["yc"], radius=0.5 * p["D"], rho_ratio=rr,
                          motion=W.FREE, gx=0.0, gy=-p["g"], internal_mass=1, mdf_nmin=5, mdf_nmax=20,
                          mdf_tol=1e-4)
             cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
-                          "collision": COLLISION_NAMES[collision], "retraction": dr,
+                          "collision": COLLISION_NAMES[collision], "retraction": dr, "wall_closure": wall_closure,
                           "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
     lats = [c["lat"] for c in cases]
     steps = 0
@@ -327,6 +328,9 @@ def main():
     ap.add_argument("--out", default="fixed_cylinder_tables.json")
     ap.add_argument("--sedimentation", action="store_true",
                     help="run the Table IV settling matrix instead of the fixed-cylinder rows")
+    ap.add_argument("--rho", default="1.01,1.1,1.5", help="density ratios of the settling matrix")
+    ap.add_argument("--wall-closure", type=int, default=0,
+                    help="0: Zou-He walls; 1: zero-velocity walls by on-node bounce-back")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
     ap.add_argument("--table-b4", action="store_true",
@@ -433,7 +437,8 @@ def main():
             json.dump(rows, fh)
         return
     if args.sedimentation:
-        rows = run_sedimentation(L, storage=W.STORAGES[args.storage])
+        rows = run_sedimentation(L, rho_ratios=tuple(float(v) for v in args.rho.split(",")),
+                                 storage=W.STORAGES[args.storage], wall_closure=args.wall_closure)
         t4 = paper_table4()
         for r in rows:
             r["paper_v_star"] = t4[(r["rho_ratio"], r["kernel"])][r["scheme"]]

@@ -94,10 +94,11 @@ BC_SETS = {
 }
 
 
-def check_domain_conditions_f64(name, nx, ny, storage=W.F64, rounds=3, steps=7):
+def check_domain_conditions_f64(name, nx, ny, storage=W.F64, rounds=3, steps=7, wall_closure=0):
     bc, ubc = BC_SETS[name]
     f0 = W.random_populations(13, nx, ny, amp=0.02)
-    spec = W.CaseSpec(name=name, nx=nx, ny=ny, bc=bc, ubc=ubc, collision=W.BGK, tau=0.7, storage=storage)
+    spec = W.CaseSpec(name=name, nx=nx, ny=ny, bc=bc, ubc=ubc, collision=W.BGK, tau=0.7, storage=storage,
+                      wall_closure=wall_closure)
     g, c = gpu_case(spec), oracle_case(spec)
     g.set_populations(f0)
     c.set_populations(f0)

@@ -51,7 +51,10 @@ def test_struct_layout_matches_header():
     """ctypes mirrors of the descriptors have the C sizes (compiled probe-free:
     sizes follow from the field lists in the header)."""
     import paper_2609_02298_b300 as L
-    assert C.sizeof(L.LatticeDesc) == 4 * 2 + 4 + 16 + 64 + 8 * 3 + 16 + 8 + 16 + 8 + 4  # + tail padding
+    # nx, ny, storage, bc[4], padding to 8, u_bc, three doubles, force, init_rho, init_u,
+    # cuda_stream, wall_closure, tail padding to 8
+    assert L.LatticeDesc.wall_closure.offset == 4 * 2 + 4 + 16 + 4 + 64 + 8 * 3 + 16 + 8 + 16 + 8
+    assert C.sizeof(L.LatticeDesc) == L.LatticeDesc.wall_closure.offset + 4 + 4
     assert C.sizeof(L.BodyDesc) % 8 == 0
 
 

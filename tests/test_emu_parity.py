@@ -209,3 +209,9 @@ def test_local_diagnostics_free_body(L):
 def test_taylor_green_ib(L, kernel, scheme):
     full_only(L)
     P.check_taylor_green_ib(kernel, scheme, D=8)
+
+
+@pytest.mark.parametrize("name", ["walls", "periodic-x"])
+def test_domain_conditions_bounce_back_walls(L, name):
+    """wall_closure = 1: zero-velocity sides by on-node bounce-back, moving sides by Zou-He."""
+    P.check_domain_conditions_f64(name, 33, 12, wall_closure=1)

@@ -164,3 +164,10 @@ def test_local_diagnostics_free_body():
 @pytest.mark.parametrize("D", [10, 20])
 def test_taylor_green_ib(scheme, kernel, D):
     P.check_taylor_green_ib(kernel, scheme, D=D)
+
+
+@pytest.mark.parametrize("name", ["walls", "periodic-x", "channel"])
+@pytest.mark.parametrize("nx,ny", [(150, 37), (65, 12)])
+def test_domain_conditions_bounce_back_walls(name, nx, ny):
+    """wall_closure = 1: zero-velocity sides by on-node bounce-back, moving sides by Zou-He."""
+    P.check_domain_conditions_f64(name, nx, ny, wall_closure=1)

@@ -667,3 +667,45 @@ def test_taylor_green_ib_order_peskin_df():
     assert abs(order - printed[4]) < 0.1
     # the absolute errors depend on the unprinted marker layout; same magnitude as printed
     assert all(0.5 < a / b < 2.0 for a, b in zip(e, printed[:4]))
+
+
+def _noise_box_growth(wall_closure, tau=0.56, nx=24, ny=90, steps=2500):
+    """max|u| after ``steps`` over its start value, in a closed box of zero-velocity
+    walls at rest seeded with 1e-6 velocity noise (BGK)."""
+    rng = np.random.default_rng(3)
+    ux, uy = 1e-6 * rng.standard_normal((2, ny, nx))
+    f = np.zeros((9, ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            f[:, j, i] = oracle.feq(1.0, ux[j, i], uy[j, i])
+    c = oracle.Case(oracle.lattice_params(nx, ny, bc=(W.VELOCITY,) * 4, collision=W.BGK, tau=tau,
+                                          wall_closure=wall_closure))
+    c.set_populations(f)
+    c.step(steps)
+    _, vx, vy = c.macro()
+    return float(np.hypot(vx, vy).max()) / float(np.hypot(ux, uy).max())
+
+
+def test_wall_closure_stability_at_low_tau():
+    """At tau = 0.56 the Zou-He walls with their tangential correction let wall-
+    adjacent noise grow under BGK, while the on-node bounce-back reading of the
+    same zero-velocity walls (wall_closure = 1) lets it decay."""
+    assert _noise_box_growth(0) > 3.0      # 8.4 here
+    assert _noise_box_growth(1) < 0.05     # 0.004 here
+
+
+def test_wall_closure_poiseuille_bulk():
+    """Bounce-back walls (wall_closure = 1) leave the bulk equation alone: the
+    body-force-driven channel still has second difference -g/nu inside and is
+    symmetric."""
+    ny, tau, g = 21, 0.8, 1e-6
+    nu = (tau - 0.5) / 3.0
+    p = oracle.lattice_params(4, ny, bc=(W.PERIODIC, W.PERIODIC, W.VELOCITY, W.VELOCITY),
+                              collision=W.BGK, tau=tau, force=(g, 0.0), wall_closure=1)
+    c = oracle.Case(p)
+    c.step(12000)
+    _, ux, _ = c.macro()
+    u = ux[:, 1]
+    d2 = u[2:] - 2 * u[1:-1] + u[:-2]
+    np.testing.assert_allclose(d2[2:-2], -g / nu, rtol=1e-5)
+    np.testing.assert_allclose(u, u[::-1], rtol=0, atol=1e-15)

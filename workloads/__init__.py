@@ -73,6 +73,7 @@ class CaseSpec:
     init_u: Tuple[float, float] = (0.0, 0.0)
     bodies: List[BodySpec] = dataclasses.field(default_factory=list)
     steps: int = 1
+    wall_closure: int = 0
 
     @property
     def nodes(self) -> int:
