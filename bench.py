@@ -41,7 +41,9 @@ BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # have no entry here (or changed since) reports traffic null.
 SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): 564.13e6 / 8388608, (2, W.TRT): 563.61e6 / 8388608,
                              (2, W.CMMRT): 564.38e6 / 8388608}
-EDGE_DRAM_BYTES_PER_LATTICE = 29.69e6 / 12
+# The edge launch gained the zero-velocity wall-closure branch after its capture: no figure
+# until it is captured again (the sweep's traffic is then reported null).
+EDGE_DRAM_BYTES_PER_LATTICE = None
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
 
 
@@ -77,7 +79,7 @@ def sweep_traffic(L, specs):
     for s in specs:
         v = L.kernel_variant(s.storage, s.collision)[0]
         bpn = SWEEP_DRAM_BYTES_PER_NODE.get((v, s.collision))
-        if bpn is None:
+        if bpn is None or EDGE_DRAM_BYTES_PER_LATTICE is None:
             return None
         total += bpn * s.nodes + EDGE_DRAM_BYTES_PER_LATTICE
     return total
