@@ -87,7 +87,9 @@ struct Pool {
         }
         for (int i = 0; i < nthreads; ++i) go[i]->release();   // release orders the writes above
         std::unique_lock<std::mutex> lk(m);
-        if (!cv_done.wait_for(lk, std::chrono::seconds(120), [&] { return remaining == 0; })) {
+        // a block that never finishes is a divergent barrier; the limit is generous so that a
+        // slow but correct block on a busy host does not trip it
+        if (!cv_done.wait_for(lk, std::chrono::seconds(600), [&] { return remaining == 0; })) {
             std::fprintf(stderr, "emu: block did not finish (divergent barrier)\n");
             std::abort();
         }
