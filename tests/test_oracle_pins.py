@@ -148,7 +148,7 @@ def test_couette_linear_profile():
     assert np.abs(uy).max() < 1e-12
 
 
-@pytest.mark.parametrize("collision", [W.BGK, W.TRT])
+@pytest.mark.parametrize("collision", [W.BGK, W.TRT, W.CMMRT])
 def test_poiseuille_parabola(collision):
     """Body-force-driven channel with Zou-He walls: the steady Eq. 4 velocity is
     a parabola with second difference -g/nu (nu = (tau - 1/2)/3)."""
@@ -709,3 +709,150 @@ def test_wall_closure_poiseuille_bulk():
     d2 = u[2:] - 2 * u[1:-1] + u[:-2]
     np.testing.assert_allclose(d2[2:-2], -g / nu, rtol=1e-5)
     np.testing.assert_allclose(u, u[::-1], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- DFC on a uniform stream
+@pytest.mark.parametrize("drive", [False, True])
+@pytest.mark.parametrize("kernel", [W.HAT, W.PESKIN4])
+def test_dfc_uniform_stream_closed_form(kernel, drive):
+    """Eqs. 15-20 on a uniform equilibrium stream (rho = 1, velocity u).  The
+    interpolated populations are f_eq(1, u) by partition of unity, and the odd part
+    of Eq. 2 gives f_eq,opp(i) - f_eq,i = -6 w_i e_i.u, so Eq. 16 and Eq. 18 give
+    delta f_i,k = 6 lambda_k w_i e_i.(U_d,k - u) and Eq. 20 gives
+    F_s,k = -2 lambda_k ds (U_d,k - u) exactly, lambda_k being Eq. 17 evaluated here
+    on the dense delta matrix.  The correction adds no mass at any node
+    (sum_i w_i e_i = 0) and adds the momentum sum_k D(x - X_k) 2 lambda_k ds
+    (U_d,k - u) at node x (Eq. 19).  With ``drive`` every marker gets its own
+    desired velocity, which separates the sign of the U_d term from the u term."""
+    nx = ny = 30
+    u = np.array([0.05, -0.02])
+    c = _periodic_case(nx, ny, u=tuple(u))
+    xy, ds = W.circle_markers(15.3, 14.6, 9.0, 27)
+    c.add_body(xy, ds, kernel, W.DFC, _body(xy, ds, kernel, W.DFC, 15.3, 14.6, 4.5))
+    ud = np.zeros((len(xy), 2))
+    if drive:
+        rng = np.random.default_rng(11)
+        ud = rng.uniform(-0.03, 0.03, size=(len(xy), 2))
+        c.set_marker_velocity(0, ud)
+    c.step(1)
+    D = _dense_D(kernel, xy, nx, ny)                  # (M, N)
+    lam = 1.0 / (2.0 * ds * (D @ D.sum(axis=0)))      # Eq. 17, rho_f = 1
+    m = c.marker_data(0)
+    np.testing.assert_allclose(m[:, 6], lam, rtol=1e-13)
+    Fs = -2.0 * lam[:, None] * ds * (ud - u[None, :])
+    np.testing.assert_allclose(m[:, 4:6], Fs, rtol=1e-11, atol=1e-17)
+    rho, ux, uy = c.macro()
+    np.testing.assert_allclose(rho, 1.0, rtol=0, atol=2e-15)
+    dj = D.T @ (2.0 * lam[:, None] * ds * (ud - u[None, :]))   # (N, 2)
+    np.testing.assert_allclose(ux.ravel(), u[0] + dj[:, 0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy.ravel(), u[1] + dj[:, 1], rtol=0, atol=1e-15)
+    assert np.abs(dj).max() > 1e-3
+
+
+# ---------------------------------------------------------------- Zou-He velocity sides
+_SIDES = {"W": 0, "E": 1, "S": 2, "N": 3}
+
+
+def _side_layout(side, u_bc):
+    """A lattice whose only velocity side is ``side`` (the opposite side zero-gradient,
+    the other axis periodic) and the index of the boundary line."""
+    s = _SIDES[side]
+    ubc = [(0.0, 0.0)] * 4
+    ubc[s] = u_bc
+    if side in "WE":
+        bc = [W.NEUMANN, W.NEUMANN, W.PERIODIC, W.PERIODIC]
+    else:
+        bc = [W.PERIODIC, W.PERIODIC, W.NEUMANN, W.NEUMANN]
+    bc[s] = W.VELOCITY
+    return bc, ubc
+
+
+@pytest.mark.parametrize("side", ["W", "E", "S", "N"])
+def test_zou_he_closure_defining_properties(side):
+    """Sec. 2.9.1 velocity sides (Zou-He closure) with a normal and a tangential
+    velocity component.  Streaming only, so the state after one step is the closed
+    boundary node itself.  The closure leaves the populations that streaming brought
+    in untouched (their values are the index shift of the start state), and the
+    unknown ones make (i) the node's momentum exactly rho u_bc, rho being the node's
+    own sum, and (ii) the non-equilibrium part of the unknown normal population equal
+    that of its opposite (bounce-back of the non-equilibrium part)."""
+    nx, ny = 9, 8
+    u_bc = {"W": (0.045, -0.03), "E": (0.035, 0.025), "S": (-0.02, 0.04), "N": (0.03, 0.05)}[side]
+    bc, ubc = _side_layout(side, u_bc)
+    c = oracle.Case(oracle.lattice_params(nx, ny, bc=bc, ubc=ubc, collision=W.STREAM_ONLY))
+    f0 = W.random_populations(21, nx, ny, amp=0.1)
+    c.set_populations(f0)
+    c.step(1)
+    f1 = c.populations()
+    shifted = np.stack([np.roll(np.roll(f0[i], EY[i], axis=0), EX[i], axis=1) for i in range(9)])
+    if side in "WE":
+        x = 0 if side == "W" else nx - 1
+        nodes = f1[:, :, x].T                    # (ny, 9)
+        known_src = shifted[:, :, x].T
+        normal = np.array([1.0, 0.0]) if side == "W" else np.array([-1.0, 0.0])
+    else:
+        y = 0 if side == "S" else ny - 1
+        nodes = f1[:, y, :].T
+        known_src = shifted[:, y, :].T
+        normal = np.array([0.0, 1.0]) if side == "S" else np.array([0.0, -1.0])
+    E = np.stack([EX, EY], axis=1)
+    unknown = (E @ normal) > 0                    # pointing into the lattice
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    i_n = int(np.flatnonzero((E == normal).all(axis=1))[0])
+    for f, fk in zip(nodes, known_src):
+        np.testing.assert_array_equal(f[~unknown], fk[~unknown])
+        rho = f.sum()
+        np.testing.assert_allclose(f @ E, rho * np.array(u_bc), rtol=0, atol=1e-16)
+        feq = oracle.feq(rho, *u_bc)
+        assert f[i_n] - feq[i_n] == pytest.approx(f[opp[i_n]] - feq[opp[i_n]], abs=1e-16)
+
+
+@pytest.mark.parametrize("inflow", ["W", "S"])
+def test_zou_he_uniform_stream_passes_unchanged(inflow):
+    """A uniform stream entering through a Zou-He velocity side at its own velocity
+    (normal and tangential parts) and leaving through the zero-gradient opposite
+    side is an exact steady state of the lattice (BGK, no force): every population
+    stays at f_eq(1, U) to round-off over many steps."""
+    U = (0.05, 0.012) if inflow == "W" else (0.015, 0.05)
+    bc, ubc = _side_layout(inflow, U)
+    nx, ny = 14, 11
+    c = oracle.Case(oracle.lattice_params(nx, ny, bc=bc, ubc=ubc, collision=W.BGK, tau=0.8))
+    c.set_uniform(1.0, *U)
+    c.step(400)
+    feq = oracle.feq(1.0, *U)
+    np.testing.assert_allclose(c.populations(), np.broadcast_to(feq[:, None, None], (9, ny, nx)),
+                               rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- CM-MRT forcing moments
+_CM_ORDER = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (2, 1), (1, 2), (2, 2)]
+
+
+def _maxwellian_central_moments(rho, ax, ay, npts=6):
+    """Central moments of the continuous Maxwellian f_M (temperature c_s^2) and of its
+    force term -a.grad_xi f_M = f_M a.(xi - u)/c_s^2, by tensor Gauss-Hermite
+    quadrature (probabilists' nodes; exact for these polynomial degrees)."""
+    z, w = np.polynomial.hermite_e.hermegauss(npts)
+    w = w / math.sqrt(2.0 * math.pi)
+    cx, cy = np.meshgrid(math.sqrt(CS2) * z, math.sqrt(CS2) * z, indexing="ij")
+    W2 = np.outer(w, w)
+    keq = np.array([rho * (W2 * cx ** p * cy ** q).sum() for p, q in _CM_ORDER])
+    R = np.array([rho * (W2 * cx ** p * cy ** q * (ax * cx + ay * cy) / CS2).sum() for p, q in _CM_ORDER])
+    return keq, R
+
+
+def test_cmmrt_forcing_moments_gauss_hermite():
+    """Eq. 5 with every rate 1: the post-collision central moments (about the Eq. 4
+    velocity) are k_eq + R/2, with k_eq and R the central moments of the continuous
+    Maxwellian and of its force term, computed here by quadrature rather than taken
+    from the oracle.  Unequal F_x and F_y separate the two third-order moments."""
+    f = W.random_populations(17, 1, 1, amp=0.15)[:, 0, 0]
+    Fx, Fy = 3.1e-3, -1.3e-3
+    p = oracle.lattice_params(4, 4, collision=W.CMMRT, tau=1.0, cm_sq=1.0, cm_se=1.0)
+    g = oracle.collide_node(p, f, Fx, Fy)
+    rho = f.sum()
+    ux, uy = ((f * EX).sum() + 0.5 * Fx) / rho, ((f * EY).sum() + 0.5 * Fy) / rho
+    k = np.array([(g * (EX - ux) ** a * (EY - uy) ** b).sum() for a, b in _CM_ORDER])
+    keq, R = _maxwellian_central_moments(rho, Fx / rho, Fy / rho)
+    assert R[6] == pytest.approx(CS2 * Fy, rel=1e-12) and R[7] == pytest.approx(CS2 * Fx, rel=1e-12)
+    np.testing.assert_allclose(k, keq + 0.5 * R, rtol=0, atol=4e-15)
