@@ -36,9 +36,9 @@ METRIC = "MLUPS & % of HBM peak per IB-LBM step; batched cases/s with p50/p99 la
 UNIT = "MLUPS"
 BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # DRAM bytes (read + write) per node of one FP32 stream-collide launch, by (variant,
-# operator), and per lattice of the edge launch, from the ncu section captures summarised in
-# profiles/sweep_matrix36_f32.md (12-lattice case, scaled by nodes).  A sweep whose kernels
-# have no entry here (or changed since) reports traffic null.
+# operator), and per lattice of the edge launch, from ncu section captures of the
+# 12-lattice case (scaled by nodes).  A sweep whose kernels have no entry here (or changed
+# since) reports traffic null.
 SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): 564.13e6 / 8388608, (2, W.TRT): 563.61e6 / 8388608,
                              (2, W.CMMRT): 564.38e6 / 8388608}
 # The edge launch gained the zero-velocity wall-closure branch after its capture: no figure

@@ -94,7 +94,9 @@ typedef struct {
                                    closure with its tangential correction (Sec. 2.9.3 names Zou
                                    and He); 1 = on-node bounce-back of the unknown populations,
                                    the same closure at u = 0 without the tangential correction,
-                                   which stays stable with BGK below tau ~ 0.6 */
+                                   which stays stable with BGK below tau ~ 0.6.  A side takes
+                                   the bounce-back form when its u_bc is exactly (0, 0) in FP64;
+                                   any other value is INVALID_ARG */
 } iblbm_lattice_desc;
 
 typedef struct {
@@ -301,9 +303,11 @@ int iblbm_server_stats(const iblbm_server* srv, size_t* used_bytes, int* residen
 
 /* ---- allocation-free lambda_k ------------------------------------------------------------ */
 /* No counterpart in the paper.  For callers that cannot allocate device memory
- * where they need the DFC factors lambda_k of Eq. 17 (during CUDA stream
- * capture, inside frameworks that own every device allocation, in real-time
- * loops), this call computes lambda_k for one marker set without allocating:
+ * where they need the DFC factors lambda_k of Eq. 17 (host code inside a
+ * framework that owns every device allocation, a solver embedded in another
+ * application's time loop where an allocation would synchronise the device or
+ * could fail mid-run, real-time loops where an allocation could block), this
+ * call computes lambda_k for one marker set without allocating:
  * no cudaMalloc, cudaFree or allocating library routine.  Its scratch (W_total
  * on the markers' bounding box) is a library-wide device array of 2^18 FP64
  * values, so the box -- (max - min stencil origin + S) in x times the same in y,

@@ -228,6 +228,7 @@ int iblbm_create(const iblbm_lattice_desc* d, int collision, double tau, iblbm_c
     if (collision < 0 || collision > 3 || !(tau > 0.5) || !std::isfinite(tau)) return IBLBM_ERR_INVALID_ARG;
     if (collision == COL_TRT && !(d->trt_lambda > 0.0)) return IBLBM_ERR_INVALID_ARG;
     if (!(d->init_rho > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    if (d->wall_closure != 0 && d->wall_closure != 1) return IBLBM_ERR_INVALID_ARG;
     iblbm_ctx* c = new iblbm_ctx();
     cudaGetDevice(&c->device);
     c->desc = *d;
@@ -253,7 +254,10 @@ int iblbm_create(const iblbm_lattice_desc* d, int collision, double tau, iblbm_c
         h.ubc[s][0] = d->u_bc[s][0];
         h.ubc[s][1] = d->u_bc[s][1];
     }
-    h.wall_closure = d->wall_closure;
+    h.wall_bb = 0;
+    for (int s = 0; s < 4; ++s)
+        if (d->wall_closure == 1 && d->bc[s] == BC_VEL && d->u_bc[s][0] == 0.0 && d->u_bc[s][1] == 0.0)
+            h.wall_bb |= 1 << s;
     h.tau = tau;
     h.omega = 1.0 / tau;
     h.s_e = 1.0 / tau;

@@ -57,7 +57,8 @@ struct CaseDev {
     BodyDev* bodies;              // device array [kMaxBodies]
     unsigned long long step;
     unsigned int status;
-    int wall_closure;             // 1: zero-velocity walls by on-node bounce-back of the unknowns
+    int wall_bb;                  // bit s: side s closes by on-node bounce-back (wall_closure = 1 and a
+                                  // zero velocity, decided once on the host from the FP64 u_bc)
 };
 
 // Dynamic FP64 state of a rigid body (what a checkpoint carries besides arrays).
@@ -383,14 +384,15 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
 // tangent t: rho = (1 + sum_{e.n=0} s + 2 sum_{e.n<0} s) / (1 - u.n) and for every
 // unknown population (e.n > 0):
 //   s_i = s_opp + 6 w_i rho (e_i.u) + (e_i.t)/2 [ (2/3) rho (u.t) - sum_{e.n=0} s_j (e_j.t) ].
-// wall_closure = 1 reads a zero-velocity side as on-node bounce-back of the unknowns,
+// With ``bounce`` (wall_closure = 1 on a side whose prescribed velocity is exactly zero,
+// decided on the host in FP64) the side closes by on-node bounce-back of the unknowns,
 // s_i = s_opp: the closure above at u = 0 without its tangential correction.
 template <class R>
-__device__ __forceinline__ void zou_he(int side, R (&s)[9], R ux, R uy, int wall_closure = 0) {
+__device__ __forceinline__ void zou_he(int side, R (&s)[9], R ux, R uy, bool bounce = false) {
     const int nnx = side == SIDE_W ? 1 : (side == SIDE_E ? -1 : 0);
     const int nny = side == SIDE_S ? 1 : (side == SIDE_N ? -1 : 0);
     const int ttx = nnx == 0 ? 1 : 0, tty = nnx == 0 ? 0 : 1;
-    if (wall_closure == 1 && ux == R(0) && uy == R(0)) {
+    if (bounce) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             if (ex(i) * nnx + ey(i) * nny > 0) s[i] = s[opp(i)];
@@ -476,7 +478,7 @@ __device__ void post_stream_node(const CaseDev& C, const S* __restrict__ src, in
         return;
     }
     pull_node<S, R>(C, src, x, y, s);
-    zou_he<R>(side, s, R(C.ubc[side][0]), R(C.ubc[side][1]), C.wall_closure);
+    zou_he<R>(side, s, R(C.ubc[side][0]), R(C.ubc[side][1]), (C.wall_bb >> side) & 1);
 }
 
 // ---- regularised delta kernels (Eq. 9, Eq. 10) --------------------------------------------

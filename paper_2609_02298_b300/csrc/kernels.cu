@@ -180,7 +180,7 @@ __device__ __forceinline__ void sc_row(const ScCase<S>& K, int y, int xseg, int 
                             R t[9];
 #pragma unroll
                             for (int i = 0; i < 9; ++i) t[i] = s[i][k];
-                            zou_he<R>(SIDE_E, t, R(C.ubc[SIDE_E][0]), R(C.ubc[SIDE_E][1]), C.wall_closure);
+                            zou_he<R>(SIDE_E, t, R(C.ubc[SIDE_E][0]), R(C.ubc[SIDE_E][1]), (C.wall_bb >> SIDE_E) & 1);
 #pragma unroll
                             for (int i = 0; i < 9; ++i) s[i][k] = t[i];
                         }
@@ -194,7 +194,7 @@ __device__ __forceinline__ void sc_row(const ScCase<S>& K, int y, int xseg, int 
                     R t[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) t[i] = s[i][0];
-                    zou_he<R>(SIDE_W, t, R(C.ubc[SIDE_W][0]), R(C.ubc[SIDE_W][1]), C.wall_closure);
+                    zou_he<R>(SIDE_W, t, R(C.ubc[SIDE_W][0]), R(C.ubc[SIDE_W][1]), (C.wall_bb >> SIDE_W) & 1);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) s[i][0] = t[i];
                 }

@@ -202,6 +202,96 @@ def check_cylinder_re20_f32(steps=2000, nx=200):
     assert np.abs(hg[:, 1] - hc[:, 1]).max() / scale < 1e-4 * np.abs(cd_c).max()
 
 
+_ORACLE_CACHE = {}
+
+
+def check_cylinder_re20_f32_scheme(collision, kernel, scheme, steps=2000, nx=200):
+    """The FP32 bar of check_cylinder_re20_f32 for another operator, kernel and
+    scheme of the same 200x100 Re = 20 cylinder (MDF adaptive in [5, 20]).  The lift
+    bar is taken relative to the drag: at Re = 20 the flow is steady and symmetric,
+    so the lift itself is round-off and a bar relative to it would be meaningless."""
+    spec = W.fixed_cylinder_re20(storage=W.F32, steps=steps, collision=collision, kernel=kernel,
+                                 scheme=scheme)
+    spec.nx = nx
+    key = ("re20", collision, kernel, scheme, steps, nx)
+    if key not in _ORACLE_CACHE:   # the oracle's result does not depend on the device variant
+        c = oracle_case(spec)
+        c.step(steps)
+        _ORACLE_CACHE[key] = (np.stack(velocity(c.populations())), c.force_history(0))
+    uc, hc = _ORACLE_CACHE[key]
+    g = gpu_case(spec)
+    g.step(steps)
+    assert g.sync() >= 0
+    ug = np.stack(velocity(g.populations()))
+    assert rel_l2(ug, uc) < 1e-5
+    hg = g.force_history(0)
+    scale = 0.5 * 0.05 ** 2 * 20.0
+    cd_max = np.abs(hc[:, 0]).max() / scale
+    assert np.abs(hg[:, 0] - hc[:, 0]).max() / scale < 1e-4 * cd_max
+    assert np.abs(hg[:, 1] - hc[:, 1]).max() / scale < 1e-4 * cd_max
+
+
+def _full_size_oracle(args):
+    """Worker of check_full_size_matrix (runs in a spawned process): the oracle's
+    velocity field and force history after ``steps`` steps of one lattice."""
+    spec, steps = args
+    c = oracle_case(spec)
+    c.step(steps)
+    ux, uy = velocity(c.populations())
+    return ux, uy, c.force_history(0)
+
+
+_FULL_SIZE_CACHE = {}
+
+
+def full_size_matrix_specs(re):
+    """The 18 lattices of one Reynolds-number half of the 2048x1024 FP32 matrix:
+    {DF, MDF(5), DFC} x {hat, Peskin} x {BGK, TRT, CM-MRT}."""
+    return [W.fixed_cylinder_2048(re=re, storage=W.F32, collision=col, kernel=ker, scheme=sch)
+            for sch in (W.DF, W.MDF, W.DFC) for ker in (W.HAT, W.PESKIN4) for col in (W.BGK, W.TRT, W.CMMRT)]
+
+
+def full_size_oracle(re, steps):
+    """Oracle results for full_size_matrix_specs(re), computed once per process in a
+    pool of spawned workers (a fork after CUDA initialisation is unsafe)."""
+    key = (re, steps)
+    if key not in _FULL_SIZE_CACHE:
+        import multiprocessing as mp
+        import os
+        specs = full_size_matrix_specs(re)
+        workers = max(1, min(len(specs), (os.cpu_count() or 1), 9))
+        with mp.get_context("spawn").Pool(workers) as pool:
+            _FULL_SIZE_CACHE[key] = pool.map(_full_size_oracle, [(s, steps) for s in specs], chunksize=1)
+    return _FULL_SIZE_CACHE[key]
+
+
+def check_full_size_matrix(L, re, steps=5):
+    """All 18 lattices of one Reynolds-number half of the benchmarked matrix
+    (2048x1024, D = 64, 201 markers, FP32 shifted storage, MDF with 5 fixed
+    iterations), stepped together in one batch as the benchmark steps them, each
+    compared over the whole field with the FP64 oracle: velocity within 1e-5
+    relative L2 and the force history within 1e-4 of the drag."""
+    specs = full_size_matrix_specs(re)
+    ref = full_size_oracle(re, steps)
+    gs = [gpu_case(s) for s in specs]
+    try:
+        L.step_batch(gs, steps)
+        for g, s, (ux, uy, hc) in zip(gs, specs, ref):
+            assert g.sync() >= 0, s.name
+            ug = velocity(g.populations())
+            err = rel_l2(np.stack(ug), np.stack([ux, uy]))
+            b = s.bodies[0]
+            tag = "%s scheme %d kernel %d collision %d" % (s.name, b.scheme, b.kernel, s.collision)
+            assert err < 1e-5, (tag, err)
+            hg = g.force_history(0)
+            assert hg.shape == hc.shape, tag
+            drag = np.abs(hc[:, 0]).max()
+            assert np.abs(hg[:, :2] - hc[:, :2]).max() < 1e-4 * drag, (tag, hg, hc)
+    finally:
+        for g in gs:
+            g.close()
+
+
 def check_f16_storage(steps=300, nx=200):
     """FP16 stores s = f - w with unit round-off u16 = 2^-11.  One rounding per
     stored population per step perturbs the velocity by at most about

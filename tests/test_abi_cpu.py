@@ -72,6 +72,9 @@ def test_create_rejects_bad_arguments_without_device_work():
     d.bc[1] = L.BC_PERIODIC
     assert lib.iblbm_create(C.byref(d), L.BGK, 0.5, C.byref(h)) == -1      # tau <= 1/2
     assert lib.iblbm_create(C.byref(d), 7, 0.8, C.byref(h)) == -1          # unknown collision
+    d.wall_closure = 2                                                     # only 0 or 1
+    assert lib.iblbm_create(C.byref(d), L.BGK, 0.8, C.byref(h)) == -1
+    d.wall_closure = 0
     assert lib.iblbm_create(None, L.BGK, 0.8, C.byref(h)) == -1
     assert lib.iblbm_step(None, 1) == -1
     assert lib.iblbm_step_batch(None, 0, 1) == -1

@@ -88,6 +88,18 @@ def test_cylinder_re20_2000_steps_f32():
     P.check_cylinder_re20_f32()
 
 
+@pytest.mark.parametrize("collision,kernel,scheme", [(W.TRT, W.PESKIN4, W.MDF), (W.CMMRT, W.PESKIN4, W.MDF),
+                                                      (W.TRT, W.PESKIN4, W.DFC), (W.CMMRT, W.PESKIN4, W.DFC),
+                                                      (W.BGK, W.HAT, W.MDF), (W.BGK, W.HAT, W.DFC)])
+def test_cylinder_re20_2000_steps_f32_schemes(collision, kernel, scheme):
+    P.check_cylinder_re20_f32_scheme(collision, kernel, scheme)
+
+
+@pytest.mark.parametrize("re", [100.0, 200.0])
+def test_full_size_matrix_2048x1024_f32(re):
+    P.check_full_size_matrix(L, re)
+
+
 def test_f16_storage_within_roundoff_bound():
     P.check_f16_storage()
 

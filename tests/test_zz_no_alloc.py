@@ -1,18 +1,20 @@
 """The allocation-free lambda_k entry point, iblbm_dfc_lambda_noalloc.
 
 Some callers cannot allocate device memory at the point where they need the
-DFC factors (while a stream is being captured, inside frameworks that own all
-device memory, in real-time loops).  The entry point keeps its scratch in a
-library-wide device array instead.  These checks call it through the C ABI on
-two marker sets in a row -- the second call reuses the array the first left
-behind -- and compare each result with lambda_k as the regular path computes
-it (a fixed DFC body on an FP64 lattice, read back after one step), within the
-FP64 bar of the parity suite (1e-12).  This file is collected last."""
+DFC factors (inside frameworks that own all device memory, solvers embedded in
+another application's time loop, real-time loops).  The entry point keeps its
+scratch in a library-wide device array instead.  These checks call it through
+the C ABI on two marker sets in a row -- the second call reuses the array the
+first left behind -- and compare each result with lambda_k as the regular path
+computes it (a fixed DFC body on an FP64 lattice, read back after one step) and
+with the FP64 oracle's Eq. 17, within the FP64 bar of the parity suite (1e-12).
+This file is collected last."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -60,6 +62,20 @@ def test_noalloc_lambda_matches_regular_path_on_consecutive_calls():
         assert rc == 0, L.strerror(rc)
         assert np.all(np.isfinite(lam))
         assert np.abs(lam - lam_ref).max() < TOL * np.abs(lam_ref).max()
+        lam_orc = oracle.dfc_lambda(kernel, xy, ds, nx, ny)
+        assert np.abs(lam - lam_orc).max() < TOL * np.abs(lam_orc).max()
+
+
+def test_noalloc_lambda_skewed_box_matches_oracle():
+    """A marker set whose bounding box is one stencil wide and thousands of nodes
+    tall (a vertical line of markers), so the W_total pass walks many tiles."""
+    n, nx, ny = 3000, 40, 3200
+    xy = np.stack([np.full(n, 20.37), 50.0 + 1.01 * np.arange(n)], axis=1)
+    for kernel in (W.HAT, W.PESKIN4):
+        rc, lam = _noalloc_lambda(xy, 1.01, kernel, nx, ny)
+        assert rc == 0, L.strerror(rc)
+        lam_orc = oracle.dfc_lambda(kernel, xy, 1.01, nx, ny)
+        assert np.abs(lam - lam_orc).max() < TOL * np.abs(lam_orc).max()
 
 
 def test_noalloc_lambda_rejects_oversized_box():
