@@ -266,6 +266,17 @@ int iblbm_step_batch(iblbm_ctx** ctxs, int n, int nsteps);
  * Errors: INVALID_ARG. */
 #define IBLBM_KERNEL_VARIANTS 4
 int iblbm_set_kernel_variant(int storage, int collision, int variant);
+/* Test hook of the bounded device wait (no counterpart in the paper).  The bulk
+ * variant's consumer warps wait for each staged tile for at most a fixed number
+ * of polls and then give up: the launch raises IBLBM_ERR_TIMEOUT in the status
+ * of the lattice it was sweeping, and its producer waits (bounded, unchanged by
+ * this call) for the copies it still has in flight before the CTA exits.  This
+ * call sets that consumer poll count process-wide (polls >= 0; 0 gives up at
+ * the first wait) or restores the default bound (polls < 0), so a test can run
+ * the give-up path without a copy that never lands.  A step taken while it is
+ * lowered leaves the lattice's populations undefined.  Syncs the device.
+ * Errors: CUDA. */
+int iblbm_test_set_consumer_poll_limit(long polls);
 int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);
 
 /* ---- serving loop ---------------------------------------------------------------------- */

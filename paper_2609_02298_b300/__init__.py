@@ -88,6 +88,7 @@ SIGNATURES = [
     ("iblbm_dfc_lambda_noalloc", _i, [_vp, _i, _d, _i, _i, _i, _vp, _vp]),
     ("iblbm_set_kernel_variant", _i, [_i, _i, _i]),
     ("iblbm_kernel_variant", _i, [_i, _i, _pi, _pd]),
+    ("iblbm_test_set_consumer_poll_limit", _i, [C.c_long]),
     ("iblbm_server_create", _i, [_sz, _i, _vp, _P(_vp)]),
     ("iblbm_server_destroy", None, [_vp]),
     ("iblbm_server_submit", _i, [_vp, _P(LatticeDesc), _i, _d, _P(BodyDesc), _pd, _i, _d, _i, _i, _i,
@@ -406,6 +407,11 @@ def set_kernel_variant(storage: int, collision: int, variant: int) -> None:
 
 
 KERNEL_VARIANTS = 4   # IBLBM_KERNEL_VARIANTS
+
+
+def test_set_consumer_poll_limit(polls: int) -> None:
+    """Test hook: polls after which the bulk sweep's consumers give up (negative: default)."""
+    _check(load_library().iblbm_test_set_consumer_poll_limit(int(polls)), "iblbm_test_set_consumer_poll_limit")
 
 
 def kernel_variant(storage: int, collision: int):

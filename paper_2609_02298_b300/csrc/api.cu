@@ -1118,6 +1118,14 @@ extern "C" int iblbm_set_kernel_variant(int storage, int collision, int variant)
     return IBLBM_OK;
 }
 
+extern "C" int iblbm_test_set_consumer_poll_limit(long polls) {
+    if (cudaDeviceSynchronize() != cudaSuccess || set_consumer_poll_limit(polls) != cudaSuccess) {
+        cudaGetLastError();
+        return IBLBM_ERR_CUDA;
+    }
+    return IBLBM_OK;
+}
+
 extern "C" int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms) {
     if (storage < 0 || storage > 2 || collision < 0 || collision > 3) return IBLBM_ERR_INVALID_ARG;
     const int cls = g_variant[storage][collision][1] >= 0 ? 1 : 0;   // the large class when tuned

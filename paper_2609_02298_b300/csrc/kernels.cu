@@ -451,6 +451,19 @@ constexpr long kBulkSpinLimit = 1L << 22;   // polls of an mbarrier before the k
 #else
 constexpr long kBulkSpinLimit = 1L << 16;   // host emulation: each poll yields the thread
 #endif
+// Polls of the consumers' wait for a staged tile (kBulkSpinLimit unless lowered through
+// iblbm_test_set_consumer_poll_limit, which exists to exercise the give-up path).  The
+// producer's waits, including its drain of copies still in flight, keep kBulkSpinLimit.
+__device__ long g_consumer_poll_limit = kBulkSpinLimit;
+
+// Wait for a phase, giving up after `limit` polls or as soon as `abort` is raised.
+__device__ __forceinline__ bool bar_wait_unless(uint64_t* bar, unsigned parity, long limit, volatile int& abort) {
+    for (long it = 0; it < limit; ++it) {
+        if (bar_test(bar, parity)) return true;
+        if (abort) return false;
+    }
+    return false;
+}
 
 __device__ __forceinline__ double lds1(const double* p) { return *p; }
 __device__ __forceinline__ float lds1(const float* p) { return *p; }
@@ -612,7 +625,8 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
             for (; job < j1 && !abort_flag; ++job) {
                 const long long t = job - j0;
                 const int k = (int)(t % NST);
-                if (t >= NST && !bar_wait(&empty[k], (unsigned)(((t / NST) - 1) & 1), kBulkSpinLimit)) {
+                if (t >= NST &&
+                    !bar_wait_unless(&empty[k], (unsigned)(((t / NST) - 1) & 1), kBulkSpinLimit, abort_flag)) {
                     abort_flag = 1;
                     break;
                 }
@@ -635,12 +649,13 @@ __global__ void __launch_bounds__(kBulkThreads, (BulkCfg<S>::MINB)) sc_kernel_bu
 
     // consumer warps
     const int lane = tid & 31;
+    const long poll_limit = g_consumer_poll_limit;
     ScCase<S> K;
     int cur = -1;
     for (long long job = j0; job < j1; ++job) {
         const long long t = job - j0;
         const int k = (int)(t % NST);
-        if (!bar_wait(&full[k], (unsigned)((t / NST) & 1), kBulkSpinLimit) || abort_flag) {
+        if (!bar_wait(&full[k], (unsigned)((t / NST) & 1), poll_limit) || abort_flag) {
             abort_flag = 1;
             break;
         }
@@ -1882,6 +1897,14 @@ cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux
     default: IBLBM_LAUNCH(macro_kernel<__half>, g, 256, st, dc, rho, ux, uy); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t set_consumer_poll_limit(long polls) {
+    const long v = polls < 0 ? kBulkSpinLimit : polls;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, (const void*)&g_consumer_poll_limit);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice);
 }
 
 }  // namespace iblbm

@@ -71,5 +71,8 @@ cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux
 cudaError_t launch_diagnostics(const CaseDev* hc, CaseDev* dc, int body, double u_ref, double kappa, double* out,
                                double* pm, cudaStream_t st);
 int sc_blocks_per_sm(int storage, int collision, int variant);
+// Polls after which the bulk sweep's consumer warps give up waiting for a staged tile
+// (negative: the default bound).  Process-wide; for tests of the give-up path.
+cudaError_t set_consumer_poll_limit(long polls);
 
 }  // namespace iblbm

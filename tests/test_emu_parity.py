@@ -193,6 +193,35 @@ def test_bulk_copy_that_never_lands_reports_timeout(L, monkeypatch):
     h.close()
 
 
+def test_bulk_consumer_poll_limit_gives_up(L):
+    """The device-side give-up path as the GPU test drives it: consumers told to give up
+    at their first wait, the launch reports the timeout status and returns, and with the
+    default bound restored a fresh lattice steps to the same state as before."""
+    bulk_only(L)
+    spec = W.CaseSpec(name="t", nx=1600, ny=5, bc=(W.PERIODIC,) * 4, ubc=((0, 0),) * 4,
+                      collision=W.BGK, tau=0.8, storage=W.F32)
+    ref = L.Lattice.from_spec(spec)
+    ref.step(2)
+    assert ref.sync() == 0
+    want = ref.populations(shifted=True)
+    ref.close()
+    try:
+        L.test_set_consumer_poll_limit(0)
+        g = L.Lattice.from_spec(spec)
+        g.step(1)
+        with pytest.raises(L.IblbmError) as err:
+            g.sync()
+        assert err.value.code == -6   # IBLBM_ERR_TIMEOUT
+        g.close()
+    finally:
+        L.test_set_consumer_poll_limit(-1)
+    h = L.Lattice.from_spec(spec)
+    h.step(2)
+    assert h.sync() == 0
+    np.testing.assert_array_equal(h.populations(shifted=True), want)
+    h.close()
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_local_diagnostics(L, scheme, kernel):

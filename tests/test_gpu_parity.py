@@ -183,3 +183,34 @@ def test_taylor_green_ib(scheme, kernel, D):
 def test_domain_conditions_bounce_back_walls(name, nx, ny):
     """wall_closure = 1: zero-velocity sides by on-node bounce-back, moving sides by Zou-He."""
     P.check_domain_conditions_f64(name, nx, ny, wall_closure=1)
+
+
+def test_bulk_sweep_wait_gives_up_with_timeout_status(variant):
+    """Failure detection on the device, without a fault: the bulk variant's consumer
+    warps are told to give up at their first wait for a staged tile, so the launch
+    must come back with IBLBM_ERR_TIMEOUT (the producer still drains its copies in
+    flight under its normal bound); with the default bound restored the library
+    steps a fresh lattice exactly as before."""
+    spec = P.channel_spec(300, 40, collision=W.BGK, storage=W.F32)
+    ref = L.Lattice.from_spec(spec)
+    ref.step(4)
+    assert ref.sync() == 0
+    want = ref.populations(shifted=True)
+    ref.close()
+    L.set_kernel_variant(W.F32, W.BGK, 3)
+    try:
+        L.test_set_consumer_poll_limit(0)
+        bad = L.Lattice.from_spec(spec)
+        bad.step(1)
+        with pytest.raises(L.IblbmError) as err:
+            bad.sync()
+        assert err.value.code == -6      # IBLBM_ERR_TIMEOUT
+        bad.close()
+    finally:
+        L.test_set_consumer_poll_limit(-1)
+        L.set_kernel_variant(W.F32, W.BGK, variant)
+    again = L.Lattice.from_spec(spec)
+    again.step(4)
+    assert again.sync() == 0
+    np.testing.assert_array_equal(again.populations(shifted=True), want)
+    again.close()
