@@ -85,15 +85,22 @@ def sweep_traffic(L, specs):
     return total
 
 
-def launches_per_step(specs) -> int:
-    """Kernel launches of one batched step: body prepare and one IB launch per
-    storage type (when any lattice has bodies), one stream-collide launch per
-    (storage, collision) group, one lattice-edge launch per storage type, and the
-    finishing body/counter launch."""
+def launches_per_step(specs, L=None) -> int:
+    """Kernel launches of one batched step: one IB launch per storage type with bodies
+    (body motion folded in), one stream-collide launch per (storage, collision) group,
+    and -- when every body is fixed and the tuned sweeps are the one- or two-node-per-lane
+    kernels, so the IB stage overlaps the sweep -- one launch per group with bodies for
+    the IB-region segments; then one lattice-edge launch per storage type and the
+    step-counter launch."""
     storages = {s.storage for s in specs}
     with_bodies = {s.storage for s in specs if s.bodies}
     groups = {(s.storage, s.collision) for s in specs}
-    return (1 + len(with_bodies) if with_bodies else 0) + len(groups) + len(storages) + 1
+    n = len(with_bodies) + len(groups) + len(storages) + 1
+    fixed = all(b.motion == W.FIXED for s in specs for b in s.bodies)
+    phased = L is None or all(L.kernel_variant(st, col)[0] in (1, 2) for st, col in groups)
+    if with_bodies and fixed and phased:
+        n += len({(s.storage, s.collision) for s in specs if s.bodies})
+    return n
 
 
 def shard(items, rank: int, world: int):
@@ -310,6 +317,7 @@ def single_case_report(L, torch, steps=2000):
     matrix (DF, Peskin, BGK, FP32).  Small lattices are latency-bound, so these
     are reported as microseconds per step beside MLUPS."""
     out = {}
+    peak, _ = read_peaks()
     cases = [("cyl-re20-200x100-f64", W.fixed_cylinder_re20(storage=W.F64), steps),
              ("cyl-re20-200x100-f32", W.fixed_cylinder_re20(storage=W.F32), steps),
              ("cyl-re100-2048x1024-f32", W.fixed_cylinder_2048(re=100.0, storage=W.F32, collision=W.BGK,
@@ -326,8 +334,18 @@ def single_case_report(L, torch, steps=2000):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         lat.sync()
+        # per-launch breakdown: the same steps launched one by one with CUDA events around
+        # each launch (no overlap between the IB stage and the sweep in this mode)
+        m = min(n, 200)
+        lat.set_timing(True)
+        lat.step(m)
+        stages = lat.stage_timing()
+        lat.set_timing(False)
         lat.close()
-        out[name] = {"us_per_step": 1e3 * ms / n, "mlups": spec.nodes * n / (ms / 1e3) / 1e6, "steps": n}
+        out[name] = {"us_per_step": 1e3 * ms / n, "mlups": spec.nodes * n / (ms / 1e3) / 1e6, "steps": n,
+                     "hbm_fraction": spec.nodes * n / (ms / 1e3) * BYTES_PER_LU[spec.storage] / (peak * 1e9),
+                     "launch_breakdown_us_per_step": {k: 1e3 * v[0] / m for k, v in stages.items()},
+                     "launches_per_step": launches_per_step([spec], L)}
     return out
 
 
@@ -544,7 +562,7 @@ def main():
                     "d2h_bytes_per_step": d2h / args.steps, "chunks": nch},
             "kernel_variants": {name: L.kernel_variant(storage, col) for name, col in
                                 (("bgk", W.BGK), ("trt", W.TRT), ("cmmrt", W.CMMRT))},
-            "gpu_launches": launches_per_step(specs) * args.steps,
+            "gpu_launches": launches_per_step(specs, L) * args.steps,
             "clocks": clocks.summary(),
             "device_status": rc,
             "single_lattice": single,

@@ -348,6 +348,13 @@ int iblbm_dfc_lambda_noalloc(const double* xy, int n, double ds, int kernel, int
  * since the last reset, then resets.  Syncs. */
 int iblbm_set_timing(iblbm_ctx* ctx, int enable);
 int iblbm_kernel_timing(iblbm_ctx* ctx, double* stream_collide_ms, int* launches);
+/* The same timed steps broken down by stage: ms[0] / launches[0] the IB stage (body
+ * motion, interface coupling and body update: one launch per storage type with
+ * bodies), [1] the stream-collide launches, [2] the lattice-edge launches, [3] the
+ * step-counter launch; sums since the last reset, then resets (this call and
+ * iblbm_set_timing reset; iblbm_kernel_timing resets only its own sums).  Either
+ * pointer may be NULL.  Syncs.  Errors: INVALID_ARG. */
+int iblbm_stage_timing(iblbm_ctx* ctx, double ms[4], int launches[4]);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("iblbm_step_batch", _i, [_P(_vp), _i, _i]),
     ("iblbm_set_timing", _i, [_vp, _i]),
     ("iblbm_kernel_timing", _i, [_vp, _pd, _pi]),
+    ("iblbm_stage_timing", _i, [_vp, _pd, _pi]),
     ("iblbm_dfc_lambda_noalloc", _i, [_vp, _i, _d, _i, _i, _i, _vp, _vp]),
     ("iblbm_set_kernel_variant", _i, [_i, _i, _i]),
     ("iblbm_kernel_variant", _i, [_i, _i, _pi, _pd]),
@@ -399,6 +400,13 @@ class Lattice:
         ms, n = C.c_double(0), C.c_int(0)
         _check(load_library().iblbm_kernel_timing(self._h, C.byref(ms), C.byref(n)), "iblbm_kernel_timing")
         return ms.value, n.value
+
+    def stage_timing(self):
+        """{stage: (ms, launches)} for the IB stage, stream-collide, lattice edges and counters."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int * 4)()
+        _check(load_library().iblbm_stage_timing(self._h, ms, n), "iblbm_stage_timing")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("ib", "stream_collide", "edges", "counters"))}
 
 
 def set_kernel_variant(storage: int, collision: int, variant: int) -> None:

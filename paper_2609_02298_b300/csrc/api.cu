@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "iblbm.h"
@@ -96,9 +97,15 @@ struct iblbm_ctx {
     int version = 0;              // bumped when bodies change; batch plans check it
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    double sc_ms = 0;
+    struct Timed {
+        cudaEvent_t a, b;
+        int stage;                // STAGE_*
+    };
+    std::vector<Timed> ev_pending;
+    double sc_ms = 0;             // stream-collide + lattice-edge launches (iblbm_kernel_timing)
     int sc_count = 0;
+    double stage_ms[4] = {0, 0, 0, 0};   // per stage (iblbm_stage_timing)
+    int stage_n[4] = {0, 0, 0, 0};
 
     void* alloc(size_t b) {
         void* p = dev_alloc(b, work);
@@ -118,6 +125,8 @@ int check(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? IBLBM_ERR_OOM : IBLBM_ERR_CUDA;
 }
 
+enum { STAGE_IB = 0, STAGE_SWEEP = 1, STAGE_EDGE = 2, STAGE_COUNTER = 3 };
+
 cudaEvent_t pool_event(iblbm_ctx* c) {
     if (!c->ev_pool.empty()) {
         cudaEvent_t e = c->ev_pool.back();
@@ -130,16 +139,32 @@ cudaEvent_t pool_event(iblbm_ctx* c) {
 }
 
 void drain_timing(iblbm_ctx* c) {
-    for (auto& pr : c->ev_pending) {
+    for (auto& t : c->ev_pending) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
-            c->sc_ms += ms;
-            c->sc_count += 1;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            if (t.stage == STAGE_SWEEP || t.stage == STAGE_EDGE) {
+                c->sc_ms += ms;
+                c->sc_count += 1;
+            }
+            c->stage_ms[t.stage] += ms;
+            c->stage_n[t.stage] += 1;
         }
-        c->ev_pool.push_back(pr.first);
-        c->ev_pool.push_back(pr.second);
+        c->ev_pool.push_back(t.a);
+        c->ev_pool.push_back(t.b);
     }
     c->ev_pending.clear();
+}
+
+// Brackets one launch with timing events when timer is set.
+template <class F>
+cudaError_t timed_launch(iblbm_ctx* timer, int stage, cudaStream_t st, F&& launch) {
+    if (!timer) return launch();
+    cudaEvent_t a = pool_event(timer), b = pool_event(timer);
+    cudaEventRecord(a, st);
+    const cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    timer->ev_pending.push_back({a, b, stage});
+    return e;
 }
 
 int sync_status(iblbm_ctx* c) {
@@ -711,6 +736,7 @@ int iblbm_restore(iblbm_ctx* c, const void* host, size_t n) {
     }
     c->steps = h.steps;
     for (int b = 0; b < h.nbodies; ++b) c->hbodies[b].t0 = bs[b].t0;
+    c->version += 1;   // footprints are rebuilt: batch plans must build them before overlapping
     return check(cudaStreamSynchronize(w));
 }
 
@@ -721,6 +747,23 @@ int iblbm_set_timing(iblbm_ctx* c, int enable) {
     c->timing = enable != 0;
     c->sc_ms = 0;
     c->sc_count = 0;
+    for (int k = 0; k < 4; ++k) {
+        c->stage_ms[k] = 0;
+        c->stage_n[k] = 0;
+    }
+    return IBLBM_OK;
+}
+
+int iblbm_stage_timing(iblbm_ctx* c, double ms[4], int launches[4]) {
+    if (!c) return IBLBM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->work);
+    drain_timing(c);
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = c->stage_ms[k];
+        if (launches) launches[k] = c->stage_n[k];
+        c->stage_ms[k] = 0;
+        c->stage_n[k] = 0;
+    }
     return IBLBM_OK;
 }
 
@@ -774,6 +817,7 @@ struct BatchGroup {
     long long* djob[SC_VARIANTS] = {};
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
     int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
+    unsigned long long* dctr = nullptr;        // job counter of the scalar variants (2 words)
 };
 
 // Stream-collide variant per (storage, collision, size class), process-wide so
@@ -803,6 +847,19 @@ struct EdgeGroup {
     int block = 0;                             // edge nodes per chunk = threads per CTA
 };
 
+// IB-region segments of the lattices of one stream-collide group, swept after the IB
+// stage while the rest of each lattice is swept during it (same specialised kernel as
+// the group, so a node's arithmetic does not depend on the order of the launches).
+struct ListGroup {
+    int storage = 0;
+    int collision = 0;
+    CaseDev** dcases = nullptr;                // the group's lattices (list indices into it)
+    int4* dlist = nullptr;
+    long long n = 0;
+    int grid = 0;
+    unsigned long long* dctr = nullptr;
+};
+
 struct BatchPlan {
     std::vector<iblbm_ctx*> ctxs;
     std::vector<int> versions;
@@ -820,6 +877,10 @@ struct BatchPlan {
     // Lattice-edge launch overlapped with the IB stage on a side stream, when no body
     // can reach a lattice edge (the edge nodes then need no IB patch).
     bool edges_early = false;
+    // Every body fixed with a valid footprint: the IB stage runs alongside the sweep of
+    // everything outside the IB regions, whose segments are swept after it (list_groups).
+    bool overlap_ok = false;
+    std::vector<ListGroup> list_groups;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_edges = nullptr;
     ~BatchPlan() {
@@ -843,33 +904,35 @@ void* plan_alloc(BatchPlan* P, size_t b) {
 cudaError_t launch_edge_groups(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer, int noib) {
     for (auto& g : P->edge_groups) {
         EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block, noib, 0};
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (timer) {
-            a = pool_event(timer);
-            b = pool_event(timer);
-            cudaEventRecord(a, st);
-        }
-        const cudaError_t e = launch_edges(g.storage, el, st);
+        const cudaError_t e = timed_launch(timer, STAGE_EDGE, st, [&] { return launch_edges(g.storage, el, st); });
         if (e != cudaSuccess) return e;
-        if (timer) {
-            cudaEventRecord(b, st);
-            timer->ev_pending.push_back({a, b});
-        }
     }
     return cudaSuccess;
 }
 
+int chosen_variant(const BatchGroup& g) {
+    const int chosen = g_variant[g.storage][g.collision][g.size_class];
+    int v = chosen < 0 ? SC_SCALAR : chosen;
+    return g.ok[v] ? v : SC_SCALAR;
+}
+
+// One IB-LBM step of every lattice of the plan.  With every body fixed (overlap): the IB
+// stage (body motion, interface coupling, body update; one CTA per body) lets the sweeps
+// of the lattices outside their IB regions start at once (programmatic dependent
+// launch) and run beside it, then the IB-region segments are swept with the spread
+// forces; otherwise the IB stage precedes whole-lattice sweeps.  Lattice-edge nodes run
+// on a side stream during the IB stage when no body can reach them, else after the
+// sweeps; the step counters advance last.
 cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     cudaError_t e = cudaSuccess;
-    FinLaunch all{P->drefs_all, P->nrefs_all, (int)P->ctxs.size(), P->dcases_all};
-    // edge nodes first, on a side stream, while the IB stage runs (they read only the
-    // source populations; launch by launch on one stream when timing)
     // (not with the vector variant, whose launch also writes side nodes that the edge
     // launch must overwrite afterwards)
     bool early = P->edges_early && !timer;
+    bool overlap = P->overlap_ok && !timer;
     for (auto& g : P->groups) {
-        const int chosen = g_variant[g.storage][g.collision][g.size_class];
-        if ((chosen < 0 ? SC_SCALAR : chosen) == SC_VECTOR && g.ok[SC_VECTOR]) early = false;
+        const int v = chosen_variant(g);
+        if (v == SC_VECTOR) early = false;
+        if (!sc_variant_phased(v)) overlap = false;
     }
     if (early) {
         cudaEventRecord(P->ev_fork, st);
@@ -877,34 +940,88 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         if ((e = launch_edge_groups(P, P->side, nullptr, 1)) != cudaSuccess) return e;
         cudaEventRecord(P->ev_edges, P->side);
     }
-    if (P->nrefs_all > 0) {
-        if ((e = launch_body(all, 0, st)) != cudaSuccess) return e;
-        for (auto& g : P->ib_groups) {
-            IbLaunch il{g.drefs, g.nrefs, 0};
-            if ((e = launch_ib(g.storage, il, st)) != cudaSuccess) return e;
-        }
-    }
-    for (auto& g : P->groups) {
-        const int chosen = g_variant[g.storage][g.collision][g.size_class];
-        int v = chosen < 0 ? SC_SCALAR : chosen;
-        if (!g.ok[v]) v = SC_SCALAR;
-        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v]};
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (timer) {
-            a = pool_event(timer);
-            b = pool_event(timer);
-            cudaEventRecord(a, st);
-        }
-        if ((e = launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st)) != cudaSuccess)
+    for (size_t k = 0; k < P->ib_groups.size(); ++k) {
+        const auto& g = P->ib_groups[k];
+        const bool last = k + 1 == P->ib_groups.size();
+        IbLaunch il{g.drefs, g.nrefs, 0, (overlap && last) ? (int)PDL_TRIGGER : 0};
+        if ((e = timed_launch(timer, STAGE_IB, st, [&] { return launch_ib(g.storage, il, st); })) != cudaSuccess)
             return e;
-        if (timer) {
-            cudaEventRecord(b, st);
-            timer->ev_pending.push_back({a, b});
-        }
     }
+    const bool dependent = overlap && !P->ib_groups.empty();
+    for (auto& g : P->groups) {
+        const int v = chosen_variant(g);
+        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], g.dctr, nullptr, overlap ? (int)SC_SKIP_IB : (int)SC_ALL,
+                    dependent ? (int)(PDL_TRIGGER | PDL_DEPENDENT) : 0};
+        if ((e = timed_launch(timer, STAGE_SWEEP, st, [&] {
+                 return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st);
+             })) != cudaSuccess)
+            return e;
+    }
+    if (overlap)
+        for (auto& lg : P->list_groups) {
+            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dctr, lg.dlist, (int)SC_LIST, 0};
+            if ((e = launch_stream_collide(lg.storage, lg.collision, SC_SCALAR2, sl, lg.n, lg.grid, st)) !=
+                cudaSuccess)
+                return e;
+        }
     if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // join before the step counters advance
     else if ((e = launch_edge_groups(P, st, timer, 0)) != cudaSuccess) return e;
-    return launch_body(all, 1, st);
+    return timed_launch(timer, STAGE_COUNTER, st, [&] { return launch_counters(P->dcases_all, (int)P->ctxs.size(), st); });
+}
+
+// IB-region segment lists of an overlap plan: footprints are built at the bodies'
+// (fixed) markers, the boxes read back and every kIbAlign-aligned 64-node segment of
+// their rows listed once per lattice.  Leaves overlap_ok false when a body is not fixed
+// or has no footprint.
+int build_ib_lists(BatchPlan* P, int sms) {
+    P->overlap_ok = false;
+    if (P->ib_groups.empty()) return IBLBM_OK;
+    for (auto* c : P->ctxs)
+        for (auto& b : c->bodies)
+            if (b.motion != MOT_FIXED) return IBLBM_OK;
+    for (auto& g : P->ib_groups) {
+        IbLaunch setup{g.drefs, g.nrefs, 1, 0};
+        int rc = check(launch_ib(g.storage, setup, P->st));
+        if (rc) return rc;
+    }
+    int rc = check(cudaStreamSynchronize(P->st));
+    if (rc) return rc;
+    for (auto& grp : P->groups) {
+        std::vector<int4> list;
+        int ci = 0;
+        for (auto* c : P->ctxs) {
+            if (c->hc.storage != grp.storage || c->hc.collision != grp.collision) continue;
+            std::set<std::pair<int, int>> segs;
+            for (int b = 0; b < (int)c->bodies.size(); ++b) {
+                BodyDev B;
+                if (cudaMemcpy(&B, &c->dbodies[b], sizeof(BodyDev), cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return check(cudaGetLastError());
+                if (B.nfp <= 0) return IBLBM_OK;
+                for (int y = B.by0; y < B.by0 + B.bh; ++y)
+                    for (int x = 0; x < c->hc.nx; x += kIbAlign)
+                        if (in_ib_region(y, x, B.bx0, B.by0, B.bw, B.bh)) segs.insert({y, x});
+            }
+            for (auto& sg : segs) list.push_back(make_int4(ci, sg.first, sg.second, 0));
+            ++ci;
+        }
+        if (list.empty()) continue;
+        ListGroup lg;
+        lg.storage = grp.storage;
+        lg.collision = grp.collision;
+        lg.dcases = grp.dcases;
+        lg.n = (long long)list.size();
+        lg.grid = (int)std::max<long long>(1, std::min<long long>((lg.n + 15) / 16, 4LL * sms));
+        lg.dlist = static_cast<int4*>(plan_alloc(P, sizeof(int4) * list.size()));
+        lg.dctr = static_cast<unsigned long long*>(plan_alloc(P, 2 * sizeof(unsigned long long)));
+        if (!lg.dlist || !lg.dctr) return IBLBM_ERR_OOM;
+        cudaMemcpyAsync(lg.dlist, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, P->st);
+        cudaMemsetAsync(lg.dctr, 0, 2 * sizeof(unsigned long long), P->st);
+        P->list_groups.push_back(lg);
+    }
+    rc = check(cudaStreamSynchronize(P->st));
+    if (rc) return rc;
+    P->overlap_ok = true;
+    return IBLBM_OK;
 }
 
 BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
@@ -1016,6 +1133,9 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                     g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
                 }
             }
+            g.dctr = static_cast<unsigned long long*>(plan_alloc(P, 2 * sizeof(unsigned long long)));
+            if (!g.dctr) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+            cudaMemsetAsync(g.dctr, 0, 2 * sizeof(unsigned long long), P->st);
             P->groups.push_back(g);
         }
     }
@@ -1046,7 +1166,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 g_variant_ms[g.storage][g.collision][g.size_class][v] = 0.0;
                 continue;
             }
-            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v]};
+            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], g.dctr, nullptr, (int)SC_ALL, 0};
             float ms = 0.f, tot = 0.f;
             launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);   // warm
             for (int r = 0; r < 3; ++r) {
@@ -1088,6 +1208,8 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         P->edges_early = true;
     }
     *rc = check(cudaStreamSynchronize(P->st));
+    if (*rc) { delete P; return nullptr; }
+    *rc = build_ib_lists(P, sms);
     if (*rc) { delete P; return nullptr; }
     g_plans[key] = P;
     return P;

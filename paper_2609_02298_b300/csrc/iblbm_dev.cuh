@@ -15,6 +15,22 @@
 #define IBLBM_LAUNCH_SMEM(kern, grid, block, smem, stream, ...) \
     kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__)
 #define IBLBM_DYNAMIC_SMEM(name) extern __shared__ __align__(128) unsigned char name[]
+// Launch that may begin before the previous kernel of the stream ends (programmatic
+// dependent launch) when `dependent` is true; a plain launch otherwise.
+#define IBLBM_LAUNCH_PDL(kern, grid, block, strm_, dependent, ...)                                  \
+    do {                                                                                           \
+        cudaLaunchConfig_t cfg_ = {};                                                              \
+        cfg_.gridDim = dim3(grid);                                                                 \
+        cfg_.blockDim = dim3(block);                                                               \
+        cfg_.dynamicSmemBytes = 0;                                                                 \
+        cfg_.stream = (strm_);                                                                     \
+        cudaLaunchAttribute at_[1];                                                                \
+        at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                            \
+        at_[0].val.programmaticStreamSerializationAllowed = 1;                                     \
+        cfg_.attrs = at_;                                                                          \
+        cfg_.numAttrs = (dependent) ? 1 : 0;                                                       \
+        cudaLaunchKernelEx(&cfg_, kern, __VA_ARGS__);                                              \
+    } while (0)
 #endif
 #include <stdint.h>
 

@@ -16,8 +16,11 @@ namespace iblbm {
 
 // ------------------------------------------------------------------------------------------
 // IB patch lookup shared by stream-collide and the macro export.
+// Returns true when a DF/MDF body spread a force onto the node (a DFC patch corrects
+// the populations and adds no force).
 template <class R>
-__device__ __forceinline__ void add_ib(const CaseDev& C, int x, int y, R (&s)[9], R& Fx, R& Fy) {
+__device__ __forceinline__ bool add_ib(const CaseDev& C, int x, int y, R (&s)[9], R& Fx, R& Fy) {
+    bool forced = false;
     for (int b = 0; b < C.nbodies; ++b) {
         const BodyDev& B = C.bodies[b];
         const int lx = x - B.bx0, ly = y - B.by0;
@@ -31,8 +34,10 @@ __device__ __forceinline__ void add_ib(const CaseDev& C, int x, int y, R (&s)[9]
         } else {
             Fx += p[0];
             Fy += p[1];
+            forced = true;
         }
     }
+    return forced;
 }
 
 __device__ __forceinline__ bool row_has_ib(const CaseDev& C, int y, int xa, int xb) {
@@ -47,6 +52,44 @@ __device__ __forceinline__ bool row_has_ib(const CaseDev& C, int y, int xa, int 
 template <class R>
 __device__ __forceinline__ bool bad_density(R rho) {
     return !(rho > R(0) && rho < R(1e30));
+}
+
+// Programmatic dependent launch (sm_90 and later): launch_dependents lets the next
+// kernel of the stream start once every CTA of this one has issued it; wait blocks
+// until the kernel this one depends on has completed and its writes are visible.
+// Both return at once for a kernel launched without the dependency.
+__device__ __forceinline__ void pdl_trigger() {
+#ifndef IBLBM_EMULATE
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#ifndef IBLBM_EMULATE
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+// True when the row segment [xseg, xseg + w) of row y lies in the IB region of a body
+// of the case (w divides kIbAlign, xseg a multiple of w).
+__device__ __forceinline__ bool seg_in_ib(const CaseDev& C, int y, int xseg) {
+    for (int b = 0; b < C.nbodies; ++b) {
+        const BodyDev& B = C.bodies[b];
+        if (B.nfp > 0 && in_ib_region(y, xseg, B.bx0, B.by0, B.bw, B.bh)) return true;
+    }
+    return false;
+}
+
+// End of a launch that takes jobs from L.ctr: the last CTA to finish resets the counters.
+__device__ __forceinline__ void release_job_counter(unsigned long long* ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(ctr + 1, 1ull);
+        if (done == (unsigned long long)gridDim.x - 1ull) {
+            ctr[0] = 0ull;
+            ctr[1] = 0ull;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -292,7 +335,6 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
     const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
-    const bool forced = ib || K.has_force;
     // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
     int koff[9];
 #pragma unroll
@@ -308,13 +350,12 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 #pragma unroll
             for (int i = 0; i < 9; ++i) s[i] = ld1_sweep(src + (a + koff[i]));
             R rho;
-            if (forced) {
-                R Fx = K.gfx, Fy = K.gfy;
-                if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
-                rho = collide<R, KIND>(K.P, s, Fx, Fy);
-            } else {
-                rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
-            }
+            // the force terms are taken per node (a node with a spread force or a body
+            // force), so a node's arithmetic does not depend on how rows are segmented
+            R Fx = K.gfx, Fy = K.gfy;
+            const bool forced = (ib && add_ib<R>(C, x, y, s, Fx, Fy)) || K.has_force;
+            if (forced) rho = collide<R, KIND>(K.P, s, Fx, Fy);
+            else rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
             unstable |= bad_density(rho);
 #pragma unroll
             for (int i = 0; i < 9; ++i) st1_sweep(dst + (a + i * plane), s[i]);
@@ -326,34 +367,59 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = 4; };
 template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
-// Dense job order: warp w takes jobs w, w + W, w + 2W, ... (W warps in the grid),
-// so the warps resident at any moment sweep one compact window of each plane;
-// measured on B300 this beats one contiguous job range per warp by ~10% of HBM.
+// Jobs in ascending order, taken kScChunk at a time by each warp from a counter in
+// global memory (the next chunk is claimed before the current one is swept, so the
+// atomic's latency overlaps the sweep), so the warps resident at any moment sweep one
+// compact window of each plane (measured on B300: ~10% of HBM over one contiguous job
+// range per warp) and CTAs that start late -- their SM busy with the IB stage --
+// simply take fewer chunks.
+constexpr int kScChunk = 2;
 template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
+    if (L.pdl & PDL_TRIGGER) pdl_trigger();
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
-    int nseg = 1;
-    for (long long job = gw; job < jobs; job += nw) {
-        if (job >= c_hi || job < c_lo) {
-            int lo = 0, hi = L.ncases - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+    int nseg = 1, cur = -1;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(L.ctr, (unsigned long long)kScChunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    while ((long long)base < jobs) {
+        unsigned long long next = 0;
+        if (lane == 0) next = atomicAdd(L.ctr, (unsigned long long)kScChunk);
+        const long long jend = min((long long)base + kScChunk, jobs);
+        for (long long job = (long long)base; job < jend; ++job) {
+            if (L.phase == SC_LIST) {
+                const int4 e = L.list[job];
+                if (e.x != cur) {
+                    K.load(L.cases[e.x]);
+                    cur = e.x;
+                }
+                sc_row_scalar<S, KIND, NPT>(K, e.y, e.z, lane);
+                continue;
             }
-            c_lo = L.job_off[lo];
-            c_hi = L.job_off[lo + 1];
-            K.load(L.cases[lo]);
-            nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
+            if (job >= c_hi || job < c_lo) {
+                int lo = 0, hi = L.ncases - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+                }
+                c_lo = L.job_off[lo];
+                c_hi = L.job_off[lo + 1];
+                K.load(L.cases[lo]);
+                nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
+            }
+            const int local = (int)(job - c_lo);   // < ny * nseg
+            const int y = local / nseg;
+            const int xseg = (local - y * nseg) * 32 * NPT;
+            if (L.phase == SC_SKIP_IB && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
+            sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
         }
-        const int local = (int)(job - c_lo);   // < ny * nseg
-        const int y = local / nseg;
-        sc_row_scalar<S, KIND, NPT>(K, y, (local - y * nseg) * 32 * NPT, lane);
+        base = __shfl_sync(0xffffffffu, next, 0);
     }
+    if (L.pdl & PDL_DEPENDENT) pdl_wait();
+    release_job_counter(L.ctr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1379,8 +1445,14 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
     }
 }
 
+__device__ void body_prepare(BodyDev& B, double* sh);
+__device__ void body_finish(BodyDev& B);
+
+// One CTA per body.  Mode 0 (a step): body motion (body_prepare), the IB stage, then the
+// end-of-step body update (body_finish); mode 1: footprint and omega_MDF only.
 template <class S>
 __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
+    if (L.pdl & PDL_TRIGGER) pdl_trigger();
     const BodyRef ref = L.refs[blockIdx.x];
     using R = typename Traits<S>::R;
     static_assert(kIbThreads == 512, "IbSmem sizes sF for 512 markers");
@@ -1393,49 +1465,29 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     R* sQc = sEw + kMdfEntryCap;
     int* sEk = reinterpret_cast<int*>(sQc + kMdfNodeCap);
     int* sQo = sEk + kMdfEntryCap;
-    if (ref.b->nfp < 0) return;
+    if (L.mode == 0) body_prepare(*ref.b, shd);
     if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
     else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
+    if (L.mode == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) body_finish(*ref.b);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
-// Body motion at the start of a step (mode PREPARE): first half of Eq. 23 with
-// F_total^n = F_h^n + F_g + dF_IM^n and the torque-only rotation (FREE), x_c(t)
-// at t = n + 1 (PRESCRIBED), then marker positions and U_d = v + omega x (X - X_c).
-// A FIXED body whose desired velocity was set per marker keeps it.
-// At the end of a step (mode FINISH): second half of Eq. 23 and Eq. A3 (FREE),
-// the body and case step counters.
-__global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
+// Rigid-body motion around the IB stage of a step, run by the body's IB CTA.
+// body_prepare (before the IB stage): first half of Eq. 23 with F_total^n = F_h^n + F_g +
+// dF_IM^n and the torque-only rotation (FREE), x_c(t) at t = n + 1 (PRESCRIBED), then marker
+// positions and U_d = v + omega x (X - X_c); a FIXED body whose desired velocity was set per
+// marker keeps it.  body_finish (after it, one thread): second half of Eq. 23 with the force
+// just computed and Eq. A3 (FREE), and the body's step counter.
+__device__ void body_prepare(BodyDev& B, double* sh) {
     const double PI = 3.14159265358979323846;
-    if ((int)blockIdx.x >= L.nrefs) {
-        if (mode == 1 && threadIdx.x == 0) L.cases[blockIdx.x - L.nrefs]->step += 1ull;
-        return;
-    }
-    BodyDev& B = *L.refs[blockIdx.x].b;
     BodyState& S = B.st;
     const double r2 = B.radius * B.radius;
     const double ms = B.rho_ratio * PI * r2, Is = 0.5 * ms * r2;
-    const double dm = (B.rho_ratio - 1.0) * PI * r2, mf = PI * r2;
-    if (mode == 1) {
-        if (threadIdx.x == 0) {
-            if (B.motion == MOT_FREE) {
-                const double vnx = S.vhx + (S.Fhx + dm * B.gx + S.dFimx) / (2.0 * ms);
-                const double vny = S.vhy + (S.Fhy + dm * B.gy + S.dFimy) / (2.0 * ms);
-                const double omn = S.omh + S.Th / (2.0 * Is);
-                if (B.internal_mass) {
-                    S.dFimx = mf * (vnx - S.vx);
-                    S.dFimy = mf * (vny - S.vy);
-                } else {
-                    S.dFimx = 0.0;
-                    S.dFimy = 0.0;
-                }
-                S.vx = vnx; S.vy = vny; S.om = omn;
-            }
-            S.nstep = S.nstep + 1;
-        }
-        return;
-    }
-    __shared__ double sh[8];
+    const double dm = (B.rho_ratio - 1.0) * PI * r2;
+    __syncthreads();   // sh may still be read by earlier code of the CTA
     if (threadIdx.x == 0) {
         double vx = S.vx, vy = S.vy, om = S.om;
         if (B.motion == MOT_FREE) {
@@ -1460,7 +1512,7 @@ __global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
     }
     __syncthreads();
     const double xc = sh[0], yc = sh[1], vx = sh[2], vy = sh[3], om = sh[4], ct = sh[5], st = sh[6];
-    for (int k = threadIdx.x; k < B.n; k += kThreads) {
+    for (int k = threadIdx.x; k < B.n; k += blockDim.x) {
         double rx, ry;
         if (B.motion == MOT_FREE) {
             rx = ct * B.r0x[k] - st * B.r0y[k];
@@ -1480,10 +1532,38 @@ __global__ void __launch_bounds__(kThreads) body_kernel(FinLaunch L, int mode) {
         B.Udx[k] = vx - om * ry;
         B.Udy[k] = vy + om * rx;
     }
+    __syncthreads();
 }
 
-// ------------------------------------------------------------------------------------------
-// Export / import / initial state / macro fields.
+__device__ void body_finish(BodyDev& B) {
+    const double PI = 3.14159265358979323846;
+    BodyState& S = B.st;
+    if (B.motion == MOT_FREE) {
+        const double r2 = B.radius * B.radius;
+        const double ms = B.rho_ratio * PI * r2, Is = 0.5 * ms * r2;
+        const double dm = (B.rho_ratio - 1.0) * PI * r2, mf = PI * r2;
+        const double vnx = S.vhx + (S.Fhx + dm * B.gx + S.dFimx) / (2.0 * ms);
+        const double vny = S.vhy + (S.Fhy + dm * B.gy + S.dFimy) / (2.0 * ms);
+        const double omn = S.omh + S.Th / (2.0 * Is);
+        if (B.internal_mass) {
+            S.dFimx = mf * (vnx - S.vx);
+            S.dFimy = mf * (vny - S.vy);
+        } else {
+            S.dFimx = 0.0;
+            S.dFimy = 0.0;
+        }
+        S.vx = vnx; S.vy = vny; S.om = omn;
+    }
+    S.nstep = S.nstep + 1;
+}
+
+// Step counters of every case: the last launch of a step (the sweep reads the
+// counter's parity to pick its source buffer).
+__global__ void __launch_bounds__(kThreads) counter_kernel(CaseDev** cases, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cases[i]->step += 1ull;
+}
+
 template <class S>
 __global__ void export_kernel(const CaseDev* __restrict__ Cp, double* out, int shifted) {
     using R = typename Traits<S>::R;
@@ -1736,8 +1816,9 @@ static int grid_for(long long work) {
 template <class S, int KIND>
 static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
     const int block = L.block > 0 ? L.block : kThreads;
-    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1>), grid, block, st, L, jobs);
-    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2>), grid, block, st, L, jobs);
+    const bool dep = (L.pdl & PDL_DEPENDENT) != 0;
+    if (variant == SC_SCALAR) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1>), grid, block, st, dep, L, jobs);
+    else if (variant == SC_SCALAR2) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2>), grid, block, st, dep, L, jobs);
     else if (variant == SC_BULK) {
         static const cudaError_t attr =
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
@@ -1852,10 +1933,9 @@ cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st) {
-    const int g = L.nrefs + (mode == 1 ? L.ncases : 0);
-    if (g <= 0) return cudaSuccess;
-    IBLBM_LAUNCH(body_kernel, g, kThreads, st, L, mode);
+cudaError_t launch_counters(CaseDev** cases, int ncases, cudaStream_t st) {
+    if (ncases <= 0) return cudaSuccess;
+    IBLBM_LAUNCH(counter_kernel, (ncases + kThreads - 1) / kThreads, kThreads, st, cases, ncases);
     return cudaGetLastError();
 }
 

@@ -16,24 +16,37 @@ struct BodyRef {
 // One stream-collide launch over many cases of one storage type.  Work unit:
 // one warp handles one row segment of 32*V nodes of one case; job_off[c] is
 // the first job of case c (prefix sum, ncases + 1 entries).
+// Phases of a scalar-variant launch: every interior node (SC_ALL); every interior
+// node outside the IB regions (SC_SKIP_IB, swept while the IB stage runs); the IB
+// regions as an explicit segment list (SC_LIST).  The IB region of a body is its
+// footprint box's rows, widened in x to multiples of kIbAlign nodes, so that every
+// 32- or 64-node segment lies wholly inside or wholly outside it.
+enum { SC_ALL = 0, SC_SKIP_IB = 1, SC_LIST = 2 };
+constexpr int kIbAlign = 64;
+// Programmatic dependent launch: PDL_TRIGGER, the kernel lets the next launch of its
+// stream begin as soon as all its CTAs run; PDL_DEPENDENT, the launch may begin before
+// the previous one ends and waits for it (griddepcontrol.wait) before it exits.
+enum { PDL_TRIGGER = 1, PDL_DEPENDENT = 2 };
+
 struct ScLaunch {
     CaseDev** cases;
     long long* job_off;
     int ncases;
     int block;   // threads per CTA for the scalar variants (0: kThreads)
+    // Scalar variants take jobs in chunks from ctr[0]; ctr[1] counts finished CTAs and
+    // the last CTA resets both, so each launch starts from zero.
+    unsigned long long* ctr;
+    const int4* list;   // SC_LIST: segment (x = index into cases, y = row, z = first node)
+    int phase;          // SC_ALL, SC_SKIP_IB or SC_LIST
+    int pdl;            // PDL_* flags
 };
 
 struct IbLaunch {
     BodyRef* refs;
     int nrefs;
-    int mode;       // 0: full IB stage; 1: set-up only (footprint and omega_MDF at the initial markers)
-};
-
-struct FinLaunch {
-    BodyRef* refs;
-    int nrefs;
-    int ncases;
-    CaseDev** cases;
+    int mode;       // 0: body motion + IB stage + end-of-step body update; 1: set-up only
+                    // (footprint and omega_MDF at the initial markers)
+    int pdl;        // PDL_* flags (PDL_TRIGGER only)
 };
 
 // host-side launchers (kernels.cu)
@@ -44,6 +57,14 @@ struct FinLaunch {
 enum { SC_VECTOR = 0, SC_SCALAR = 1, SC_SCALAR2 = 2, SC_BULK = 3, SC_VARIANTS = 4 };
 cudaError_t launch_stream_collide(int storage, int collision, int variant, const ScLaunch& L, long long jobs,
                                   int grid, cudaStream_t st);
+// true when the variant honours ScLaunch.ctr / phase / list (the scalar variants)
+inline bool sc_variant_phased(int variant) { return variant == SC_SCALAR || variant == SC_SCALAR2; }
+// IB region test shared by the SC_SKIP_IB launch and the host that builds the SC_LIST table.
+__host__ __device__ inline bool in_ib_region(int y, int xseg, int bx0, int by0, int bw, int bh) {
+    const int ax0 = (bx0 >= 0 ? bx0 / kIbAlign : -((-bx0 + kIbAlign - 1) / kIbAlign)) * kIbAlign;
+    const int ax1 = ((bx0 + bw + kIbAlign - 1) / kIbAlign) * kIbAlign;
+    return y >= by0 && y < by0 + bh && xseg >= ax0 && xseg < ax1;
+}
 int sc_segment(int storage, int variant);
 bool sc_variant_ok(int variant, const void* f0, const void* f1);   // alignment a variant needs
 // Lattice-edge nodes: chunk k covers edge nodes [first, end) of case c (at most
@@ -62,7 +83,8 @@ struct EdgeLaunch {
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
-cudaError_t launch_body(const FinLaunch& L, int mode, cudaStream_t st);   // 0 prepare, 1 finish
+// advances the step counter of every case (the last launch of a step)
+cudaError_t launch_counters(CaseDev** cases, int ncases, cudaStream_t st);
 cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st);
 cudaError_t launch_import(const CaseDev* hc, CaseDev* dc, const double* in, cudaStream_t st);
 cudaError_t launch_fill_equilibrium(const CaseDev* hc, CaseDev* dc, double rho, double ux, double uy, cudaStream_t st);

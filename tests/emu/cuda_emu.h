@@ -92,10 +92,18 @@ inline T __shfl_xor_sync(unsigned, T v, int mask) {
     const int lane = (int)(threadIdx.x & 31u);
     return emu_from_bits<T>(emu::exchange(emu_to_bits(v), lane ^ mask));
 }
+template <class T>
+inline T __shfl_sync(unsigned, T v, int src) {
+    return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src & 31));
+}
 inline int __any_sync(unsigned, int pred) { return emu::any(pred); }
 inline void __syncwarp(unsigned = 0xffffffffu) { emu::any(0); }
 
 inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
+    return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST);
+}
+inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline unsigned atomicOr(unsigned* p, unsigned v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
 
 using std::max;
@@ -106,3 +114,5 @@ using std::min;
 #define IBLBM_LAUNCH_SMEM(kern, grid, block, smem, stream, ...) \
     emu::launch(dim3(grid), dim3(block), [=]() { kern(__VA_ARGS__); }, (stream))
 #define IBLBM_DYNAMIC_SMEM(name) unsigned char* name = emu::dyn_smem()
+#define IBLBM_LAUNCH_PDL(kern, grid, block, stream, dependent, ...) \
+    emu::launch(dim3(grid), dim3(block), [=]() { kern(__VA_ARGS__); }, (stream))
