@@ -81,6 +81,7 @@ def lib():
             "orc_mdf_iterations": (i, [vp, i]),
             "orc_mdf_omega": (d, [vp, i]),
             "orc_mdf_residual": (d, [vp, i]),
+            "orc_mdf_omega_end": (d, [vp, i]),
             "orc_phi": (d, [i, d]),
             "orc_feq": (None, [d, d, d, pd]),
             "orc_guo": (None, [d, d, d, d, d, pd]),
@@ -276,6 +277,9 @@ class Case:
 
     def mdf_residual(self, b: int) -> float:
         return lib().orc_mdf_residual(self._h, b)
+
+    def mdf_omega_end(self, b: int) -> float:
+        return lib().orc_mdf_omega_end(self._h, b)
 
     def set_marker_velocity(self, b: int, ud=None) -> None:
         if ud is None:

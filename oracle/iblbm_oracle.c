@@ -26,6 +26,7 @@ static const double PI = 3.14159265358979323846;
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 
 #define ORC_ERR_MARKER_OUT_OF_DOMAIN (-4)
+#define ORC_MAX_COUPLED 64   /* MDF bodies of one lattice iterated together */
 
 typedef struct {
     int n, kernel, scheme;
@@ -45,6 +46,7 @@ typedef struct {
     double mdf_omega;
     int mdf_iters;
     double mdf_res;
+    double mdf_omega_end;   /* coupled path: relaxation in use when the iteration ended */
     double* hist;
     int hist_n, hist_cap;
 } orc_body;
@@ -686,6 +688,115 @@ static void ib_mdf(orc_case* c, orc_body* B) {
     free(rk); free(Fnx); free(Fny); free(sx); free(sy);
 }
 
+/* Residual of Eq. 12-13 at every marker of the coupled bodies for the iterate (ux, uy):
+ * r = max_k |U_d,k - U(X_k)|_2 over all of them, and F = 2 rho_k (U_d,k - U(X_k)). */
+static double coupled_residual(orc_case* c, orc_body** Bs, int nb, const double* ux, const double* uy,
+                               double** rk, double** Fx, double** Fy) {
+    double r = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        orc_body* B = Bs[b];
+        for (int k = 0; k < B->n; ++k) {
+            double Ux = interp_one(B->kernel, c->nx, ux, B->X[k], B->Y[k]);
+            double Uy = interp_one(B->kernel, c->nx, uy, B->X[k], B->Y[k]);
+            double dx = B->Udx[k] - Ux, dy = B->Udy[k] - Uy;
+            double e = sqrt(dx * dx + dy * dy);
+            if (e > r) r = e;
+            Fx[b][k] = 2.0 * rk[b][k] * dx;
+            Fy[b][k] = 2.0 * rk[b][k] * dy;
+        }
+    }
+    return r;
+}
+
+/* Sec. 2.5.2, coupled path (two or more MDF bodies in one lattice): the bodies' marker
+ * forces share one fluid update per iteration, u^(n) = u^(n-1) + omega/(2 rho) sum_b
+ * spread_b(F_b^(n)), and one L_inf residual over all their markers decides.  The
+ * relaxation starts at omega_0 = min(0.8, omega_MDF of every body); a trial iteration
+ * whose residual exceeds 1.2 times the residual of the iterate it started from is
+ * rejected (the iterate is kept) and omega halved, and the iteration ends once omega
+ * has come down to 0.125 omega_0.  Readings: every trial counts as one of the N_max
+ * iterations; at least N_min accepted increments come before the tolerance may stop
+ * the loop; N_min, N_max and tol are those of the first MDF body. */
+static void ib_mdf_coupled(orc_case* c, orc_body** Bs, int nb) {
+    size_t N = (size_t)c->nx * c->ny;
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* tx = (double*)malloc(sizeof(double) * N);
+    double* ty = (double*)malloc(sizeof(double) * N);
+    double* sx = (double*)malloc(sizeof(double) * N);
+    double* sy = (double*)malloc(sizeof(double) * N);
+    memcpy(ux, c->uxr, sizeof(double) * N);   /* u^(0): post-streaming velocity */
+    memcpy(uy, c->uyr, sizeof(double) * N);
+    double *rk[ORC_MAX_COUPLED], *Fx[ORC_MAX_COUPLED], *Fy[ORC_MAX_COUPLED], *Gx[ORC_MAX_COUPLED],
+        *Gy[ORC_MAX_COUPLED];
+    double om0 = 0.8;
+    for (int b = 0; b < nb; ++b) {
+        orc_body* B = Bs[b];
+        rk[b] = (double*)malloc(sizeof(double) * B->n);
+        Fx[b] = (double*)malloc(sizeof(double) * B->n);
+        Fy[b] = (double*)malloc(sizeof(double) * B->n);
+        Gx[b] = (double*)malloc(sizeof(double) * B->n);
+        Gy[b] = (double*)malloc(sizeof(double) * B->n);
+        for (int k = 0; k < B->n; ++k) {
+            rk[b][k] = interp_one(B->kernel, c->nx, c->rho, B->X[k], B->Y[k]);
+            B->Fx[k] = 0.0;
+            B->Fy[k] = 0.0;
+        }
+        if (B->mdf_omega < om0) om0 = B->mdf_omega;
+    }
+    const int nmin = Bs[0]->p.mdf_nmin, nmax = Bs[0]->p.mdf_nmax;
+    const double tol = Bs[0]->p.mdf_tol;
+    double om = om0;
+    double ra = coupled_residual(c, Bs, nb, ux, uy, rk, Fx, Fy);
+    int applied = 0, trials = 0;
+    for (;;) {
+        if (applied >= nmin && ra < tol) break;
+        if (trials >= nmax) break;
+        /* trial iterate from the accepted one (Eq. 14 with the shared update) */
+        memset(sx, 0, sizeof(double) * N);
+        memset(sy, 0, sizeof(double) * N);
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < Bs[b]->n; ++k) {
+                spread_one(Bs[b]->kernel, c->nx, sx, Fx[b][k], Bs[b]->X[k], Bs[b]->Y[k], Bs[b]->ds);
+                spread_one(Bs[b]->kernel, c->nx, sy, Fy[b][k], Bs[b]->X[k], Bs[b]->Y[k], Bs[b]->ds);
+            }
+        for (size_t q = 0; q < N; ++q) {
+            tx[q] = ux[q] + om / (2.0 * c->rho[q]) * sx[q];
+            ty[q] = uy[q] + om / (2.0 * c->rho[q]) * sy[q];
+        }
+        ++trials;
+        double rt = coupled_residual(c, Bs, nb, tx, ty, rk, Gx, Gy);
+        if (rt > 1.2 * ra) {          /* rejected: keep the iterate, halve the relaxation */
+            om *= 0.5;
+            if (om <= 0.125 * om0) break;
+            continue;
+        }
+        for (int b = 0; b < nb; ++b)  /* accepted */
+            for (int k = 0; k < Bs[b]->n; ++k) {
+                Bs[b]->Fx[k] += om * Fx[b][k];
+                Bs[b]->Fy[k] += om * Fy[b][k];
+                Fx[b][k] = Gx[b][k];
+                Fy[b][k] = Gy[b][k];
+            }
+        memcpy(ux, tx, sizeof(double) * N);
+        memcpy(uy, ty, sizeof(double) * N);
+        ra = rt;
+        ++applied;
+    }
+    for (int b = 0; b < nb; ++b) {
+        orc_body* B = Bs[b];
+        B->mdf_iters = trials;
+        B->mdf_res = ra;
+        B->mdf_omega_end = om;
+        for (int k = 0; k < B->n; ++k) {
+            spread_one(B->kernel, c->nx, c->Fx, B->Fx[k], B->X[k], B->Y[k], B->ds);
+            spread_one(B->kernel, c->nx, c->Fy, B->Fy[k], B->X[k], B->Y[k], B->ds);
+        }
+        free(rk[b]); free(Fx[b]); free(Fy[b]); free(Gx[b]); free(Gy[b]);
+    }
+    free(ux); free(uy); free(tx); free(ty); free(sx); free(sy);
+}
+
 /* Eq. 17 across every DFC marker of the case: W_total sums over all of them. */
 static void dfc_lambdas(orc_case* c) {
     size_t N = (size_t)c->nx * c->ny;
@@ -778,12 +889,17 @@ static int step_once(orc_case* c) {
     int any_dfc = 0;
     for (int b = 0; b < c->nbodies; ++b) any_dfc |= (c->bodies[b].scheme == ORC_DFC);
     if (any_dfc) dfc_lambdas(c);
+    orc_body* coupled[ORC_MAX_COUPLED];
+    int nmdf = 0;
+    for (int b = 0; b < c->nbodies; ++b)
+        if (c->bodies[b].scheme == ORC_MDF && nmdf < ORC_MAX_COUPLED) coupled[nmdf++] = &c->bodies[b];
     for (int b = 0; b < c->nbodies; ++b) {
         orc_body* B = &c->bodies[b];
         if (B->scheme == ORC_DF) ib_df(c, B);
-        else if (B->scheme == ORC_MDF) ib_mdf(c, B);
+        else if (B->scheme == ORC_MDF) { if (nmdf == 1) ib_mdf(c, B); }
         else ib_dfc(c, B);
     }
+    if (nmdf >= 2) ib_mdf_coupled(c, coupled, nmdf);
     double v[9];
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -857,6 +973,7 @@ void orc_marker_stencils(const orc_case* c, int b, int* ij) {
 int orc_mdf_iterations(const orc_case* c, int b) { return c->bodies[b].mdf_iters; }
 double orc_mdf_omega(const orc_case* c, int b) { return c->bodies[b].mdf_omega; }
 double orc_mdf_residual(const orc_case* c, int b) { return c->bodies[b].mdf_res; }
+double orc_mdf_omega_end(const orc_case* c, int b) { return c->bodies[b].mdf_omega_end; }
 
 /* ---- Sec. 2.8 local diagnostics ------------------------------------------------
  * Readings (the paper names the three metrics and their normalisations only):

@@ -75,6 +75,9 @@ void      orc_marker_stencils(const orc_case* c, int b, int* ij);
 int       orc_mdf_iterations(const orc_case* c, int b);
 double    orc_mdf_omega(const orc_case* c, int b);
 double    orc_mdf_residual(const orc_case* c, int b);
+/* coupled MDF path (two or more MDF bodies): relaxation factor when the last step's
+ * iteration ended (omega_0 = min(0.8, omega_MDF of the bodies), halved per rejection) */
+double    orc_mdf_omega_end(const orc_case* c, int b);
 
 /* Fixed bodies: desired velocity of every marker (ud[2*n]) from the next step on,
  * or NULL for U_d = 0.  Returns 0, or 1 for a bad index or a moving body. */

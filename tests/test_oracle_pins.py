@@ -856,3 +856,116 @@ def test_cmmrt_forcing_moments_gauss_hermite():
     keq, R = _maxwellian_central_moments(rho, Fx / rho, Fy / rho)
     assert R[6] == pytest.approx(CS2 * Fy, rel=1e-12) and R[7] == pytest.approx(CS2 * Fx, rel=1e-12)
     np.testing.assert_allclose(k, keq + 0.5 * R, rtol=0, atol=4e-15)
+
+
+# ---------------------------------------------------------------- coupled two-particle MDF
+def _coupled_dense_sequence(Ds, dss, omegas, e0, nmin, nmax, tol):
+    """Sec. 2.5.2 coupled path on a frozen uniform field (rho = 1), in marker space: the
+    marker slip obeys e <- (I - omega A) e with the joint A = D D^T diag(ds) over both
+    bodies' markers (dense, brute force); omega_0 = min(0.8, omega of each body); a trial
+    whose max-norm residual exceeds 1.2 times the current one is rejected and omega
+    halved, down to 0.125 omega_0; accepted trials add omega * 2 e to F_total.  Returns
+    (F_total, iterations tried, final residual, final omega, omegas of the trials)."""
+    D = np.vstack(Ds)
+    ds = np.concatenate([np.full(len(d), s) for d, s in zip(Ds, dss)])
+    A = D @ D.T * ds[None, :]
+    om0 = min([0.8] + list(omegas))
+    om = om0
+    e = e0.copy()
+
+    def res(v):
+        return np.sqrt((v ** 2).sum(axis=1)).max()
+
+    ra, Ft, applied, tried, oms = res(e), np.zeros_like(e), 0, 0, []
+    while not (applied >= nmin and ra < tol) and tried < nmax:
+        et = e - om * (A @ e)
+        tried += 1
+        oms.append(om)
+        rt = res(et)
+        if rt > 1.2 * ra:
+            om *= 0.5
+            if om <= 0.125 * om0:
+                break
+            continue
+        Ft += om * 2.0 * e
+        e, ra = et, rt
+        applied += 1
+    return Ft, tried, ra, om, oms
+
+
+def _coupled_case(kernels, centers, D, nm, dsfac=1.0, omega=0.0, u=(0.04, 0.015), nx=48, ny=40):
+    c = _periodic_case(nx, ny, u=u)
+    Ds, dss = [], []
+    for k, (xc, yc) in zip(kernels, centers):
+        xy, ds = W.circle_markers(xc, yc, D, nm)
+        ds *= dsfac
+        c.add_body(xy, ds, k, W.MDF, _body(xy, ds, k, W.MDF, xc, yc, D / 2, mdf_nmin=5, mdf_nmax=20,
+                                           mdf_tol=1e-4, mdf_omega=omega))
+        Ds.append(_dense_D(k, xy, nx, ny))
+        dss.append(ds)
+    return c, Ds, dss
+
+
+@pytest.mark.parametrize("kernels", [(W.HAT, W.HAT), (W.PESKIN4, W.HAT)])
+def test_mdf_coupled_shared_update_matches_dense(kernels):
+    """Two MDF disks whose footprints overlap, on a uniform stream: the coupled iteration
+    shares one fluid update, so the cross terms of the joint A act, and omega_0 is capped
+    at 0.8 (each body alone would take 1/||A_b||_inf > 0.8 here).  The marker forces,
+    iteration count, residual and relaxation follow the dense marker-space sequence."""
+    u = np.array([0.04, 0.015])
+    c, Ds, dss = _coupled_case(kernels, [(17.3, 19.6), (26.4, 20.4)], 9.0, 28, u=tuple(u))
+    c.step(1)
+    om_b = [c.mdf_omega(b) for b in range(2)]
+    for b in range(2):   # omega_MDF of each body alone: 1 / ||A_b||_inf by brute force
+        Ab = Ds[b] @ Ds[b].T * dss[b]
+        assert om_b[b] == pytest.approx(1.0 / np.abs(Ab).sum(axis=1).max(), rel=1e-13)
+    assert min(om_b) > 0.8
+    D = np.vstack(Ds)
+    assert np.abs(Ds[0] @ Ds[1].T).max() > 0.05          # the footprints overlap
+    e0 = np.tile(-u, (len(D), 1))
+    Ft, tried, ra, om, _ = _coupled_dense_sequence(Ds, dss, om_b, e0, 5, 20, 1e-4)
+    got = np.vstack([c.marker_data(b)[:, 4:6] for b in range(2)])
+    np.testing.assert_allclose(got, Ft, rtol=1e-11, atol=1e-15)
+    for b in range(2):
+        assert c.mdf_iterations(b) == tried
+        assert c.mdf_residual(b) == pytest.approx(ra, rel=1e-10)
+        assert c.mdf_omega_end(b) == om == 0.8
+
+
+@pytest.mark.parametrize("dsfac,rejections,terminated", [(6.0, 1, False), (14.0, 2, False), (27.0, 3, True)])
+def test_mdf_coupled_rejection_and_halving(dsfac, rejections, terminated):
+    """The 20 % guard of the coupled path.  Arc lengths scaled up make omega A large
+    enough that the first trials grow the residual: by 31 % with ds x 6 (rejected by the
+    20 % guard, though a 50 % guard would accept it), several-fold with ds x 14 (two
+    rejections) and with ds x 27 (three rejections: omega reaches 0.125 omega_0 and the
+    iteration ends with no force).  Forces, iteration counts and final omega follow the
+    dense sequence."""
+    u = np.array([0.04, 0.015])
+    c, Ds, dss = _coupled_case((W.PESKIN4, W.PESKIN4), [(17.3, 19.6), (27.9, 20.4)], 9.0, 45,
+                               dsfac=dsfac, omega=5.0, u=tuple(u))
+    c.step(1)
+    e0 = np.tile(-u, (sum(len(d) for d in Ds), 1))
+    Ft, tried, ra, om, oms = _coupled_dense_sequence(Ds, dss, [5.0, 5.0], e0, 5, 20, 1e-4)
+    assert om == pytest.approx(0.8 * 0.5 ** rejections)
+    assert (tried == 3) == terminated
+    got = np.vstack([c.marker_data(b)[:, 4:6] for b in range(2)])
+    np.testing.assert_allclose(got, Ft, rtol=1e-11, atol=1e-15)
+    if terminated:
+        assert np.abs(got).max() == 0.0
+    for b in range(2):
+        assert c.mdf_iterations(b) == tried
+        assert c.mdf_omega_end(b) == pytest.approx(om, rel=0, abs=0)
+        assert c.mdf_residual(b) == pytest.approx(ra, rel=1e-10)
+
+
+def test_mdf_coupled_momentum_exchange():
+    """Newton's third law with two coupled MDF bodies (Sec. 2.7): the fluid momentum
+    gained in one step is minus the sum of the forces on the two bodies."""
+    c, _, _ = _coupled_case((W.PESKIN4, W.HAT), [(17.3, 19.6), (26.4, 20.4)], 9.0, 28)
+    c.step(2)
+    f0 = c.populations()
+    c.step(1)
+    f1 = c.populations()
+    Fb = c.body_forces(0)[:2] + c.body_forces(1)[:2]
+    np.testing.assert_allclose(_momentum(f1) - _momentum(f0), -Fb, rtol=1e-11, atol=1e-15)
+    assert f1.sum() == pytest.approx(f0.sum(), rel=1e-15)
