@@ -88,17 +88,18 @@ def sweep_traffic(L, specs):
 def launches_per_step(specs, L=None) -> int:
     """Kernel launches of one batched step: one IB launch per storage type with bodies
     (body motion folded in), one stream-collide launch per (storage, collision) group,
-    and -- when every body is fixed and the tuned sweeps are the one- or two-node-per-lane
-    kernels, so the IB stage overlaps the sweep -- one launch per group with bodies for
-    the IB-region segments; then one lattice-edge launch per storage type and the
-    step-counter launch."""
+    and -- when at most eight bodies, all fixed, of one storage type and the tuned sweeps
+    are the one- or two-node-per-lane kernels, so the IB stage overlaps the sweep -- one
+    launch per group with bodies for the IB-region segments; then one lattice-edge launch
+    per storage type and the step-counter launch."""
     storages = {s.storage for s in specs}
     with_bodies = {s.storage for s in specs if s.bodies}
     groups = {(s.storage, s.collision) for s in specs}
     n = len(with_bodies) + len(groups) + len(storages) + 1
     fixed = all(b.motion == W.FIXED for s in specs for b in s.bodies)
     phased = L is None or all(L.kernel_variant(st, col)[0] in (1, 2) for st, col in groups)
-    if with_bodies and fixed and phased:
+    nbodies = sum(len(s.bodies) for s in specs)
+    if len(with_bodies) == 1 and 0 < nbodies <= 8 and fixed and phased:
         n += len({(s.storage, s.collision) for s in specs if s.bodies})
     return n
 
@@ -190,7 +191,7 @@ class ClockSampler:
 def cpu_baseline(spec, budget_s: float = 15.0):
     """The FP64 oracle as it stands, single thread, on a bounded number of steps
     of one lattice of the workload; returns (MLUPS, steps, seconds)."""
-    import oracle
+    import oracle  # noqa: F401
     from tests.harness import oracle_case
     c = oracle_case(spec)
     t0 = time.perf_counter()
@@ -201,6 +202,42 @@ def cpu_baseline(spec, budget_s: float = 15.0):
     c.step(n)
     dt = time.perf_counter() - t0
     return spec.nodes * n / dt / 1e6, n, dt
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baselines(budget_s: float):
+    """The oracle timed in fresh processes (no GPU context, no other threads of this
+    program): one thread, then the all-cores build (OpenMP over its node loops) with
+    one thread per core; (single, all_cores) dicts of MLUPS, steps, seconds, threads."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads as W; "
+            "spec = W.fixed_cylinder_2048(re=100.0, storage=W.F64, collision=W.BGK, kernel=W.HAT, scheme=W.DF); "
+            "print(json.dumps(bench.cpu_baseline(spec, %r)))" % (ROOT, budget_s))
+    cores = os.cpu_count() or 1
+    out = []
+    for omp in (False, True):
+        env = dict(os.environ)
+        env.pop("IBLBM_ORACLE_OPENMP", None)
+        if omp:
+            env["IBLBM_ORACLE_OPENMP"] = "1"
+            env["OMP_NUM_THREADS"] = str(cores)
+            env["OMP_PROC_BIND"] = "spread"
+        else:
+            env["OMP_NUM_THREADS"] = "1"
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            raise RuntimeError("oracle baseline failed: " + r.stderr[-500:])
+        mlups, n, dt = json.loads(r.stdout.strip().splitlines()[-1])
+        out.append({"mlups": mlups, "steps": n, "seconds": dt, "threads": cores if omp else 1})
+    return out[0], out[1]
 
 
 def _pct(xs, q):
@@ -220,8 +257,9 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
     _, specs, resampled = W.serving_requests(seed=seed, n=n_requests, rate=1.0, steps=steps, grids=grids)
     budget = int(budget_gb * 1e9)
 
-    def run_server(arrivals):
+    def run_server(arrivals, graphs=True):
         srv = L.Server(budget, max_slots=128)
+        srv.set_graphs(graphs)
         t0 = time.perf_counter()
         pending = list(zip(arrivals, specs))
         ids = []
@@ -253,8 +291,11 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
 
     cap = run_server([0.0] * len(specs))
     rate_cap = cap["cases_per_s"]
+    cap_direct = run_server([0.0] * len(specs), graphs=False)
     out = {"requests": len(specs), "steps_per_request": steps, "tau_resampled": resampled,
-           "budget_gb": budget_gb, "tick_steps": tick, "capacity": cap}
+           "budget_gb": budget_gb, "tick_steps": tick, "capacity": cap,
+           "capacity_launch_by_launch": cap_direct,
+           "updates_per_s_capacity": sum(sp.nodes for sp in specs) * steps / cap["wall_s"]}
     rng = np.random.default_rng(seed + 1)
     gaps = rng.exponential(1.0, size=len(specs))
     for frac in (0.5, 0.9):
@@ -311,7 +352,7 @@ def storage_report(L, torch, steps=20):
     return out
 
 
-def single_case_report(L, torch, steps=2000):
+def single_case_report(L, torch, steps=2000, only_large=False):
     """One lattice stepped alone (graph-replayed iblbm_step): the 200x100 Re=20
     cylinder (DF, hat, BGK) in FP64 and FP32, and one 2048x1024 lattice of the
     matrix (DF, Peskin, BGK, FP32).  Small lattices are latency-bound, so these
@@ -322,6 +363,8 @@ def single_case_report(L, torch, steps=2000):
              ("cyl-re20-200x100-f32", W.fixed_cylinder_re20(storage=W.F32), steps),
              ("cyl-re100-2048x1024-f32", W.fixed_cylinder_2048(re=100.0, storage=W.F32, collision=W.BGK,
                                                                kernel=W.PESKIN4, scheme=W.DF), steps // 4)]
+    if only_large:
+        cases = cases[-1:]
     for name, spec, n in cases:
         lat = L.Lattice.from_spec(spec)
         lat.step(20)
@@ -383,7 +426,7 @@ def run_reference(args, specs):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": workload_config(specs),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
                              "sample": "each step = %.1f s of FP64 oracle steps on one %dx%d lattice of the "
                                        "matrix (%s), scaled to lattice updates per second"
                                        % (args.ref_budget, spec.nx, spec.ny, spec.name)},
@@ -409,6 +452,8 @@ def main():
                     help="lattice chunks of the end-to-end leg (copy-in of one overlaps the steps of the last)")
     ap.add_argument("--kernel-variant", type=int, default=-1,
                     help="fix the stream-collide variant (0-3) instead of tuning it (profiling)")
+    ap.add_argument("--single", action="store_true",
+                    help="only the single-lattice report (one 2048x1024 lattice alone; profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     nx, ny = (256, 128) if args.small else (2048, 1024)
@@ -435,6 +480,9 @@ def main():
 
     import paper_2609_02298_b300 as L
     L.use_torch_allocator()
+    if args.single:
+        print(json.dumps(single_case_report(L, torch, steps=4 * args.steps, only_large=True)), flush=True)
+        return
     if args.kernel_variant >= 0:
         for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
             L.set_kernel_variant(specs[0].storage, col, args.kernel_variant)
@@ -539,11 +587,17 @@ def main():
     if rank == 0:
         cpu = None
         if not args.small and args.cpu_budget > 0:
-            mlups_cpu, n_cpu, dt_cpu = cpu_baseline(W.fixed_cylinder_2048(re=100.0, storage=W.F64,
-                                                                          collision=W.BGK, kernel=W.HAT,
-                                                                          scheme=W.DF), args.cpu_budget)
-            cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "%d steps of one 2048x1024 lattice (DF, hat, BGK, FP64), %.1f s" % (n_cpu, dt_cpu)}
+            try:
+                one, allc = cpu_baselines(args.cpu_budget)
+                cpu = {"value": one["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "sample": "%d steps of one 2048x1024 lattice (DF, hat, BGK, FP64), %.1f s, fresh process"
+                                 % (one["steps"], one["seconds"]),
+                       "cpu_model": cpu_model(),
+                       "all_cores": {"value": allc["mlups"], "cores": allc["threads"],
+                                     "sample": "%d steps of the same lattice, %.1f s, OpenMP over the oracle's "
+                                               "node loops" % (allc["steps"], allc["seconds"])}}
+            except Exception as exc:
+                cpu = {"error": repr(exc)}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

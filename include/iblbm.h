@@ -139,8 +139,10 @@ void iblbm_destroy(iblbm_ctx* ctx);
  * relaxation 1/||A||_inf is computed here once (Sec. 2.5.2); for DFC the
  * factors lambda_k of Eq. 17 are computed on the device.  Every kernel
  * footprint must lie inside the lattice.  *body_id receives the index (0, 1,
- * ...).  Errors: INVALID_ARG, MARKER_OUT_OF_DOMAIN, BODY_OVERLAP (two MDF
- * bodies whose footprints could overlap), OOM. */
+ * ...).  A second MDF body in a lattice switches its MDF bodies to the coupled
+ * iteration (iblbm_mdf_relaxation) and allocates a lattice-wide scratch of three
+ * values per node.  Errors: INVALID_ARG, MARKER_OUT_OF_DOMAIN, OOM.
+ * (IBLBM_ERR_BODY_OVERLAP is no longer returned: MDF bodies may share nodes.) */
 int iblbm_add_body(iblbm_ctx* ctx, const double* xy, int n, double ds, int kernel, int scheme,
                    const iblbm_body_desc* body, int* body_id);
 
@@ -213,6 +215,15 @@ int iblbm_local_diagnostics(iblbm_ctx* ctx, int body_id, double u_ref, double ka
 /* MDF diagnostics of the last step: increments applied, last L_inf residual
  * (FP64) and omega_MDF.  Syncs. */
 int iblbm_mdf_info(iblbm_ctx* ctx, int body_id, int* iterations, double* residual, double* omega);
+/* Relaxation factor in use when the body's last MDF iteration ended.  A lattice with
+ * two or more MDF bodies iterates them coupled (Sec. 2.5.2): one fluid update per
+ * iteration shared by every MDF body, omega starting at min(0.8, omega_MDF of the
+ * bodies) and halved for every trial iteration whose L_inf residual (over all their
+ * markers) grows by more than 20 %, the iteration ending at 0.125 of the start value;
+ * iblbm_mdf_info then reports the trial iterations (rejected ones included) and the
+ * joint residual, the same for every coupled body.  A single MDF body keeps omega_MDF
+ * (this call returns it).  Syncs.  Errors: INVALID_ARG. */
+int iblbm_mdf_relaxation(iblbm_ctx* ctx, int body_id, double* omega_end);
 
 /* Post-collision populations into f[9*nx*ny] (layout above).  shifted = 0
  * returns f; shifted = 1 returns the stored values f - w_i exactly as held in
@@ -311,6 +322,10 @@ int iblbm_server_poll(iblbm_server* srv, long long req_id, double* forces_out, i
                       double* latency_s);
 /* Device bytes held by resident cases and the resident / queued counts. */
 int iblbm_server_stats(const iblbm_server* srv, size_t* used_bytes, int* resident, int* queued);
+/* Whether ticks replay the batch's captured CUDA graphs (1, the default: a new set
+ * of resident requests captures its graphs on its first tick) or launch each step's
+ * kernels one by one (0).  Results are the same either way.  Errors: INVALID_ARG. */
+int iblbm_server_set_graphs(iblbm_server* srv, int enable);
 
 /* ---- allocation-free lambda_k ------------------------------------------------------------ */
 /* No counterpart in the paper.  For callers that cannot allocate device memory

@@ -20,6 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "iblbm_oracle.c")
 _HDR = os.path.join(_HERE, "iblbm_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# all-cores build of the same source (OpenMP over the node loops), used when the
+# environment sets IBLBM_ORACLE_OPENMP=1 (the all-cores CPU baseline)
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 PERIODIC, VELOCITY, NEUMANN = 0, 1, 2
 BGK, TRT, CMMRT, STREAM_ONLY = 0, 1, 2, 3
@@ -30,16 +33,19 @@ FIXED, PRESCRIBED, FREE = 0, 1, 2
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add); returns the .so path."""
-    stale = not os.path.exists(_LIB) or any(
-        os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add); returns the .so path.
+    ``openmp`` builds the all-cores copy (the node loops' OpenMP pragmas enabled)."""
+    out = _LIB_OMP if openmp else _LIB
+    stale = not os.path.exists(out) or any(
+        os.path.getmtime(p) > os.path.getmtime(out) for p in (_SRC, _HDR))
     if force or stale:
-        tmp = _LIB + ".tmp%d" % os.getpid()
+        tmp = out + ".tmp%d" % os.getpid()
+        flags = ["-fopenmp"] if openmp else ["-Wno-unknown-pragmas"]
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
-                               "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-Wall"] + flags + ["-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class LatticeParams(C.Structure):
@@ -60,7 +66,7 @@ class BodyParams(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(build(openmp=os.environ.get("IBLBM_ORACLE_OPENMP") == "1"))
         P = C.POINTER
         d, i, vp = C.c_double, C.c_int, C.c_void_p
         pd, pi = P(C.c_double), P(C.c_int)

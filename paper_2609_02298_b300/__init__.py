@@ -73,6 +73,7 @@ SIGNATURES = [
     ("iblbm_marker_data", _i, [_vp, _i, _pd]),
     ("iblbm_marker_stencils", _i, [_vp, _i, _pi]),
     ("iblbm_mdf_info", _i, [_vp, _i, _pi, _pd, _pd]),
+    ("iblbm_mdf_relaxation", _i, [_vp, _i, _pd]),
     ("iblbm_local_diagnostics", _i, [_vp, _i, C.c_double, C.c_double, _pd, _vp]),
     ("iblbm_set_marker_velocity", _i, [_vp, _i, _vp]),
     ("iblbm_get_populations", _i, [_vp, _pd, _i]),
@@ -97,6 +98,7 @@ SIGNATURES = [
     ("iblbm_server_tick", _i, [_vp, _i, _pi, _pi]),
     ("iblbm_server_poll", _i, [_vp, _ll, _pd, _i, _pi, _pd]),
     ("iblbm_server_stats", _i, [_vp, _P(_sz), _pi, _pi]),
+    ("iblbm_server_set_graphs", _i, [_vp, _i]),
 ]
 
 _lib = None
@@ -322,6 +324,12 @@ class Lattice:
                "iblbm_mdf_info")
         return it.value, res.value, om.value
 
+    def mdf_relaxation(self, b: int = 0) -> float:
+        """Relaxation in use when the last MDF iteration ended (coupled path: halved per rejection)."""
+        om = C.c_double(0)
+        _check(load_library().iblbm_mdf_relaxation(self._h, b, C.byref(om)), "iblbm_mdf_relaxation")
+        return om.value
+
     def set_marker_velocity(self, b: int, ud=None) -> None:
         """Desired velocity per marker of a fixed body (``[n, 2]``), or None for the
         rigid velocity again (iblbm_set_marker_velocity)."""
@@ -472,6 +480,10 @@ class Server:
         if getattr(self, "_h", None) is not None and self._h.value:
             load_library().iblbm_server_destroy(self._h)
         self._h = None
+
+    def set_graphs(self, enable: bool) -> None:
+        """Ticks replay captured step graphs (True, the default) or launch step by step."""
+        _check(load_library().iblbm_server_set_graphs(self._h, 1 if enable else 0), "iblbm_server_set_graphs")
 
     def __del__(self):
         try:

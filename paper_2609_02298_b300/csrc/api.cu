@@ -350,11 +350,6 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
         if (!stencil_ok(S, c->hc.nx, c->hc.ny, xy[2 * k], xy[2 * k + 1])) return IBLBM_ERR_MARKER_OUT_OF_DOMAIN;
         reach = std::max(reach, std::hypot(xy[2 * k] - bd->xc, xy[2 * k + 1] - bd->yc));
     }
-    if (scheme == SCH_MDF) {
-        for (auto& o : c->bodies)
-            if (o.scheme == SCH_MDF && std::hypot(o.xc - bd->xc, o.yc - bd->yc) < o.reach + reach + 5.0)
-                return IBLBM_ERR_BODY_OVERLAP;
-    }
     const size_t rb = real_bytes(c->hc.storage);
     const int box_cap = box_capacity(reach, S);
     const int nent = n * S * S;
@@ -412,6 +407,18 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     cudaMemsetAsync(B.lam, 0, 8 * n, w);
     cudaMemsetAsync(B.hist, 0, 24 * (size_t)hist_cap, w);
     const int id = (int)c->bodies.size();
+    if (scheme == SCH_MDF) {
+        // two or more MDF bodies iterate coupled (Sec. 2.5.2) over a lattice-wide scratch
+        if (c->hc.n_mdf == 0) c->hc.mdf_lead = id;
+        c->hc.n_mdf += 1;
+        if (c->hc.n_mdf == 2 && !c->hc.cpl) {
+            c->hc.cpl = c->alloc(3 * (size_t)c->hc.nx * c->hc.ny * rb);
+            if (!c->hc.cpl) return IBLBM_ERR_OOM;
+        }
+        cudaMemcpyAsync(&c->dc->n_mdf, &c->hc.n_mdf, sizeof(int), cudaMemcpyHostToDevice, w);
+        cudaMemcpyAsync(&c->dc->mdf_lead, &c->hc.mdf_lead, sizeof(int), cudaMemcpyHostToDevice, w);
+        cudaMemcpyAsync(&c->dc->cpl, &c->hc.cpl, sizeof(void*), cudaMemcpyHostToDevice, w);
+    }
     cudaMemcpyAsync(&c->dbodies[id], &B, sizeof(BodyDev), cudaMemcpyHostToDevice, w);
     BodyRef ref{c->dc, &c->dbodies[id], id, 0};
     cudaMemcpyAsync(&c->drefs[id], &ref, sizeof(BodyRef), cudaMemcpyHostToDevice, w);
@@ -602,6 +609,15 @@ int iblbm_mdf_info(iblbm_ctx* c, int id, int* iters, double* res, double* omega)
     if (iters) *iters = b.st.mdf_iters;
     if (res) *res = b.st.mdf_res;
     if (omega) *omega = b.st.mdf_omega;
+    return rc;
+}
+
+int iblbm_mdf_relaxation(iblbm_ctx* c, int id, double* omega_end) {
+    if (!body_index_ok(c, id) || !omega_end) return IBLBM_ERR_INVALID_ARG;
+    int rc = sync_status(c);
+    if (rc < 0) return rc;
+    BodyDev b = fetch_body(c, id);
+    *omega_end = b.st.mdf_omega_end;
     return rc;
 }
 
@@ -817,7 +833,7 @@ struct BatchGroup {
     long long* djob[SC_VARIANTS] = {};
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
     int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
-    unsigned long long* dctr = nullptr;        // job counter of the scalar variants (2 words)
+    int grid_overlap[SC_VARIANTS] = {};        // grid while the IB stage holds some SMs
 };
 
 // Stream-collide variant per (storage, collision, size class), process-wide so
@@ -857,7 +873,6 @@ struct ListGroup {
     int4* dlist = nullptr;
     long long n = 0;
     int grid = 0;
-    unsigned long long* dctr = nullptr;
 };
 
 struct BatchPlan {
@@ -877,8 +892,9 @@ struct BatchPlan {
     // Lattice-edge launch overlapped with the IB stage on a side stream, when no body
     // can reach a lattice edge (the edge nodes then need no IB patch).
     bool edges_early = false;
-    // Every body fixed with a valid footprint: the IB stage runs alongside the sweep of
-    // everything outside the IB regions, whose segments are swept after it (list_groups).
+    // Every body fixed with a valid footprint, and few enough bodies: the IB stage runs
+    // alongside the sweep of everything outside the IB regions, on SMs the sweep's grid
+    // leaves free; the IB-region segments are swept after it (list_groups).
     bool overlap_ok = false;
     std::vector<ListGroup> list_groups;
     cudaStream_t side = nullptr;
@@ -934,6 +950,9 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         if (v == SC_VECTOR) early = false;
         if (!sc_variant_phased(v)) overlap = false;
     }
+    // the sweep beside the IB stage needs every free SM slot at once: the edge launch
+    // then follows the sweeps instead of running beside them
+    if (overlap) early = false;
     if (early) {
         cudaEventRecord(P->ev_fork, st);
         cudaStreamWaitEvent(P->side, P->ev_fork, 0);
@@ -950,16 +969,17 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     const bool dependent = overlap && !P->ib_groups.empty();
     for (auto& g : P->groups) {
         const int v = chosen_variant(g);
-        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], g.dctr, nullptr, overlap ? (int)SC_SKIP_IB : (int)SC_ALL,
+        ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], nullptr, overlap ? (int)SC_SKIP_IB : (int)SC_ALL,
                     dependent ? (int)(PDL_TRIGGER | PDL_DEPENDENT) : 0};
+        const int grid = overlap ? g.grid_overlap[v] : g.grid[v];
         if ((e = timed_launch(timer, STAGE_SWEEP, st, [&] {
-                 return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], st);
+                 return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], grid, st);
              })) != cudaSuccess)
             return e;
     }
     if (overlap)
         for (auto& lg : P->list_groups) {
-            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dctr, lg.dlist, (int)SC_LIST, 0};
+            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dlist, (int)SC_LIST, 0};
             if ((e = launch_stream_collide(lg.storage, lg.collision, SC_SCALAR2, sl, lg.n, lg.grid, st)) !=
                 cudaSuccess)
                 return e;
@@ -973,12 +993,25 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
 // (fixed) markers, the boxes read back and every kIbAlign-aligned 64-node segment of
 // their rows listed once per lattice.  Leaves overlap_ok false when a body is not fixed
 // or has no footprint.
+// At most this many IB CTAs (bodies) for the overlap: each holds a whole SM that the
+// sweep beside it gives up (so all the sweep's CTAs run at once and its static job
+// split stays balanced); beyond that the SMs given up cost more than the overlap saves.
+constexpr int kOverlapMaxBodies = 8;
+
 int build_ib_lists(BatchPlan* P, int sms) {
     P->overlap_ok = false;
-    if (P->ib_groups.empty()) return IBLBM_OK;
+    if (P->ib_groups.size() != 1 || P->ib_groups[0].nrefs > kOverlapMaxBodies) return IBLBM_OK;
     for (auto* c : P->ctxs)
         for (auto& b : c->bodies)
             if (b.motion != MOT_FIXED) return IBLBM_OK;
+    const int free_sms = sms - P->ib_groups[0].nrefs;
+    for (auto& g : P->groups)
+        for (int v = 0; v < SC_VARIANTS; ++v) {
+            const long long cap = (long long)free_sms * sc_blocks_per_sm(g.storage, g.collision, v);
+            g.grid_overlap[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 7) / 8, cap));
+            if (g.block[v] == 64)
+                g.grid_overlap[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
+        }
     for (auto& g : P->ib_groups) {
         IbLaunch setup{g.drefs, g.nrefs, 1, 0};
         int rc = check(launch_ib(g.storage, setup, P->st));
@@ -1012,10 +1045,8 @@ int build_ib_lists(BatchPlan* P, int sms) {
         lg.n = (long long)list.size();
         lg.grid = (int)std::max<long long>(1, std::min<long long>((lg.n + 15) / 16, 4LL * sms));
         lg.dlist = static_cast<int4*>(plan_alloc(P, sizeof(int4) * list.size()));
-        lg.dctr = static_cast<unsigned long long*>(plan_alloc(P, 2 * sizeof(unsigned long long)));
-        if (!lg.dlist || !lg.dctr) return IBLBM_ERR_OOM;
+        if (!lg.dlist) return IBLBM_ERR_OOM;
         cudaMemcpyAsync(lg.dlist, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, P->st);
-        cudaMemsetAsync(lg.dctr, 0, 2 * sizeof(unsigned long long), P->st);
         P->list_groups.push_back(lg);
     }
     rc = check(cudaStreamSynchronize(P->st));
@@ -1133,9 +1164,6 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                     g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
                 }
             }
-            g.dctr = static_cast<unsigned long long*>(plan_alloc(P, 2 * sizeof(unsigned long long)));
-            if (!g.dctr) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
-            cudaMemsetAsync(g.dctr, 0, 2 * sizeof(unsigned long long), P->st);
             P->groups.push_back(g);
         }
     }
@@ -1166,7 +1194,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 g_variant_ms[g.storage][g.collision][g.size_class][v] = 0.0;
                 continue;
             }
-            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], g.dctr, nullptr, (int)SC_ALL, 0};
+            ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], nullptr, (int)SC_ALL, 0};
             float ms = 0.f, tot = 0.f;
             launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], g.grid[v], P->st);   // warm
             for (int r = 0; r < 3; ++r) {

@@ -75,6 +75,9 @@ struct CaseDev {
     unsigned int status;
     int wall_bb;                  // bit s: side s closes by on-node bounce-back (wall_closure = 1 and a
                                   // zero velocity, decided once on the host from the FP64 u_bc)
+    int n_mdf, mdf_lead;          // MDF bodies; with two or more they iterate coupled, stepped by
+                                  // the IB CTA of the first (mdf_lead)
+    void* cpl;                    // coupled MDF scratch, 3 nx ny R: spread F_x, F_y, 1/(2 rho) per node
 };
 
 // Dynamic FP64 state of a rigid body (what a checkpoint carries besides arrays).
@@ -85,6 +88,7 @@ struct BodyState {
     double mdf_omega, mdf_res;
     long long nstep, hist_n;
     int mdf_iters, omega_valid;
+    double mdf_omega_end;                    // relaxation in use when the last MDF iteration ended
 };
 
 // One rigid body in device memory (R-typed scratch as void*).

@@ -79,18 +79,6 @@ __device__ __forceinline__ bool seg_in_ib(const CaseDev& C, int y, int xseg) {
     return false;
 }
 
-// End of a launch that takes jobs from L.ctr: the last CTA to finish resets the counters.
-__device__ __forceinline__ void release_job_counter(unsigned long long* ctr) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned long long done = atomicAdd(ctr + 1, 1ull);
-        if (done == (unsigned long long)gridDim.x - 1ull) {
-            ctr[0] = 0ull;
-            ctr[1] = 0ull;
-        }
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // Stream-collide of one row segment [xseg, xseg + 32V) of row y, one warp.
@@ -367,59 +355,51 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = 4; };
 template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
-// Jobs in ascending order, taken kScChunk at a time by each warp from a counter in
-// global memory (the next chunk is claimed before the current one is swept, so the
-// atomic's latency overlaps the sweep), so the warps resident at any moment sweep one
-// compact window of each plane (measured on B300: ~10% of HBM over one contiguous job
-// range per warp) and CTAs that start late -- their SM busy with the IB stage --
-// simply take fewer chunks.
-constexpr int kScChunk = 2;
+// Dense job order: warp w takes jobs w, w + W, w + 2W, ... (W warps in the grid),
+// so the warps resident at any moment sweep one compact window of each plane;
+// measured on B300 this beats one contiguous job range per warp by ~10% of HBM.
+// (Taking jobs from a global counter instead, two jobs per atomic, ran 1.7-2.5x
+// slower: the counter's atomics serialise.)  All CTAs of a launch must be resident
+// together for the split to balance, which the host arranges when the IB stage runs
+// beside the sweep (the grid leaves its SMs free).
 template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     if (L.pdl & PDL_TRIGGER) pdl_trigger();
     const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
     int nseg = 1, cur = -1;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(L.ctr, (unsigned long long)kScChunk);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    while ((long long)base < jobs) {
-        unsigned long long next = 0;
-        if (lane == 0) next = atomicAdd(L.ctr, (unsigned long long)kScChunk);
-        const long long jend = min((long long)base + kScChunk, jobs);
-        for (long long job = (long long)base; job < jend; ++job) {
-            if (L.phase == SC_LIST) {
-                const int4 e = L.list[job];
-                if (e.x != cur) {
-                    K.load(L.cases[e.x]);
-                    cur = e.x;
-                }
-                sc_row_scalar<S, KIND, NPT>(K, e.y, e.z, lane);
-                continue;
+    for (long long job = gw; job < jobs; job += nw) {
+        if (L.phase == SC_LIST) {
+            const int4 e = L.list[job];
+            if (e.x != cur) {
+                K.load(L.cases[e.x]);
+                cur = e.x;
             }
-            if (job >= c_hi || job < c_lo) {
-                int lo = 0, hi = L.ncases - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
-                }
-                c_lo = L.job_off[lo];
-                c_hi = L.job_off[lo + 1];
-                K.load(L.cases[lo]);
-                nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
-            }
-            const int local = (int)(job - c_lo);   // < ny * nseg
-            const int y = local / nseg;
-            const int xseg = (local - y * nseg) * 32 * NPT;
-            if (L.phase == SC_SKIP_IB && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
-            sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
+            sc_row_scalar<S, KIND, NPT>(K, e.y, e.z, lane);
+            continue;
         }
-        base = __shfl_sync(0xffffffffu, next, 0);
+        if (job >= c_hi || job < c_lo) {
+            int lo = 0, hi = L.ncases - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.job_off[mid] <= job) lo = mid; else hi = mid - 1;
+            }
+            c_lo = L.job_off[lo];
+            c_hi = L.job_off[lo + 1];
+            K.load(L.cases[lo]);
+            nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
+        }
+        const int local = (int)(job - c_lo);   // < ny * nseg
+        const int y = local / nseg;
+        const int xseg = (local - y * nseg) * 32 * NPT;
+        if (L.phase == SC_SKIP_IB && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
+        sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
     }
     if (L.pdl & PDL_DEPENDENT) pdl_wait();
-    release_job_counter(L.ctr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -977,19 +957,23 @@ template <class R> struct IbSmem {
                                  (kMdfEntryCap + kMdfNodeCap + 1) * 4;
 };
 
+// Parts of the per-body IB stage: all of it; footprint and gather only (the coupled MDF
+// runs between); spread and force sums of marker forces already set.
+enum { IB_WHOLE = 0, IB_GATHER = 1, IB_SPREAD = 2 };
+
 // Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
 template <class S, int SX>
 __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
                                        typename Traits<S>::R* sU, typename Traits<S>::R* sF,
                                        typename Traits<S>::R* sEw, int* sEk, typename Traits<S>::R* sQc,
-                                       int* sQo) {
+                                       int* sQo, int part = IB_WHOLE) {
     using R = typename Traits<S>::R;
     constexpr int SS = SX * SX;
     const CaseDev& C = *ref.c;
     BodyDev& B = *ref.b;
     const int tid = threadIdx.x;
     const int n = B.n, scheme = B.scheme;
-    if (!B.cache_valid) {
+    if (part != IB_SPREAD && !B.cache_valid) {
         if (!build_footprint<R>(C, B, shi)) return;
         if (tid == 0) B.cache_valid = (B.motion == MOT_FIXED) ? 1 : 0;
     }
@@ -1004,7 +988,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
 
     // MDF relaxation 1/||A||_inf (Sec. 2.5.2): sum_m A_lm = ds sum_x D_l(x) W(x),
     // W(x) = sum_m D_m(x); computed once on the first step.
-    if (scheme == SCH_MDF && !B.st.omega_valid) {
+    if (part != IB_SPREAD && scheme == SCH_MDF && !B.st.omega_valid) {
         for (int q = tid; q < nfp; q += kIbThreads) {
             R w = R(0);
             for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) w += cw[o];
@@ -1065,6 +1049,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         if (tid == 0) B.lam_valid = 1;
     }
 
+    if (part != IB_SPREAD) {
     // gather the post-streaming state at every footprint node
     const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
     // GB footprint nodes per thread at a time: their pulls are issued together
@@ -1117,7 +1102,9 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         }
         }
     }
+    }
     __syncthreads();
+    if (part == IB_GATHER) return;
 
     // force and torque on the body (Sec. 2.7), accumulated in FP64 by each thread as its
     // markers' forces are final (ascending k per thread), reduced at the end
@@ -1129,7 +1116,10 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         gys += gy;
         ts += rx * gy - ry * gx;
     };
-    if (scheme == SCH_DF) {
+    if (part == IB_SPREAD) {
+        // marker forces already final (coupled MDF): mk[16k + 0..1] and B.Fx, B.Fy
+        for (int k = tid; k < n; k += kIbThreads) body_force(k, -B.Fx[k] * B.ds, -B.Fy[k] * B.ds);
+    } else if (scheme == SCH_DF) {
         // Eq. 7 on rho and u_raw, Eq. 11
         for (int k = tid; k < n; k += kIbThreads) {
             int sl[SS];
@@ -1273,6 +1263,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         if (tid == 0) {
             B.st.mdf_iters = applied;
             B.st.mdf_res = r;
+            B.st.mdf_omega_end = B.st.mdf_omega;
             if (guard || (!tol_met && B.mdf_nmax > B.mdf_nmin)) {
                 B.status |= STAT_MDF_WARN;
                 atomicOr(const_cast<unsigned*>(&C.status), STAT_MDF_WARN);
@@ -1357,6 +1348,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         if (tid == 0) {
             B.st.mdf_iters = applied;
             B.st.mdf_res = r;
+            B.st.mdf_omega_end = B.st.mdf_omega;
             if (guard || (!tol_met && B.mdf_nmax > B.mdf_nmin)) {
                 B.status |= STAT_MDF_WARN;
                 atomicOr(const_cast<unsigned*>(&C.status), STAT_MDF_WARN);
@@ -1448,6 +1440,231 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
 __device__ void body_prepare(BodyDev& B, double* sh);
 __device__ void body_finish(BodyDev& B);
 
+// Global node index of footprint slot q of body B.
+__device__ __forceinline__ int slot_node(const BodyDev& B, int nx, int q) {
+    const int node = B.fp_node[q];
+    return (B.by0 + node / B.bw) * nx + B.bx0 + node % B.bw;
+}
+
+// Marker m of the coupled set -> (body index in C, marker index in that body).
+__device__ __forceinline__ void coupled_marker(const CaseDev& C, const int* list, int nb, const int* off, int m,
+                                               int& b, int& k) {
+    int j = 0;
+    while (j + 1 < nb && off[j + 1] <= m) ++j;
+    b = list[j];
+    k = m - off[j];
+}
+
+// Interpolation weights and global nodes of marker k of B (its SX x SX stencil).
+template <class R>
+__device__ __forceinline__ int marker_nodes(const BodyDev& B, int nx, int k, int (&g)[16], R (&D)[16]) {
+    const int SX = B.S, SS = SX * SX;
+    const R* wts = static_cast<const R*>(B.wts);
+    for (int r = 0; r < SS; ++r) {
+        g[r] = slot_node(B, nx, B.mslot[k * SS + r]);
+        D[r] = wts[k * 8 + (r % SX)] * wts[k * 8 + 4 + (r / SX)];
+    }
+    return SS;
+}
+
+// Coupled MDF of every MDF body of the case (Sec. 2.5.2, two or more of them), run by
+// one CTA after each body's footprint gather.  The bodies' marker forces share one
+// fluid update per iteration: S(x) = sum_b spread_b(F_b) (bodies in index order, each
+// node summing its markers in ascending order), and, Eq. 12-14 being linear in the
+// iterate, a trial with relaxation omega moves every marker velocity to
+// U + omega G(k), G(k) = sum_x D(x - X_k) S(x) / (2 rho(x)), so a rejected trial is
+// retried with omega / 2 at no extra spreading.  omega_0 = min(0.8, omega_MDF of the
+// bodies); a trial whose L_inf residual (FP64, all markers) exceeds 1.2 times the
+// current one is rejected and omega halved, ending the iteration at 0.125 omega_0; every
+// trial counts towards N_max; at least N_min accepted increments precede a tolerance
+// stop; N_min, N_max and tol are the first MDF body's.  Marker scratch mk[16k + ...]:
+// 2 rho_k, 3-4 F_total, 5-6 F, 7-8 U, 9-10 G.
+template <class S>
+__device__ void mdf_coupled(const CaseDev& C, int* shi, double* shd) {
+    using R = typename Traits<S>::R;
+    const int tid = threadIdx.x, nx = C.nx;
+    const long long N = (long long)C.nx * C.ny;
+    R* Sx = static_cast<R*>(C.cpl);
+    R* Sy = Sx + N;
+    R* Q = Sy + N;
+    int* list = shi;              // MDF bodies of the case, ascending index
+    int* off = shi + kMaxBodies;  // first coupled marker of each (plus the total)
+    __syncthreads();
+    if (tid == 0) {
+        int nb = 0, m = 0;
+        for (int b = 0; b < C.nbodies; ++b)
+            if (C.bodies[b].scheme == SCH_MDF) {
+                list[nb] = b;
+                off[nb] = m;
+                m += C.bodies[b].n;
+                ++nb;
+            }
+        off[nb] = m;
+        shi[2 * kMaxBodies + 1] = nb;
+    }
+    __syncthreads();
+    const int nb = shi[2 * kMaxBodies + 1], M = off[nb];
+    bool ok = true;
+    double om0 = 0.8;
+    for (int j = 0; j < nb; ++j) {
+        ok = ok && C.bodies[list[j]].nfp > 0;
+        om0 = fmin(om0, C.bodies[list[j]].st.mdf_omega);
+    }
+    const BodyDev& B0 = C.bodies[list[0]];
+    const int nmin = B0.mdf_nmin, nmax = B0.mdf_nmax;
+    const double tol = B0.mdf_tol;
+    int trials = 0, applied = 0;
+    double ra = 0.0, om = om0;
+    bool tol_met = false;
+    if (ok) {
+        // 1 / (2 rho(x)) at every footprint node; rho_k, U^(0) and F per marker
+        for (int j = 0; j < nb; ++j) {
+            const BodyDev& B = C.bodies[list[j]];
+            const R* fp = static_cast<const R*>(B.fpdata);
+            for (int q = tid; q < B.nfp; q += kIbThreads) Q[slot_node(B, nx, q)] = R(1) / (R(2) * fp[(size_t)q * 9]);
+        }
+        double e2 = 0.0;
+        for (int m = tid; m < M; m += kIbThreads) {
+            int b, k;
+            coupled_marker(C, list, nb, off, m, b, k);
+            const BodyDev& B = C.bodies[b];
+            const R* fp = static_cast<const R*>(B.fpdata);
+            R* mk = static_cast<R*>(B.mk) + (size_t)k * 16;
+            int g[16];
+            R D[16];
+            const int SS = marker_nodes<R>(B, nx, k, g, D);
+            R rk = R(0), Ux = R(0), Uy = R(0);
+            for (int r = 0; r < SS; ++r) {
+                const int q = B.mslot[k * SS + r];
+                rk += fp[(size_t)q * 9] * D[r];
+                Ux += fp[(size_t)q * 9 + 1] * D[r];
+                Uy += fp[(size_t)q * 9 + 2] * D[r];
+            }
+            const double dx = B.Udx[k] - (double)Ux, dy = B.Udy[k] - (double)Uy;
+            e2 = fmax(e2, dx * dx + dy * dy);
+            mk[2] = rk;
+            mk[3] = R(0);
+            mk[4] = R(0);
+            mk[5] = R(2) * rk * (R(B.Udx[k]) - Ux);   // Eq. 13
+            mk[6] = R(2) * rk * (R(B.Udy[k]) - Uy);
+            mk[7] = Ux;
+            mk[8] = Uy;
+        }
+        ra = block_max_sqrt(e2, shd);
+        bool need_g = true;
+        for (;;) {
+            if (applied >= nmin && ra < tol) { tol_met = true; break; }
+            if (trials >= nmax) break;
+            if (need_g) {
+                for (int j = 0; j < nb; ++j) {
+                    const BodyDev& B = C.bodies[list[j]];
+                    for (int q = tid; q < B.nfp; q += kIbThreads) {
+                        const int gq = slot_node(B, nx, q);
+                        Sx[gq] = R(0);
+                        Sy[gq] = R(0);
+                    }
+                }
+                __syncthreads();
+                for (int j = 0; j < nb; ++j) {   // bodies in order: S(x) = sum_b spread_b(F_b)
+                    const BodyDev& B = C.bodies[list[j]];
+                    const int SS = B.S * B.S;
+                    const R* cw = static_cast<const R*>(B.csr_w);
+                    const R* mkb = static_cast<const R*>(B.mk);
+                    const R ds = R(B.ds);
+                    for (int q = tid; q < B.nfp; q += kIbThreads) {
+                        R sx = R(0), sy = R(0);
+                        for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) {
+                            const int k = B.csr_ent[o] / SS;
+                            sx += mkb[(size_t)k * 16 + 5] * cw[o] * ds;
+                            sy += mkb[(size_t)k * 16 + 6] * cw[o] * ds;
+                        }
+                        const int gq = slot_node(B, nx, q);
+                        Sx[gq] += sx;
+                        Sy[gq] += sy;
+                    }
+                    __syncthreads();
+                }
+                for (int m = tid; m < M; m += kIbThreads) {
+                    int b, k;
+                    coupled_marker(C, list, nb, off, m, b, k);
+                    const BodyDev& B = C.bodies[b];
+                    R* mk = static_cast<R*>(B.mk) + (size_t)k * 16;
+                    int g[16];
+                    R D[16];
+                    const int SS = marker_nodes<R>(B, nx, k, g, D);
+                    R Gx = R(0), Gy = R(0);
+                    for (int r = 0; r < SS; ++r) {
+                        Gx += Sx[g[r]] * Q[g[r]] * D[r];
+                        Gy += Sy[g[r]] * Q[g[r]] * D[r];
+                    }
+                    mk[9] = Gx;
+                    mk[10] = Gy;
+                }
+                need_g = false;
+            }
+            // trial: every marker velocity at U + omega G
+            const R rom = R(om);
+            double t2 = 0.0;
+            for (int m = tid; m < M; m += kIbThreads) {
+                int b, k;
+                coupled_marker(C, list, nb, off, m, b, k);
+                const BodyDev& B = C.bodies[b];
+                const R* mk = static_cast<const R*>(B.mk) + (size_t)k * 16;
+                const double dx = B.Udx[k] - (double)(mk[7] + rom * mk[9]);
+                const double dy = B.Udy[k] - (double)(mk[8] + rom * mk[10]);
+                t2 = fmax(t2, dx * dx + dy * dy);
+            }
+            const double rt = block_max_sqrt(t2, shd);
+            ++trials;
+            if (rt > 1.2 * ra) {          // rejected: keep the iterate, halve the relaxation
+                om *= 0.5;
+                if (om <= 0.125 * om0) break;
+                continue;
+            }
+            for (int m = tid; m < M; m += kIbThreads) {   // accepted
+                int b, k;
+                coupled_marker(C, list, nb, off, m, b, k);
+                const BodyDev& B = C.bodies[b];
+                R* mk = static_cast<R*>(B.mk) + (size_t)k * 16;
+                const R Ux = mk[7] + rom * mk[9], Uy = mk[8] + rom * mk[10];
+                mk[3] += rom * mk[5];
+                mk[4] += rom * mk[6];
+                mk[7] = Ux;
+                mk[8] = Uy;
+                mk[5] = R(2) * mk[2] * (R(B.Udx[k]) - Ux);
+                mk[6] = R(2) * mk[2] * (R(B.Udy[k]) - Uy);
+            }
+            ra = rt;
+            ++applied;
+            need_g = true;
+        }
+    }
+    // final marker forces for the spread, and the diagnostics of every coupled body
+    for (int m = tid; m < M; m += kIbThreads) {
+        int b, k;
+        coupled_marker(C, list, nb, off, m, b, k);
+        BodyDev& B = C.bodies[b];
+        R* mk = static_cast<R*>(B.mk) + (size_t)k * 16;
+        const R fx = ok ? mk[3] : R(0), fy = ok ? mk[4] : R(0);
+        mk[0] = fx;
+        mk[1] = fy;
+        B.Fx[k] = (double)fx;
+        B.Fy[k] = (double)fy;
+    }
+    if (tid == 0)
+        for (int j = 0; j < nb; ++j) {
+            BodyDev& B = C.bodies[list[j]];
+            B.st.mdf_iters = trials;
+            B.st.mdf_res = ra;
+            B.st.mdf_omega_end = om;
+            if (!tol_met && ok) {
+                B.status |= STAT_MDF_WARN;
+                atomicOr(const_cast<unsigned*>(&C.status), STAT_MDF_WARN);
+            }
+        }
+    __syncthreads();
+}
+
 // One CTA per body.  Mode 0 (a step): body motion (body_prepare), the IB stage, then the
 // end-of-step body update (body_finish); mode 1: footprint and omega_MDF only.
 template <class S>
@@ -1465,6 +1682,31 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     R* sQc = sEw + kMdfEntryCap;
     int* sEk = reinterpret_cast<int*>(sQc + kMdfNodeCap);
     int* sQo = sEk + kMdfEntryCap;
+    const CaseDev& C = *ref.c;
+    if (L.mode == 0 && C.n_mdf >= 2 && ref.b->scheme == SCH_MDF) {
+        // coupled MDF: the CTA of the first MDF body steps all of them
+        if (ref.index != C.mdf_lead) return;
+        for (int b = 0; b < C.nbodies; ++b)
+            if (C.bodies[b].scheme == SCH_MDF) body_prepare(C.bodies[b], shd);
+        for (int b = 0; b < C.nbodies; ++b) {
+            if (C.bodies[b].scheme != SCH_MDF) continue;
+            const BodyRef rb{ref.c, &C.bodies[b], b, 0};
+            if (C.bodies[b].S == 2) ib_run<S, 2>(L, rb, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_GATHER);
+            else ib_run<S, 4>(L, rb, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_GATHER);
+        }
+        mdf_coupled<S>(C, shi, shd);
+        for (int b = 0; b < C.nbodies; ++b) {
+            if (C.bodies[b].scheme != SCH_MDF) continue;
+            const BodyRef rb{ref.c, &C.bodies[b], b, 0};
+            if (C.bodies[b].nfp > 0) {
+                if (C.bodies[b].S == 2) ib_run<S, 2>(L, rb, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_SPREAD);
+                else ib_run<S, 4>(L, rb, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_SPREAD);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) body_finish(C.bodies[b]);
+        }
+        return;
+    }
     if (L.mode == 0) body_prepare(*ref.b, shd);
     if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
     else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);

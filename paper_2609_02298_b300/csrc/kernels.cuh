@@ -33,9 +33,6 @@ struct ScLaunch {
     long long* job_off;
     int ncases;
     int block;   // threads per CTA for the scalar variants (0: kThreads)
-    // Scalar variants take jobs in chunks from ctr[0]; ctr[1] counts finished CTAs and
-    // the last CTA resets both, so each launch starts from zero.
-    unsigned long long* ctr;
     const int4* list;   // SC_LIST: segment (x = index into cases, y = row, z = first node)
     int phase;          // SC_ALL, SC_SKIP_IB or SC_LIST
     int pdl;            // PDL_* flags

@@ -55,6 +55,7 @@ struct iblbm_server {
     std::deque<Request*> queue;
     std::vector<Request*> resident;
     std::map<long long, Request*> all;
+    int use_graphs = 1;   // ticks replay the batch plan's captured step graphs
 };
 
 namespace {
@@ -191,7 +192,7 @@ int iblbm_server_tick(iblbm_server* s, int max_steps, int* resident, int* queued
         for (auto* r : s->resident) step = std::min(step, r->remaining);
         std::vector<iblbm_ctx*> ctxs;
         for (auto* r : s->resident) ctxs.push_back(r->ctx);
-        rc = iblbm_internal_step_batch(ctxs.data(), (int)ctxs.size(), (int)step, 0);
+        rc = iblbm_internal_step_batch(ctxs.data(), (int)ctxs.size(), (int)step, s->use_graphs);
         // while the device works, bring in requests that fit next to the running ones
         std::vector<Request*> before = s->resident;
         admit(s);
@@ -230,6 +231,12 @@ int iblbm_server_poll(iblbm_server* s, long long req_id, double* forces_out, int
     if (n) *n = m;
     if (latency_s) *latency_s = r->t_done - r->t_submit;
     return 1;
+}
+
+int iblbm_server_set_graphs(iblbm_server* s, int enable) {
+    if (!s) return IBLBM_ERR_INVALID_ARG;
+    s->use_graphs = enable ? 1 : 0;
+    return IBLBM_OK;
 }
 
 int iblbm_server_stats(const iblbm_server* s, size_t* used_bytes, int* resident, int* queued) {

@@ -244,6 +244,8 @@ def paper_table5():
 
 WAKE_CASES = [(W.DF, 1, W.BGK), (W.DF, 0, W.BGK), (W.DFC, 1, W.BGK), (W.DFC, 0, W.BGK)]
 WAKE_COLLISION_CASES = [(W.DF, 1, W.TRT), (W.DF, 1, W.CMMRT)]
+# coupled two-particle MDF (Sec. 2.5.2), adaptive N in [5, 20], tol 1e-4
+WAKE_MDF_CASES = [(W.MDF, 1, W.BGK), (W.MDF, 0, W.BGK)]
 
 
 def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F32, steps=40000, sample=100):
@@ -269,10 +271,10 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
             xc, yc = X / dx, (Y + 1.0) / dx
             xy, ds = W.circle_markers(xc, yc, D, nb)
             lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr, motion=W.FREE,
-                         gx=g, gy=0.0, internal_mass=im)
+                         gx=g, gy=0.0, internal_mass=im, mdf_nmin=5, mdf_nmax=20, mdf_tol=1e-4)
         cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
                       "collision": COLLISION_NAMES[col],
-                      "re": [[], []], "x": [[], []], "stopped": False})
+                      "re": [[], []], "x": [[], []], "mdf": [], "stopped": False})
     lats = [c["lat"] for c in cases]
     done = 0
     while done < steps and not all(c["stopped"] for c in cases):
@@ -286,6 +288,9 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
                     st = c["lat"].body_state(b)
                     c["re"][b].append(math.hypot(st[2], st[3]) * D / nu)
                     c["x"][b].append(float(st[0]))
+                if c["scheme"] == "MDF":   # iterations, joint residual and relaxation of the last step
+                    it, res, _ = c["lat"].mdf_info(0)
+                    c["mdf"].append((it, res, c["lat"].mdf_relaxation(0)))
                 if max(c["x"][0][-1], c["x"][1][-1]) > 4000.0 - 3.0 * D:
                     c["stopped"], c["stop_step"] = True, done
             except Exception as exc:
@@ -300,6 +305,14 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
         c["heavy_x_at_peak_D"] = (c["x"][0][c["heavy_step"] // sample - 1] - 320.0) / D
         c["light_x_at_peak_D"] = (c["x"][1][c["light_step"] // sample - 1] - 480.0) / D
         del c["x"]
+        mdf = c.pop("mdf")
+        if mdf:
+            its = np.array([m[0] for m in mdf])
+            res = np.array([m[1] for m in mdf])
+            c["mdf_iters_mean"], c["mdf_iters_min"], c["mdf_iters_max"] = float(its.mean()), int(its.min()), int(its.max())
+            c["mdf_at_nmax_frac"] = float((its >= 20).mean())
+            c["mdf_residual_median"], c["mdf_residual_p90"] = float(np.median(res)), float(np.percentile(res, 90))
+            c["mdf_relaxation_min"] = float(min(m[2] for m in mdf))
     return cases
 
 
@@ -428,7 +441,7 @@ def main():
             json.dump(rows, fh)
         return
     if args.wake:
-        rows = run_wake_interaction(L, storage=W.STORAGES[args.storage])
+        rows = run_wake_interaction(L, WAKE_CASES + WAKE_MDF_CASES, storage=W.STORAGES[args.storage])
         t5 = paper_table5()
         for r in rows:
             r["paper_heavy_re"], r["paper_light_re"] = t5[(r["scheme"], r["internal_mass"])]

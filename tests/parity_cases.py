@@ -374,6 +374,37 @@ def check_two_particle_dfc_f64(nx=100, ny=260, D=20.0, steps=100):
     assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
 
 
+def check_coupled_mdf_f64(kernels, dsfac=1.0, nx=90, ny=64, D=14.0, n=44, steps=25, free=False):
+    """Two MDF disks 0.1 D apart at the surface (footprints sharing nodes) in the inflow
+    channel: the coupled iteration of Sec. 2.5.2 on the device against the oracle --
+    populations and velocity at the FP64 bar, marker forces, the trial-iteration count,
+    the joint residual and the final relaxation of every step.  dsfac scales the arc
+    lengths so that trials are rejected and omega halved; ``free`` releases both disks
+    (density ratios 1.5 and 1.25, gravity across the stream)."""
+    kw = dict(mdf_nmin=5, mdf_nmax=20, mdf_omega=5.0 if dsfac != 1.0 else 0.0)
+    if free:
+        kw.update(motion=W.FREE, gx=0.0, gy=-2e-4)
+    xc0, yc0 = 0.3 * nx, 0.5 * ny
+    b0 = cylinder_body(xc0, yc0 - 0.55 * D, D, n, kernels[0], W.MDF, rho_ratio=1.5, **kw)
+    b1 = cylinder_body(xc0 + 0.2 * D, yc0 + 0.55 * D, D, n, kernels[1], W.MDF, rho_ratio=1.25, **kw)
+    for b in (b0, b1):
+        b.ds *= dsfac
+    spec = channel_spec(nx, ny, collision=W.BGK, tau=0.7, storage=W.F64, u=0.03, bodies=[b0, b1])
+    g, c = gpu_case(spec), oracle_case(spec)
+    for _ in range(steps):
+        stepped(g, c, 1)
+        it_g = [g.mdf_info(b)[0] for b in range(2)]
+        assert it_g == [c.mdf_iterations(b) for b in range(2)]
+        assert it_g[0] == it_g[1]
+        for b in range(2):
+            assert g.mdf_relaxation(b) == c.mdf_omega_end(b)
+            np.testing.assert_allclose(g.mdf_info(b)[1], c.mdf_residual(b), rtol=1e-9, atol=1e-15)
+            np.testing.assert_allclose(g.marker_data(b)[:, 4:6], c.marker_data(b)[:, 4:6], rtol=1e-10, atol=1e-14)
+            np.testing.assert_allclose(g.body_state(b), c.body_state(b), rtol=1e-11, atol=1e-14)
+    assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
+    g.close()
+
+
 # ---------------------------------------------------------------- batching, checkpoints, errors
 def batch_specs(scale=1.0):
     s = lambda v: max(8, int(v * scale))  # noqa: E731

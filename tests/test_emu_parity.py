@@ -140,6 +140,13 @@ def test_free_body_f64(L, scheme):
     P.check_free_body_f64(scheme, 1, nx=24, ny=64, D=6.0, steps=4)
 
 
+@pytest.mark.parametrize("kernels,dsfac,free", [((W.HAT, W.PESKIN4), 1.0, False), ((W.PESKIN4, W.PESKIN4), 6.0, False),
+                                                 ((W.PESKIN4, W.HAT), 1.0, True)])
+def test_coupled_mdf_f64(L, kernels, dsfac, free):
+    full_only(L)
+    P.check_coupled_mdf_f64(kernels, dsfac=dsfac, nx=44, ny=34, D=8.0, n=26, steps=4, free=free)
+
+
 def test_two_particle_dfc_f64(L):
     full_only(L)
     P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3)

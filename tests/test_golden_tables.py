@@ -70,8 +70,13 @@ def test_wake_values_match_printed_gaps():
     is +19.60 % for DF and +12.30 % for DFC; Table V: -2.16 % and -13.78 % for the
     A arm of DF relative to the reference 276.61 / 231.41."""
     t5 = PS.paper_table5()
-    for sch, gap in (("DF", 19.60), ("DFC", 12.30)):
+    for sch, gap in (("DF", 19.60), ("MDF", 21.51), ("DFC", 12.30)):
         eh, none = t5[(sch, "B-2")][1], t5[(sch, "A")][1]
         assert 100.0 * (eh / none - 1.0) == pytest.approx(gap, abs=0.01), sch
+    # App. C, Sec. C.2: heavy spread |eh - none| / mean and light deficit (none - eh) / eh
+    for sch, spread, deficit in (("DF", 2.55, -16.39), ("MDF", 2.99, -17.71), ("DFC", 2.87, -10.95)):
+        (h_eh, l_eh), (h_no, l_no) = t5[(sch, "B-2")], t5[(sch, "A")]
+        assert 100.0 * abs(h_eh - h_no) / (0.5 * (h_eh + h_no)) == pytest.approx(spread, abs=0.01), sch
+        assert 100.0 * (l_no - l_eh) / l_eh == pytest.approx(deficit, abs=0.01), sch
     assert 100.0 * (t5[("DF", "A")][0] / 276.61 - 1.0) == pytest.approx(-2.16, abs=0.01)
     assert 100.0 * (t5[("DF", "A")][1] / 231.41 - 1.0) == pytest.approx(-13.78, abs=0.01)

@@ -119,6 +119,13 @@ def test_free_body_f64(scheme, internal_mass):
     P.check_free_body_f64(scheme, internal_mass)
 
 
+@pytest.mark.parametrize("kernels,dsfac,free", [((W.HAT, W.PESKIN4), 1.0, False), ((W.PESKIN4, W.PESKIN4), 1.0, False),
+                                                 ((W.PESKIN4, W.PESKIN4), 6.0, False), ((W.HAT, W.HAT), 14.0, False),
+                                                 ((W.PESKIN4, W.HAT), 1.0, True), ((W.PESKIN4, W.PESKIN4), 1.0, True)])
+def test_coupled_mdf_f64(kernels, dsfac, free):
+    P.check_coupled_mdf_f64(kernels, dsfac=dsfac, free=free)
+
+
 def test_two_particle_dfc_f64():
     P.check_two_particle_dfc_f64()
 
