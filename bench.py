@@ -323,6 +323,44 @@ def serving_report(L, n_requests=256, steps=2000, tick=100, budget_gb=64.0, seed
     return out
 
 
+def moving_report(L, torch, steps=400):
+    """Bodies whose markers move every step (footprint and node lists rebuilt on the
+    device each step, DFC lambda_k recomputed): one 1024x512 in-line oscillating
+    cylinder (D = 40, KC = 5, DFC, Peskin, FP32) and one 400x1600 channel with two
+    settling disks (D = 20, DFC, Peskin, FP32), each stepped alone.  Graph-replayed
+    microseconds per step, then the same steps launched one by one with events around
+    each launch for the IB share of the step."""
+    out = {}
+    peak, _ = read_peaks()
+    cases = [("osc-1024x512-dfc-p4-f32", W.oscillating_cylinder(storage=W.F32, kernel=W.PESKIN4, scheme=W.DFC)),
+             ("sed2-400x1600-dfc-p4-f32", W.sedimentation(two_particles=True, storage=W.F32, kernel=W.PESKIN4,
+                                                           scheme=W.DFC))]
+    for name, spec in cases:
+        lat = L.Lattice.from_spec(spec)
+        lat.step(20)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        lat.step(steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        lat.sync()
+        lat.set_timing(True)
+        lat.step(steps)
+        stages = lat.stage_timing()
+        lat.set_timing(False)
+        lat.close()
+        per = {k: 1e3 * v[0] / steps for k, v in stages.items()}
+        out[name] = {"us_per_step": 1e3 * ms / steps, "mlups": spec.nodes * steps / (ms / 1e3) / 1e6,
+                     "hbm_fraction": spec.nodes * steps / (ms / 1e3) * BYTES_PER_LU[spec.storage] / (peak * 1e9),
+                     "launch_breakdown_us_per_step": per,
+                     "ib_share": per["ib"] / max(1e-9, sum(per.values())), "steps": steps,
+                     "bodies": len(spec.bodies)}
+    return out
+
+
 def storage_report(L, torch, steps=20):
     """The same 36-lattice matrix with FP16 and FP64 shifted storage: graph-replayed
     steps timed with CUDA events, MLUPS and the fraction of the HBM bound at each
@@ -572,6 +610,12 @@ def main():
             single = single_case_report(L, torch)
         except Exception as exc:
             single = {"error": repr(exc)}
+    moving = None
+    if rank == 0 and args.serving_requests > 0 and not args.small:
+        try:
+            moving = moving_report(L, torch)
+        except Exception as exc:
+            moving = {"error": repr(exc)}
     storages = None
     if rank == 0 and args.serving_requests > 0 and not args.small:
         try:
@@ -620,6 +664,7 @@ def main():
             "clocks": clocks.summary(),
             "device_status": rc,
             "single_lattice": single,
+            "moving_body": moving,
             "other_storage": storages,
             "serving": serving,
         }
