@@ -990,8 +990,8 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
 }
 
 // IB-region segment lists of an overlap plan: footprints are built at the bodies'
-// (fixed) markers, the boxes read back and every kIbAlign-aligned 64-node segment of
-// their rows listed once per lattice.  Leaves overlap_ok false when a body is not fixed
+// (fixed) markers, the boxes read back and every segment of the list launch (the
+// two-per-lane scalar variant) in the kIbAlign-aligned regions listed once per lattice.  Leaves overlap_ok false when a body is not fixed
 // or has no footprint.
 // At most this many IB CTAs (bodies) for the overlap: each holds a whole SM that the
 // sweep beside it gives up (so all the sweep's CTAs run at once and its static job
@@ -1030,8 +1030,9 @@ int build_ib_lists(BatchPlan* P, int sms) {
                 if (cudaMemcpy(&B, &c->dbodies[b], sizeof(BodyDev), cudaMemcpyDeviceToHost) != cudaSuccess)
                     return check(cudaGetLastError());
                 if (B.nfp <= 0) return IBLBM_OK;
+                const int seg = sc_segment(grp.storage, SC_SCALAR2);   // the list launch's segment
                 for (int y = B.by0; y < B.by0 + B.bh; ++y)
-                    for (int x = 0; x < c->hc.nx; x += kIbAlign)
+                    for (int x = 0; x < c->hc.nx; x += seg)
                         if (in_ib_region(y, x, B.bx0, B.by0, B.bw, B.bh)) segs.insert({y, x});
             }
             for (auto& sg : segs) list.push_back(make_int4(ci, sg.first, sg.second, 0));

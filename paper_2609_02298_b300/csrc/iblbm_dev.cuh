@@ -154,6 +154,32 @@ __device__ __forceinline__ float ld1_sweep(const float* p) {
 #endif
 }
 
+// FP16 storage, two adjacent nodes per 32-bit word (the pair sweep): read-only load
+// with the same 256-byte L2 fetch as the FP32 sweep, the unpacking to FP32, and the
+// store of two correctly rounded values.
+__device__ __forceinline__ unsigned ld2h_sweep(const __half* p) {
+#ifdef IBLBM_EMULATE
+    unsigned v;
+    std::memcpy(&v, p, 4);
+    return v;
+#else
+    unsigned v;
+    asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#endif
+}
+__device__ __forceinline__ float2 unpack2h(unsigned v) {
+    __half2_raw r;
+    r.x = (unsigned short)(v & 0xffffu);
+    r.y = (unsigned short)(v >> 16);
+    return __half22float2(__half2(r));
+}
+__device__ __forceinline__ void st2h(__half* p, float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const __half2_raw r = h;
+    *reinterpret_cast<unsigned*>(p) = (unsigned)r.x | ((unsigned)r.y << 16);
+}
+
 __device__ __forceinline__ void st1(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v); }

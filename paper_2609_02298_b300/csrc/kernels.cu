@@ -8,6 +8,7 @@
 //                  before the IB stage, second half with Eq. A3 after it; advances
 //                  the step counters.
 #include <climits>
+#include <type_traits>
 
 #include "async_copy.cuh"
 #include "kernels.cuh"
@@ -352,6 +353,76 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
 }
 
+// FP16 storage, NP pairs of adjacent nodes per lane: a warp handles NP chunks of 64
+// nodes of a row, lane l the pair (x0, x0 + 1), x0 = xseg + 64 j + 2 l.  Each
+// population is one aligned 32-bit load of the source row's pair at x0 (two nodes, half
+// the load instructions of one node per lane); the pull from x - 1 or x + 1 takes one
+// half from the neighbouring lane's word (warp shuffle) and the edge lanes load the
+// missing word.  Nodes are unpacked, collided and rounded exactly as in sc_row_scalar,
+// so the results are bit for bit those of the one-node-per-lane sweep.
+template <int KIND, int NP>
+__device__ __forceinline__ void sc_row_pair(const ScCase<__half>& K, int y, int xseg, int lane) {
+    using R = float;
+    const CaseDev& C = *K.C;
+    const __half* __restrict__ src = K.src;
+    __half* __restrict__ dst = K.dst;
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
+    if (y == 0 || y == ny - 1) return;
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 64 * NP);
+    const int row = y * pitch;
+    bool unstable = false;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const int x0 = xseg + 64 * j + 2 * lane;
+        const bool inrow = x0 < pitch;   // the pair lies in the padded row (pitch is even)
+        R s0[9], s1[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const __half* sr = src + (row + i * plane - ey(i) * pitch);   // source row of population i
+            const unsigned a = inrow ? ld2h_sweep(sr + x0) : 0u;
+            unsigned v;
+            if (ex(i) == 0) {
+                v = a;
+            } else if (ex(i) == 1) {        // the pair pulls from x0 - 1, x0
+                unsigned p = __shfl_up_sync(0xffffffffu, a, 1);
+                if (lane == 0) p = (inrow && x0 >= 2) ? ld2h_sweep(sr + x0 - 2) : 0u;
+                v = __byte_perm(p, a, 0x5432);
+            } else {                        // from x0 + 1, x0 + 2
+                unsigned q = __shfl_down_sync(0xffffffffu, a, 1);
+                if (lane == 31) q = (x0 + 2 < pitch) ? ld2h_sweep(sr + x0 + 2) : 0u;
+                v = __byte_perm(a, q, 0x5432);
+            }
+            const float2 f = unpack2h(v);
+            s0[i] = f.x;
+            s1[i] = f.y;
+        }
+        const bool w0 = x0 >= 1 && x0 < nx - 1, w1 = x0 + 1 < nx - 1;
+        if (w0) {
+            R Fx = K.gfx, Fy = K.gfy;
+            const bool forced = (ib && add_ib<R>(C, x0, y, s0, Fx, Fy)) || K.has_force;
+            const R rho = forced ? collide<R, KIND>(K.P, s0, Fx, Fy) : collide<R, KIND, false>(K.P, s0, R(0), R(0));
+            unstable |= bad_density(rho);
+        }
+        if (w1) {
+            R Fx = K.gfx, Fy = K.gfy;
+            const bool forced = (ib && add_ib<R>(C, x0 + 1, y, s1, Fx, Fy)) || K.has_force;
+            const R rho = forced ? collide<R, KIND>(K.P, s1, Fx, Fy) : collide<R, KIND, false>(K.P, s1, R(0), R(0));
+            unstable |= bad_density(rho);
+        }
+        __half* d = dst + (row + x0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (w0 && w1) {
+                st2h(d + i * plane, s0[i], s1[i]);
+            } else {
+                if (w0) st1(d + i * plane, s0[i]);
+                if (w1) st1(d + i * plane + 1, s1[i]);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+}
+
 template <class S, int KIND, int NPT> struct ScScalarMinBlocks { static constexpr int value = 4; };
 template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { static constexpr int value = 2; };
 
@@ -362,9 +433,20 @@ template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { stati
 // slower: the counter's atomics serialise.)  All CTAs of a launch must be resident
 // together for the split to balance, which the host arranges when the IB stage runs
 // beside the sweep (the grid leaves its SMs free).
+// Row segment of the scalar variants: NPT nodes per lane, or NPT adjacent pairs per lane
+// for FP16 storage (sc_row_pair).
+template <class S, int NPT> struct ScSeg { static constexpr int value = 32 * NPT; };
+template <int NPT> struct ScSeg<__half, NPT> { static constexpr int value = 64 * NPT; };
+template <class S, int KIND, int NPT>
+__device__ __forceinline__ void sc_row_nodes(const ScCase<S>& K, int y, int xseg, int lane) {
+    if constexpr (std::is_same<S, __half>::value) sc_row_pair<KIND, NPT>(K, y, xseg, lane);
+    else sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
+}
+
 template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
+    constexpr int kSegW = ScSeg<S, NPT>::value;
     if (L.pdl & PDL_TRIGGER) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -379,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
                 K.load(L.cases[e.x]);
                 cur = e.x;
             }
-            sc_row_scalar<S, KIND, NPT>(K, e.y, e.z, lane);
+            sc_row_nodes<S, KIND, NPT>(K, e.y, e.z, lane);
             continue;
         }
         if (job >= c_hi || job < c_lo) {
@@ -391,13 +473,13 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
             c_lo = L.job_off[lo];
             c_hi = L.job_off[lo + 1];
             K.load(L.cases[lo]);
-            nseg = (K.nx + 32 * NPT - 1) / (32 * NPT);
+            nseg = (K.nx + kSegW - 1) / kSegW;
         }
         const int local = (int)(job - c_lo);   // < ny * nseg
         const int y = local / nseg;
-        const int xseg = (local - y * nseg) * 32 * NPT;
+        const int xseg = (local - y * nseg) * kSegW;
         if (L.phase == SC_SKIP_IB && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
-        sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
+        sc_row_nodes<S, KIND, NPT>(K, y, xseg, lane);
     }
     if (L.pdl & PDL_DEPENDENT) pdl_wait();
 }
@@ -2134,7 +2216,8 @@ int sc_segment(int storage, int variant) {
     const int V = storage == ST_F64 ? 2 : (storage == ST_F32 ? 4 : 8);
     if (variant == SC_BULK)
         return storage == ST_F64 ? BulkGeom<double>::TW : (storage == ST_F32 ? BulkGeom<float>::TW : BulkGeom<__half>::TW);
-    return variant == SC_SCALAR ? 32 : (variant == SC_SCALAR2 ? 64 : 32 * V);
+    const int pair = storage == ST_F16 ? 2 : 1;   // FP16 scalar variants take adjacent node pairs
+    return variant == SC_SCALAR ? 32 * pair : (variant == SC_SCALAR2 ? 64 * pair : 32 * V);
 }
 
 bool sc_variant_ok(int variant, const void* f0, const void* f1) {

@@ -20,9 +20,9 @@ struct BodyRef {
 // node outside the IB regions (SC_SKIP_IB, swept while the IB stage runs); the IB
 // regions as an explicit segment list (SC_LIST).  The IB region of a body is its
 // footprint box's rows, widened in x to multiples of kIbAlign nodes, so that every
-// 32- or 64-node segment lies wholly inside or wholly outside it.
+// segment of a scalar variant (32, 64 or 128 nodes) lies wholly inside or outside it.
 enum { SC_ALL = 0, SC_SKIP_IB = 1, SC_LIST = 2 };
-constexpr int kIbAlign = 64;
+constexpr int kIbAlign = 128;
 // Programmatic dependent launch: PDL_TRIGGER, the kernel lets the next launch of its
 // stream begin as soon as all its CTAs run; PDL_DEPENDENT, the launch may begin before
 // the previous one ends and waits for it (griddepcontrol.wait) before it exits.

@@ -97,6 +97,13 @@ inline T __shfl_sync(unsigned, T v, int src) {
     return emu_from_bits<T>(emu::exchange(emu_to_bits(v), src & 31));
 }
 inline int __any_sync(unsigned, int pred) { return emu::any(pred); }
+// bytes of {y, x} (x the low word) picked by the four selector nibbles of s
+inline unsigned __byte_perm(unsigned x, unsigned y, unsigned s) {
+    const unsigned long long v = ((unsigned long long)y << 32) | x;
+    unsigned r = 0;
+    for (int k = 0; k < 4; ++k) r |= (unsigned)((v >> (8 * ((s >> (4 * k)) & 7u))) & 0xffu) << (8 * k);
+    return r;
+}
 inline void __syncwarp(unsigned = 0xffffffffu) { emu::any(0); }
 
 inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }

@@ -124,8 +124,11 @@ def test_free_body_f64(scheme, internal_mass):
                                                  ((W.PESKIN4, W.HAT), 1.0, True), ((W.PESKIN4, W.PESKIN4), 1.0, True)])
 def test_coupled_mdf_f64(kernels, dsfac, free):
     # scaled arc lengths exist to make trials be rejected; a few steps show that (the
-    # scaled forces would not give a stable flow for long)
-    P.check_coupled_mdf_f64(kernels, dsfac=dsfac, free=free, steps=25 if dsfac == 1.0 else 3)
+    # scaled forces would not give a stable flow for long).  Free MDF disks at these
+    # density ratios and this small size go unstable after a few tens of steps in the
+    # oracle as well (explicit coupling): eight steps, as for the single free MDF body.
+    steps = 3 if dsfac != 1.0 else (8 if free else 25)
+    P.check_coupled_mdf_f64(kernels, dsfac=dsfac, free=free, steps=steps)
 
 
 def test_two_particle_dfc_f64():
