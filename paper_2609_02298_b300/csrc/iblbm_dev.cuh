@@ -271,9 +271,84 @@ __device__ __forceinline__ void to_raw(R& c0, R& c1, R& c2, R u) {
 // Returns rho for the stability check.
 // KIND >= 0 fixes the operator at compile time (specialised kernels); -1 reads it from P.
 // FORCED = false drops every force term (nodes with F = 0 exactly), saving issue slots.
+
+template <class R, bool FORCED>
+__device__ __forceinline__ R collide_cm(const CollParams<R>& P, R (&s)[9], R Fx, R Fy) {
+    // Central-moment MRT (Eq. 5) on the deviation from rest.  With k(f) the
+    // central moments about u and f = w + s:
+    //   s* = T^-1 [ (I - L) k(s) + L (k_eq - k(w)) + (I - L/2) R ],
+    // where k(w) are the central moments of the rest weights (closed form).
+    // Raw moments use the tensor-product structure of D2Q9 (velocity
+    // components in {-1, 0, 1}); central moments follow by 1-D binomial shifts.
+    // Population index by (cx, cy): row cy=0 -> (3, 0, 1), cy=1 -> (6, 2, 5), cy=-1 -> (7, 4, 8).
+    R m[3][3];   // m[p][q] = sum s cx^p cy^q
+    {
+        R a0 = s[3] + s[0] + s[1], b0 = s[1] - s[3], c0 = s[1] + s[3];
+        R a1 = s[6] + s[2] + s[5], b1 = s[5] - s[6], c1 = s[5] + s[6];
+        R a2 = s[7] + s[4] + s[8], b2 = s[8] - s[7], c2 = s[8] + s[7];   // cy = -1
+        m[0][0] = a0 + a1 + a2; m[0][1] = a1 - a2; m[0][2] = a1 + a2;
+        m[1][0] = b0 + b1 + b2; m[1][1] = b1 - b2; m[1][2] = b1 + b2;
+        m[2][0] = c0 + c1 + c2; m[2][1] = c1 - c2; m[2][2] = c1 + c2;
+    }
+    // density and momentum are among these raw moments (m00 = drho, m10 = j_x, m01 = j_y)
+    const R drho = m[0][0];
+    const R rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    const R ux = (FORCED ? m[1][0] + R(0.5) * Fx : m[1][0]) * inv;   // Eq. 4
+    const R uy = (FORCED ? m[0][1] + R(0.5) * Fy : m[0][1]) * inv;
+    const R uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) to_central(m[0][q], m[1][q], m[2][q], ux);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) to_central(m[p][0], m[p][1], m[p][2], uy);
+    const R cs2 = R(1) / R(3), cs4 = R(1) / R(9);
+    const R ux2 = ux * ux, uy2 = uy * uy;
+    const R w = P.omega;
+    // second order: k20, k02, k11 relax with omega
+    R k20 = (R(1) - w) * m[2][0] + w * (drho * cs2 - ux2);
+    R k02 = (R(1) - w) * m[0][2] + w * (drho * cs2 - uy2);
+    R k11 = (R(1) - w) * m[1][1] + w * (-ux * uy);
+    // third order: k21, k12 relax with s_q, source cs2 F
+    R k21 = (R(1) - P.sq) * m[2][1] + P.sq * (uy * (cs2 + ux2));
+    R k12 = (R(1) - P.sq) * m[1][2] + P.sq * (ux * (cs2 + uy2));
+    if (FORCED) {
+        k21 += (R(1) - R(0.5) * P.sq) * cs2 * Fy;
+        k12 += (R(1) - R(0.5) * P.sq) * cs2 * Fx;
+    }
+    // fourth order: k22 relaxes with s_e
+    R k22 = (R(1) - P.se) * m[2][2] + P.se * (drho * cs4 - cs2 * uu - ux2 * uy2);
+    // conserved k00, and k10/k01 carry the full source (I - 0/2) R = F
+    if (FORCED) {
+        m[1][0] += Fx;
+        m[0][1] += Fy;
+    }
+    m[2][0] = k20; m[0][2] = k02; m[1][1] = k11; m[2][1] = k21; m[1][2] = k12; m[2][2] = k22;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) to_raw(m[p][0], m[p][1], m[p][2], uy);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) to_raw(m[0][q], m[1][q], m[2][q], ux);
+    // raw moments -> populations: g_q(0) = m0q - m2q, g_q(+1) = (m1q + m2q)/2, g_q(-1) = (m2q - m1q)/2
+    R g[3][3];   // g[cxi][q], cxi: 0 -> cx=0, 1 -> cx=+1, 2 -> cx=-1
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        g[0][q] = m[0][q] - m[2][q];
+        g[1][q] = R(0.5) * (m[1][q] + m[2][q]);
+        g[2][q] = R(0.5) * (m[2][q] - m[1][q]);
+    }
+    // s(cx, cy) = h(cy) over q: cy=0 -> g0 - g2, cy=+1 -> (g1 + g2)/2, cy=-1 -> (g2 - g1)/2
+    auto h0 = [&](int c) { return g[c][0] - g[c][2]; };
+    auto hp = [&](int c) { return R(0.5) * (g[c][1] + g[c][2]); };
+    auto hm = [&](int c) { return R(0.5) * (g[c][2] - g[c][1]); };
+    s[0] = h0(0); s[1] = h0(1); s[3] = h0(2);
+    s[2] = hp(0); s[5] = hp(1); s[6] = hp(2);
+    s[4] = hm(0); s[8] = hm(1); s[7] = hm(2);
+    return rho;
+}
+
 template <class R, int KIND = -1, bool FORCED = true>
 __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R Fy) {
     const int kind = KIND >= 0 ? KIND : P.kind;
+    if (kind == COL_CM) return collide_cm<R, FORCED>(P, s, Fx, Fy);
     R drho = R(0), jx = R(0), jy = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -361,69 +436,9 @@ __device__ __forceinline__ R collide(const CollParams<R>& P, R (&s)[9], R Fx, R 
         for (int i = 0; i < 9; ++i) s[i] = out[i];
         return rho;
     }
-    // Central-moment MRT (Eq. 5) on the deviation from rest.  With k(f) the
-    // central moments about u and f = w + s:
-    //   s* = T^-1 [ (I - L) k(s) + L (k_eq - k(w)) + (I - L/2) R ],
-    // where k(w) are the central moments of the rest weights (closed form).
-    // Raw moments use the tensor-product structure of D2Q9 (velocity
-    // components in {-1, 0, 1}); central moments follow by 1-D binomial shifts.
-    // Population index by (cx, cy): row cy=0 -> (3, 0, 1), cy=1 -> (6, 2, 5), cy=-1 -> (7, 4, 8).
-    R m[3][3];   // m[p][q] = sum s cx^p cy^q
-    {
-        R a0 = s[3] + s[0] + s[1], b0 = s[1] - s[3], c0 = s[1] + s[3];
-        R a1 = s[6] + s[2] + s[5], b1 = s[5] - s[6], c1 = s[5] + s[6];
-        R a2 = s[7] + s[4] + s[8], b2 = s[8] - s[7], c2 = s[8] + s[7];   // cy = -1
-        m[0][0] = a0 + a1 + a2; m[0][1] = a1 - a2; m[0][2] = a1 + a2;
-        m[1][0] = b0 + b1 + b2; m[1][1] = b1 - b2; m[1][2] = b1 + b2;
-        m[2][0] = c0 + c1 + c2; m[2][1] = c1 - c2; m[2][2] = c1 + c2;
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) to_central(m[0][q], m[1][q], m[2][q], ux);
-#pragma unroll
-    for (int p = 0; p < 3; ++p) to_central(m[p][0], m[p][1], m[p][2], uy);
-    const R cs2 = R(1) / R(3), cs4 = R(1) / R(9);
-    const R ux2 = ux * ux, uy2 = uy * uy;
-    const R w = P.omega;
-    // second order: k20, k02, k11 relax with omega
-    R k20 = (R(1) - w) * m[2][0] + w * (drho * cs2 - ux2);
-    R k02 = (R(1) - w) * m[0][2] + w * (drho * cs2 - uy2);
-    R k11 = (R(1) - w) * m[1][1] + w * (-ux * uy);
-    // third order: k21, k12 relax with s_q, source cs2 F
-    R k21 = (R(1) - P.sq) * m[2][1] + P.sq * (uy * (cs2 + ux2));
-    R k12 = (R(1) - P.sq) * m[1][2] + P.sq * (ux * (cs2 + uy2));
-    if (FORCED) {
-        k21 += (R(1) - R(0.5) * P.sq) * cs2 * Fy;
-        k12 += (R(1) - R(0.5) * P.sq) * cs2 * Fx;
-    }
-    // fourth order: k22 relaxes with s_e
-    R k22 = (R(1) - P.se) * m[2][2] + P.se * (drho * cs4 - cs2 * uu - ux2 * uy2);
-    // conserved k00, and k10/k01 carry the full source (I - 0/2) R = F
-    if (FORCED) {
-        m[1][0] += Fx;
-        m[0][1] += Fy;
-    }
-    m[2][0] = k20; m[0][2] = k02; m[1][1] = k11; m[2][1] = k21; m[1][2] = k12; m[2][2] = k22;
-#pragma unroll
-    for (int p = 0; p < 3; ++p) to_raw(m[p][0], m[p][1], m[p][2], uy);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) to_raw(m[0][q], m[1][q], m[2][q], ux);
-    // raw moments -> populations: g_q(0) = m0q - m2q, g_q(+1) = (m1q + m2q)/2, g_q(-1) = (m2q - m1q)/2
-    R g[3][3];   // g[cxi][q], cxi: 0 -> cx=0, 1 -> cx=+1, 2 -> cx=-1
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        g[0][q] = m[0][q] - m[2][q];
-        g[1][q] = R(0.5) * (m[1][q] + m[2][q]);
-        g[2][q] = R(0.5) * (m[2][q] - m[1][q]);
-    }
-    // s(cx, cy) = h(cy) over q: cy=0 -> g0 - g2, cy=+1 -> (g1 + g2)/2, cy=-1 -> (g2 - g1)/2
-    auto h0 = [&](int c) { return g[c][0] - g[c][2]; };
-    auto hp = [&](int c) { return R(0.5) * (g[c][1] + g[c][2]); };
-    auto hm = [&](int c) { return R(0.5) * (g[c][2] - g[c][1]); };
-    s[0] = h0(0); s[1] = h0(1); s[3] = h0(2);
-    s[2] = hp(0); s[5] = hp(1); s[6] = hp(2);
-    s[4] = hm(0); s[8] = hm(1); s[7] = hm(2);
     return rho;
 }
+
 
 // ---- domain conditions (Sec. 2.9) -------------------------------------------------------
 // Zou-He velocity closure written once for any side from its inward normal n and
