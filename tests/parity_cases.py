@@ -389,7 +389,9 @@ def check_coupled_mdf_f64(kernels, dsfac=1.0, nx=90, ny=64, D=14.0, n=44, steps=
     b1 = cylinder_body(xc0 + 0.2 * D, yc0 + 0.55 * D, D, n, kernels[1], W.MDF, rho_ratio=1.25, **kw)
     for b in (b0, b1):
         b.ds *= dsfac
-    spec = channel_spec(nx, ny, collision=W.BGK, tau=0.7, storage=W.F64, u=0.03, bodies=[b0, b1])
+    # free disks settle from rest in a quiescent channel (a stream hitting disks at rest
+    # kicks them harder than the explicit MDF coupling tolerates at this size)
+    spec = channel_spec(nx, ny, collision=W.BGK, tau=0.7, storage=W.F64, u=0.0 if free else 0.03, bodies=[b0, b1])
     g, c = gpu_case(spec), oracle_case(spec)
     for _ in range(steps):
         stepped(g, c, 1)
