@@ -490,12 +490,14 @@ def main():
                     help="lattice chunks of the end-to-end leg (copy-in of one overlaps the steps of the last)")
     ap.add_argument("--kernel-variant", type=int, default=-1,
                     help="fix the stream-collide variant (0-3) instead of tuning it (profiling)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"],
+                    help="population storage of the matrix (the bench line is FP32; others for profiling)")
     ap.add_argument("--single", action="store_true",
                     help="only the single-lattice report (one 2048x1024 lattice alone; profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     nx, ny = (256, 128) if args.small else (2048, 1024)
-    specs = matrix_specs(nx=nx, ny=ny) if not args.small else [
+    specs = matrix_specs(storage=W.STORAGES[args.storage], nx=nx, ny=ny) if not args.small else [
         W.fixed_cylinder_2048(re=re, storage=W.F32, collision=c, kernel=k, scheme=s, nx=nx, ny=ny,
                               diameter=16.0, nmark=50, mdf_iters=5)
         for re in (100.0, 200.0) for s in (W.DF, W.MDF, W.DFC) for k in (W.HAT, W.PESKIN4)

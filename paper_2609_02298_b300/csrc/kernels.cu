@@ -323,7 +323,11 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     S* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
-    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
+    // IB patch lookup and the force terms for the whole kIbAlign block holding the segment
+    // (uniform over the segment, and the same however a row is segmented)
+    const int xb = xseg / kIbAlign * kIbAlign;
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xb, xb + kIbAlign);
+    const bool forced = ib || K.has_force;
     // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
     int koff[9];
 #pragma unroll
@@ -339,12 +343,13 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
 #pragma unroll
             for (int i = 0; i < 9; ++i) s[i] = ld1_sweep(src + (a + koff[i]));
             R rho;
-            // the force terms are taken per node (a node with a spread force or a body
-            // force), so a node's arithmetic does not depend on how rows are segmented
-            R Fx = K.gfx, Fy = K.gfy;
-            const bool forced = (ib && add_ib<R>(C, x, y, s, Fx, Fy)) || K.has_force;
-            if (forced) rho = collide<R, KIND>(K.P, s, Fx, Fy);
-            else rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
+            if (forced) {
+                R Fx = K.gfx, Fy = K.gfy;
+                if (ib) add_ib<R>(C, x, y, s, Fx, Fy);
+                rho = collide<R, KIND>(K.P, s, Fx, Fy);
+            } else {
+                rho = collide<R, KIND, false>(K.P, s, R(0), R(0));
+            }
             unstable |= bad_density(rho);
 #pragma unroll
             for (int i = 0; i < 9; ++i) st1_sweep(dst + (a + i * plane), s[i]);
@@ -368,7 +373,9 @@ __device__ __forceinline__ void sc_row_pair(const ScCase<__half>& K, int y, int 
     __half* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
-    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 64 * NP);
+    const int xb = xseg / kIbAlign * kIbAlign;   // as in sc_row_scalar
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xb, xb + kIbAlign);
+    const bool forced = ib || K.has_force;
     const int row = y * pitch;
     bool unstable = false;
 #pragma unroll
@@ -397,17 +404,20 @@ __device__ __forceinline__ void sc_row_pair(const ScCase<__half>& K, int y, int 
             s1[i] = f.y;
         }
         const bool w0 = x0 >= 1 && x0 < nx - 1, w1 = x0 + 1 < nx - 1;
-        if (w0) {
-            R Fx = K.gfx, Fy = K.gfy;
-            const bool forced = (ib && add_ib<R>(C, x0, y, s0, Fx, Fy)) || K.has_force;
-            const R rho = forced ? collide<R, KIND>(K.P, s0, Fx, Fy) : collide<R, KIND, false>(K.P, s0, R(0), R(0));
-            unstable |= bad_density(rho);
-        }
-        if (w1) {
-            R Fx = K.gfx, Fy = K.gfy;
-            const bool forced = (ib && add_ib<R>(C, x0 + 1, y, s1, Fx, Fy)) || K.has_force;
-            const R rho = forced ? collide<R, KIND>(K.P, s1, Fx, Fy) : collide<R, KIND, false>(K.P, s1, R(0), R(0));
-            unstable |= bad_density(rho);
+        if (forced) {
+            if (w0) {
+                R Fx = K.gfx, Fy = K.gfy;
+                if (ib) add_ib<R>(C, x0, y, s0, Fx, Fy);
+                unstable |= bad_density(collide<R, KIND>(K.P, s0, Fx, Fy));
+            }
+            if (w1) {
+                R Fx = K.gfx, Fy = K.gfy;
+                if (ib) add_ib<R>(C, x0 + 1, y, s1, Fx, Fy);
+                unstable |= bad_density(collide<R, KIND>(K.P, s1, Fx, Fy));
+            }
+        } else {
+            if (w0) unstable |= bad_density(collide<R, KIND, false>(K.P, s0, R(0), R(0)));
+            if (w1) unstable |= bad_density(collide<R, KIND, false>(K.P, s1, R(0), R(0)));
         }
         __half* d = dst + (row + x0);
 #pragma unroll

@@ -201,6 +201,8 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
                 c["done"], c["error"], c["error_step"] = True, str(exc), steps
                 continue
             c["vy"].append(float(st[3]))
+            if c["scheme"] == "MDF":   # iterations of the sampled step (App. A.2 reports 5-7)
+                c.setdefault("mdf_iters", []).append(c["lat"].mdf_info(0)[0])
             if not c["done"]:
                 if abs(st[3]) > c["vmax"]:
                     c["vmax"], c["y_at_vmax"] = abs(st[3]), float(st[1])
@@ -215,6 +217,12 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
         status = c.get("error", 0)
         c.update(v_star=c.pop("vmax") / p["u_g"], u_g=p["u_g"], g=p["g"], tau=p["tau"], steps=steps,
                  status=status, vy_series=c.pop("vy"))
+        its = c.pop("mdf_iters", None)
+        if its:
+            its = np.array(its)
+            c.update(mdf_iters_mean=float(its.mean()), mdf_iters_median=float(np.median(its)),
+                     mdf_iters_5_7_frac=float(((its >= 5) & (its <= 7)).mean()),
+                     mdf_iters_at_nmax_frac=float((its >= 20).mean()))
         del c["done"]
         lat.close()
         out.append(c)
@@ -248,7 +256,8 @@ WAKE_COLLISION_CASES = [(W.DF, 1, W.TRT), (W.DF, 1, W.CMMRT)]
 WAKE_MDF_CASES = [(W.MDF, 1, W.BGK), (W.MDF, 0, W.BGK)]
 
 
-def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F32, steps=40000, sample=100):
+def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F32, steps=40000, sample=100,
+                         trace=False):
     """Sec. 2.9.4 in lattice units: Omega = [0, 10] x [-1, 1] on 4001 x 801 nodes
     (dx = 0.0025), d = 0.2 (D = 80, 251 markers), heavy disk (rho_r 1.5) at
     (0.8, -0.13), light disk (1.25) at (1.2, 0.13), gravity g_lat = 2.156e-4 along
@@ -291,6 +300,10 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
                 if c["scheme"] == "MDF":   # iterations, joint residual and relaxation of the last step
                     it, res, _ = c["lat"].mdf_info(0)
                     c["mdf"].append((it, res, c["lat"].mdf_relaxation(0)))
+                if trace:
+                    print(json.dumps({"case": c["scheme"] + "/" + c["internal_mass"], "step": done,
+                                      "re": [c["re"][0][-1], c["re"][1][-1]], "x": [c["x"][0][-1], c["x"][1][-1]],
+                                      "mdf": c["mdf"][-1] if c["mdf"] else None}), flush=True)
                 if max(c["x"][0][-1], c["x"][1][-1]) > 4000.0 - 3.0 * D:
                     c["stopped"], c["stop_step"] = True, done
             except Exception as exc:
@@ -344,6 +357,8 @@ def main():
     ap.add_argument("--rho", default="1.01,1.1,1.5", help="density ratios of the settling matrix")
     ap.add_argument("--wall-closure", type=int, default=0,
                     help="0: Zou-He walls; 1: zero-velocity walls by on-node bounce-back")
+    ap.add_argument("--wake-mdf-trace", type=int, default=0,
+                    help="run the coupled-MDF wake cases for this many steps, printing every sample")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
     ap.add_argument("--table-b4", action="store_true",
@@ -439,6 +454,12 @@ def main():
             print(json.dumps({k: v for k, v in r.items() if k not in ("cd_series", "re", "vy_series")}), flush=True)
         with open(args.out, "w") as fh:
             json.dump(rows, fh)
+        return
+    if args.wake_mdf_trace:
+        rows = run_wake_interaction(L, WAKE_MDF_CASES, storage=W.STORAGES[args.storage],
+                                    steps=args.wake_mdf_trace, trace=True)
+        for r in rows:
+            print(json.dumps({k: v for k, v in r.items() if k != "re"}), flush=True)
         return
     if args.wake:
         rows = run_wake_interaction(L, WAKE_CASES + WAKE_MDF_CASES, storage=W.STORAGES[args.storage])
