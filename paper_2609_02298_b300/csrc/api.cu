@@ -441,7 +441,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     }
     // MDF relaxation from the markers as given (Sec. 2.5.2: computed once at initialisation)
     if (scheme == SCH_MDF) {
-        IbLaunch setup{c->drefs + id, 1, 1};
+        IbLaunch setup{c->drefs + id, 1, 1, 0, 0};
         int rc = check(launch_ib(c->hc.storage, setup, w));
         if (rc) return rc;
     }
@@ -897,6 +897,9 @@ struct BatchPlan {
     // leaves free; the IB-region segments are swept after it (list_groups).
     bool overlap_ok = false;
     std::vector<ListGroup> list_groups;
+    // A lattice with several DFC bodies, one of them moving: W_total of Eq. 17 reads every
+    // DFC body's markers, so all bodies move in a launch of their own before the IB stage.
+    bool prepare_first = false;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_edges = nullptr;
     ~BatchPlan() {
@@ -959,10 +962,14 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
         if ((e = launch_edge_groups(P, P->side, nullptr, 1)) != cudaSuccess) return e;
         cudaEventRecord(P->ev_edges, P->side);
     }
+    if (P->prepare_first && P->nrefs_all > 0)
+        if ((e = timed_launch(timer, STAGE_IB, st, [&] { return launch_prepare(P->drefs_all, P->nrefs_all, st); })) !=
+            cudaSuccess)
+            return e;
     for (size_t k = 0; k < P->ib_groups.size(); ++k) {
         const auto& g = P->ib_groups[k];
         const bool last = k + 1 == P->ib_groups.size();
-        IbLaunch il{g.drefs, g.nrefs, 0, (overlap && last) ? (int)PDL_TRIGGER : 0};
+        IbLaunch il{g.drefs, g.nrefs, 0, (overlap && last) ? (int)PDL_TRIGGER : 0, P->prepare_first ? 1 : 0};
         if ((e = timed_launch(timer, STAGE_IB, st, [&] { return launch_ib(g.storage, il, st); })) != cudaSuccess)
             return e;
     }
@@ -1013,7 +1020,7 @@ int build_ib_lists(BatchPlan* P, int sms) {
                 g.grid_overlap[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
         }
     for (auto& g : P->ib_groups) {
-        IbLaunch setup{g.drefs, g.nrefs, 1, 0};
+        IbLaunch setup{g.drefs, g.nrefs, 1, 0, 0};
         int rc = check(launch_ib(g.storage, setup, P->st));
         if (rc) return rc;
     }
@@ -1238,6 +1245,16 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
     }
     *rc = check(cudaStreamSynchronize(P->st));
     if (*rc) { delete P; return nullptr; }
+    for (int i = 0; i < n; ++i) {
+        int ndfc = 0;
+        bool moving = false;
+        for (const auto& b : ctxs[i]->bodies)
+            if (b.scheme == SCH_DFC) {
+                ++ndfc;
+                moving = moving || b.motion != MOT_FIXED;
+            }
+        if (ndfc >= 2 && moving) P->prepare_first = true;
+    }
     *rc = build_ib_lists(P, sms);
     if (*rc) { delete P; return nullptr; }
     g_plans[key] = P;

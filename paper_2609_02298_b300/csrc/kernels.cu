@@ -1778,8 +1778,9 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     if (L.mode == 0 && C.n_mdf >= 2 && ref.b->scheme == SCH_MDF) {
         // coupled MDF: the CTA of the first MDF body steps all of them
         if (ref.index != C.mdf_lead) return;
-        for (int b = 0; b < C.nbodies; ++b)
-            if (C.bodies[b].scheme == SCH_MDF) body_prepare(C.bodies[b], shd);
+        if (!L.prepared)
+            for (int b = 0; b < C.nbodies; ++b)
+                if (C.bodies[b].scheme == SCH_MDF) body_prepare(C.bodies[b], shd);
         for (int b = 0; b < C.nbodies; ++b) {
             if (C.bodies[b].scheme != SCH_MDF) continue;
             const BodyRef rb{ref.c, &C.bodies[b], b, 0};
@@ -1799,7 +1800,7 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
         }
         return;
     }
-    if (L.mode == 0) body_prepare(*ref.b, shd);
+    if (L.mode == 0 && !L.prepared) body_prepare(*ref.b, shd);
     if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
     else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
     if (L.mode == 0) {
@@ -1889,6 +1890,13 @@ __device__ void body_finish(BodyDev& B) {
         S.vx = vnx; S.vy = vny; S.om = omn;
     }
     S.nstep = S.nstep + 1;
+}
+
+// Body motion of the step for every body (one CTA each), when an IB launch must not
+// move markers that another body's CTA reads.
+__global__ void __launch_bounds__(kThreads) prepare_kernel(BodyRef* refs, int n) {
+    __shared__ double sh[8];
+    if ((int)blockIdx.x < n) body_prepare(*refs[blockIdx.x].b, sh);
 }
 
 // Step counters of every case: the last launch of a step (the sweep reads the
@@ -2265,6 +2273,12 @@ cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {
     case ST_F32: return launch_ib_s<float>(L, st);
     default: return launch_ib_s<__half>(L, st);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(BodyRef* refs, int nrefs, cudaStream_t st) {
+    if (nrefs <= 0) return cudaSuccess;
+    IBLBM_LAUNCH(prepare_kernel, nrefs, kThreads, st, refs, nrefs);
     return cudaGetLastError();
 }
 

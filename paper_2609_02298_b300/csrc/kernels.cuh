@@ -44,6 +44,8 @@ struct IbLaunch {
     int mode;       // 0: body motion + IB stage + end-of-step body update; 1: set-up only
                     // (footprint and omega_MDF at the initial markers)
     int pdl;        // PDL_* flags (PDL_TRIGGER only)
+    int prepared;   // 1: body motion of the step already done by launch_prepare (another
+                    // body's IB CTA reads these markers: DFC W_total over several bodies)
 };
 
 // host-side launchers (kernels.cu)
@@ -80,6 +82,9 @@ struct EdgeLaunch {
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
+// body motion of the step (first half of Eq. 23, markers, U_d) for every body, one CTA
+// each, before an IB launch with IbLaunch.prepared = 1
+cudaError_t launch_prepare(BodyRef* refs, int nrefs, cudaStream_t st);
 // advances the step counter of every case (the last launch of a step)
 cudaError_t launch_counters(CaseDev** cases, int ncases, cudaStream_t st);
 cudaError_t launch_export(const CaseDev* hc, CaseDev* dc, double* out, int shifted, cudaStream_t st);

@@ -357,13 +357,15 @@ def check_free_body_f64(scheme, internal_mass, nx=64, ny=160, D=12.0, steps=150)
     np.testing.assert_array_equal(g.marker_stencils(0), c.marker_stencils(0))
 
 
-def check_two_particle_dfc_f64(nx=100, ny=260, D=20.0, steps=100):
-    """Two settling disks (rho_s/rho_f 1.5 below 1.01, 1.5 D apart), DFC with a
-    shared W_total, g and tau of the 400x1600 sedimentation workload."""
+def check_two_particle_dfc_f64(nx=100, ny=260, D=20.0, steps=100, spacing=1.5):
+    """Two settling disks (rho_s/rho_f 1.5 below 1.01, ``spacing`` D apart centre to
+    centre), DFC with a shared W_total, g and tau of the 400x1600 sedimentation
+    workload.  At spacing 1.1 the disks' footprints share nodes, so each disk's
+    lambda_k depends on where the other's markers are in the same step."""
     spec = W.sedimentation(two_particles=True, storage=W.F64, kernel=W.PESKIN4, scheme=W.DFC, nx=nx,
                            ny=ny, diameter=D, tau=0.65, g=8.33e-5)
     y0 = 0.5 * ny
-    for b, yc in zip(spec.bodies, (y0, y0 + 1.5 * D)):
+    for b, yc in zip(spec.bodies, (y0, y0 + spacing * D)):
         b.xy, b.ds = W.circle_markers(b.xc, yc, D, 31)
         b.yc = yc
     g, c = gpu_case(spec), oracle_case(spec)

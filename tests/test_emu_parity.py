@@ -152,6 +152,11 @@ def test_two_particle_dfc_f64(L):
     P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3)
 
 
+def test_two_particle_dfc_sharing_nodes_f64(L):
+    full_only(L)
+    P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3, spacing=1.1)
+
+
 def test_batch_equals_alone_bitwise(L):
     if L._test_variant not in (1, 3):
         pytest.skip("checked with the one-node-per-lane and bulk-staged variants")

@@ -135,6 +135,10 @@ def test_two_particle_dfc_f64():
     P.check_two_particle_dfc_f64()
 
 
+def test_two_particle_dfc_sharing_nodes_f64():
+    P.check_two_particle_dfc_f64(steps=40, spacing=1.1)
+
+
 def test_batch_equals_alone_bitwise():
     P.check_batch_equals_alone(L, P.batch_specs())
 
