@@ -520,12 +520,14 @@ def main():
 
     import paper_2609_02298_b300 as L
     L.use_torch_allocator()
-    if args.single:
-        print(json.dumps(single_case_report(L, torch, steps=4 * args.steps, only_large=True)), flush=True)
-        return
     if args.kernel_variant >= 0:
         for col in (W.BGK, W.TRT, W.CMMRT, W.STREAM_ONLY):
             L.set_kernel_variant(specs[0].storage, col, args.kernel_variant)
+    if args.single:
+        out = single_case_report(L, torch, steps=4 * args.steps, only_large=True)
+        out["kernel_variant_bgk_f32"] = L.kernel_variant(W.F32, W.BGK)
+        print(json.dumps(out), flush=True)
+        return
     lats = [L.Lattice.from_spec(s) for s in specs]
     nodes = sum(s.nodes for s in specs)
     storage = specs[0].storage

@@ -192,7 +192,7 @@ bool valid_bc(const int* bc) {
 }
 
 int stencil_ok(int S, int nx, int ny, double X, double Y) {
-    if (!std::isfinite(X) || !std::isfinite(Y)) return 0;
+    if (!(X >= 0.0 && X < (double)nx && Y >= 0.0 && Y < (double)ny)) return 0;   // before int conversion
     const int i0 = (int)std::floor(X) - (S == 4 ? 1 : 0), j0 = (int)std::floor(Y) - (S == 4 ? 1 : 0);
     return i0 >= 0 && j0 >= 0 && i0 + S <= nx && j0 + S <= ny;
 }
@@ -1221,6 +1221,17 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        // the one- and two-node-per-lane sweeps can run beside the IB stage: keep the fastest
+        // of them unless another variant is clearly faster on its own
+        int best_phased = -1;
+        for (int v = 0; v < SC_VARIANTS; ++v)
+            if (sc_variant_phased(v) && g.ok[v] &&
+                (best_phased < 0 || g_variant_ms[g.storage][g.collision][g.size_class][v] <
+                                        g_variant_ms[g.storage][g.collision][g.size_class][best_phased]))
+                best_phased = v;
+        if (best_phased >= 0 && !sc_variant_phased(best) &&
+            g_variant_ms[g.storage][g.collision][g.size_class][best_phased] < 1.1 * best_ms)
+            best = best_phased;
         g_variant[g.storage][g.collision][g.size_class] = best;
     }
     // edge launch overlapped with the IB stage when no footprint can reach a lattice

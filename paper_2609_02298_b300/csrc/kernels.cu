@@ -920,8 +920,14 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, err = 0;
     for (int k = tid; k < n; k += kIbThreads) {
         const double X = B.X[k], Y = B.Y[k];
+        // range first, in FP64: a diverged body can put markers at coordinates whose
+        // conversion to int would overflow (NaN fails these comparisons too)
+        if (!(X >= 0.0 && X < (double)C.nx && Y >= 0.0 && Y < (double)C.ny)) {
+            err = 1;
+            continue;
+        }
         const int i0 = (int)floor(X) - (Sx == 4 ? 1 : 0), j0 = (int)floor(Y) - (Sx == 4 ? 1 : 0);
-        if (!(X == X) || !(Y == Y) || i0 < 0 || j0 < 0 || i0 + Sx > C.nx || j0 + Sx > C.ny) err = 1;
+        if (i0 < 0 || j0 < 0 || i0 + Sx > C.nx || j0 + Sx > C.ny) err = 1;
         B.ij[2 * k] = i0;
         B.ij[2 * k + 1] = j0;
         for (int a = 0; a < Sx; ++a) {
@@ -2007,6 +2013,10 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const CaseDev* __res
     int bad = 0;
     for (int k = tid; k < n; k += kDiagThreads) {
         const double X = B.X[k], Y = B.Y[k], Udx = B.Udx[k], Udy = B.Udy[k];
+        if (!(X >= 0.0 && X < (double)C.nx && Y >= 0.0 && Y < (double)C.ny)) {   // before any int conversion
+            bad = 1;
+            continue;
+        }
         const int b0 = (int)floor(X), c0 = (int)floor(Y);
         const int i0 = b0 - (kern == K_HAT ? 0 : 1), j0 = c0 - (kern == K_HAT ? 0 : 1);
         if (!(X == X) || !(Y == Y) || i0 < 0 || j0 < 0 || i0 + SW > C.nx || j0 + SW > C.ny || b0 < 0 || c0 < 0 ||
@@ -2082,8 +2092,12 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const CaseDev* __res
     const double ri = B.radius - kappa;
     if (ri > 0.0) {
         const double rr = __dmul_rn(ri, ri);
-        const int x0 = max(0, (int)floor(xc - ri)), x1 = min(C.nx - 1, (int)ceil(xc + ri));
-        const int y0 = max(0, (int)floor(yc - ri)), y1 = min(C.ny - 1, (int)ceil(yc + ri));
+        // clamp to the lattice in FP64 before converting (a diverged body may be anywhere)
+        const double fx0 = fmax(0.0, floor(xc - ri)), fx1 = fmin((double)(C.nx - 1), ceil(xc + ri));
+        const double fy0 = fmax(0.0, floor(yc - ri)), fy1 = fmin((double)(C.ny - 1), ceil(yc + ri));
+        const bool inside = fx1 >= fx0 && fy1 >= fy0;   // false for NaN too
+        const int x0 = inside ? (int)fx0 : 0, x1 = inside ? (int)fx1 : -1;
+        const int y0 = inside ? (int)fy0 : 0, y1 = inside ? (int)fy1 : -1;
         const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
         if (bw > 0 && bh > 0) {
             for (long long q = tid; q < (long long)bw * bh; q += kDiagThreads) {

@@ -187,10 +187,9 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
             cases.append({"rho_ratio": rr, "kernel": KERNEL_NAMES[kern], "scheme": SCHEME_NAMES[sch],
                           "collision": COLLISION_NAMES[collision], "retraction": dr, "wall_closure": wall_closure,
                           "lat": lat, "p": p, "vmax": 0.0, "y_at_vmax": p["yc"], "done": False, "vy": []})
-    lats = [c["lat"] for c in cases]
     steps = 0
     while steps < max_steps and not all(c["done"] for c in cases):
-        L.step_batch(lats, sample)
+        L.step_batch([c["lat"] for c in cases if not c["done"]], sample)   # finished cases rest
         steps += sample
         for c in cases:
             if c["done"]:
@@ -212,8 +211,8 @@ def run_sedimentation(L, rho_ratios=(1.01, 1.1, 1.5), storage=W.F32, kernels=(W.
     for c in cases:
         lat = c.pop("lat")
         p = c.pop("p")
-        # a case that reached the bottom keeps being stepped with the others and
-        # eventually meets the wall; its record is the one taken when it arrived
+        # a case that reached the bottom (or failed) is not stepped further; its record
+        # is the one taken when it arrived
         status = c.get("error", 0)
         c.update(v_star=c.pop("vmax") / p["u_g"], u_g=p["u_g"], g=p["g"], tau=p["tau"], steps=steps,
                  status=status, vy_series=c.pop("vy"))
@@ -284,10 +283,9 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
         cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
                       "collision": COLLISION_NAMES[col],
                       "re": [[], []], "x": [[], []], "mdf": [], "stopped": False})
-    lats = [c["lat"] for c in cases]
     done = 0
     while done < steps and not all(c["stopped"] for c in cases):
-        L.step_batch(lats, sample)
+        L.step_batch([c["lat"] for c in cases if not c["stopped"]], sample)   # stopped cases rest
         done += sample
         for c in cases:
             if c["stopped"]:
