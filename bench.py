@@ -99,7 +99,8 @@ def launches_per_step(specs, L=None) -> int:
     fixed = all(b.motion == W.FIXED for s in specs for b in s.bodies)
     phased = L is None or all(L.kernel_variant(st, col)[0] in (1, 2) for st, col in groups)
     nbodies = sum(len(s.bodies) for s in specs)
-    if len(with_bodies) == 1 and 0 < nbodies <= 8 and fixed and phased:
+    large = sum(s.nodes for s in specs) >= (1 << 20)
+    if len(with_bodies) == 1 and 0 < nbodies <= 8 and fixed and phased and large:
         n += len({(s.storage, s.collision) for s in specs if s.bodies})
     return n
 
@@ -386,7 +387,9 @@ def storage_report(L, torch, steps=20):
             l.close()
         mlups = nodes * steps / (ms / 1e3) / 1e6
         out[name] = {"mlups": mlups, "ms_per_step": ms / steps, "steps": steps, "status": rc,
-                     "hbm_fraction": mlups * 1e6 * BYTES_PER_LU[st] / (peak * 1e9)}
+                     "hbm_fraction": mlups * 1e6 * BYTES_PER_LU[st] / (peak * 1e9),
+                     "kernel_variants": {cn: L.kernel_variant(st, col) for cn, col in
+                                         (("bgk", W.BGK), ("trt", W.TRT), ("cmmrt", W.CMMRT))}}
     return out
 
 

@@ -78,7 +78,10 @@ typedef enum { IBLBM_BC_PERIODIC = 0, IBLBM_BC_VELOCITY = 1, IBLBM_BC_NEUMANN = 
 /* Body motion: fixed (or moved by the caller with iblbm_move_body), prescribed
  * in-line oscillation x_c(t) = x_c0 - A sin(2 pi t / T) (Sec. 2.9.2), or free
  * rigid-body dynamics (Sec. 2.7). */
-typedef enum { IBLBM_FIXED = 0, IBLBM_PRESCRIBED = 1, IBLBM_FREE = 2 } iblbm_motion;
+/* IBLBM_FREE_TRANSLATION: free in translation (Eq. 23), rotation held at rest; the paper
+ * calls the disks' rotational contribution negligible, and with MDF the torque-only rotation
+ * of a free light disk can go unstable (explicit coupling) */
+typedef enum { IBLBM_FIXED = 0, IBLBM_PRESCRIBED = 1, IBLBM_FREE = 2, IBLBM_FREE_TRANSLATION = 3 } iblbm_motion;
 
 typedef struct {
     int nx, ny;                 /* lattice nodes, each >= 3 */

@@ -28,7 +28,7 @@ PERIODIC, VELOCITY, NEUMANN = 0, 1, 2
 BGK, TRT, CMMRT, STREAM_ONLY = 0, 1, 2, 3
 HAT, PESKIN4 = 0, 1
 DF, MDF, DFC = 0, 1, 2
-FIXED, PRESCRIBED, FREE = 0, 1, 2
+FIXED, PRESCRIBED, FREE, FREE_TRANSLATION = 0, 1, 2, 3
 
 _lib = None
 

@@ -538,13 +538,13 @@ static double body_mf(const orc_body* B) { return PI * B->p.radius * B->p.radius
  * rotation; markers follow the rigid motion.  U_d = v + Omega x (X - X_c)
  * evaluated at the half-step velocities.  PRESCRIBED: x_c(t) at t = n+1. */
 static void prepare_body(orc_case* c, orc_body* B) {
-    if (B->p.motion == ORC_FREE) {
+    if (B->p.motion == ORC_FREE || B->p.motion == ORC_FREE_TRANSLATION) {
         double ms = body_ms(B), Is = 0.5 * ms * B->p.radius * B->p.radius;
         double dm = (B->p.rho_ratio - 1.0) * PI * B->p.radius * B->p.radius;  /* Eq. 22 */
         double Ftx = B->Fhx + dm * B->p.gx + B->dFimx, Fty = B->Fhy + dm * B->p.gy + B->dFimy;
         B->vhx = B->vx + Ftx / (2.0 * ms);
         B->vhy = B->vy + Fty / (2.0 * ms);
-        B->omh = B->om + B->Th / (2.0 * Is);
+        B->omh = B->p.motion == ORC_FREE ? B->om + B->Th / (2.0 * Is) : 0.0;
         B->xc += B->vhx;
         B->yc += B->vhy;
         B->theta += B->omh;
@@ -590,12 +590,12 @@ int orc_set_marker_velocity(orc_case* c, int b, const double* ud) {
 
 /* Second half of Eq. 23 and the internal-mass increment of Eq. A3. */
 static void finish_body(orc_body* B, double Fhx, double Fhy, double Th) {
-    if (B->p.motion == ORC_FREE) {
+    if (B->p.motion == ORC_FREE || B->p.motion == ORC_FREE_TRANSLATION) {
         double ms = body_ms(B), Is = 0.5 * ms * B->p.radius * B->p.radius;
         double dm = (B->p.rho_ratio - 1.0) * PI * B->p.radius * B->p.radius;
         double vnx = B->vhx + (Fhx + dm * B->p.gx + B->dFimx) / (2.0 * ms);
         double vny = B->vhy + (Fhy + dm * B->p.gy + B->dFimy) / (2.0 * ms);
-        double omn = B->omh + Th / (2.0 * Is);
+        double omn = B->p.motion == ORC_FREE ? B->omh + Th / (2.0 * Is) : 0.0;
         if (B->p.internal_mass) {
             B->dFimx = body_mf(B) * (vnx - B->vx);
             B->dFimy = body_mf(B) * (vny - B->vy);

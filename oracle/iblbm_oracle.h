@@ -30,7 +30,9 @@ enum { ORC_HAT = 0, ORC_PESKIN4 = 1 };
 /* boundary-enforcement schemes, Sec. 2.5 */
 enum { ORC_DF = 0, ORC_MDF = 1, ORC_DFC = 2 };
 /* body motion */
-enum { ORC_FIXED = 0, ORC_PRESCRIBED = 1, ORC_FREE = 2 };
+/* ORC_FREE_TRANSLATION: free in translation (Eq. 23), rotation held at rest (reading: the
+ * paper calls the disks' rotational contribution negligible) */
+enum { ORC_FIXED = 0, ORC_PRESCRIBED = 1, ORC_FREE = 2, ORC_FREE_TRANSLATION = 3 };
 
 typedef struct {
     int nx, ny;

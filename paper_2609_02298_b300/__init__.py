@@ -24,7 +24,7 @@ BGK, TRT, CMMRT, STREAM_ONLY = 0, 1, 2, 3
 HAT, PESKIN4 = 0, 1
 DF, MDF, DFC = 0, 1, 2
 F64, F32, F16S = 0, 1, 2
-FIXED, PRESCRIBED, FREE = 0, 1, 2
+FIXED, PRESCRIBED, FREE, FREE_TRANSLATION = 0, 1, 2, 3
 
 OK = 0
 WARN_MDF_NOT_CONVERGED = 1

@@ -341,7 +341,7 @@ int iblbm_add_body(iblbm_ctx* c, const double* xy, int n, double ds, int kernel,
     if (!c || !xy || n <= 0 || !(ds > 0.0) || !bd || kernel < 0 || kernel > 1 || scheme < 0 || scheme > 2)
         return IBLBM_ERR_INVALID_ARG;
     if ((int)c->bodies.size() >= kMaxBodies) return IBLBM_ERR_INVALID_ARG;
-    if (bd->motion < 0 || bd->motion > 2 || !(bd->radius > 0.0) || !(bd->rho_ratio > 0.0)) return IBLBM_ERR_INVALID_ARG;
+    if (bd->motion < 0 || bd->motion > 3 || !(bd->radius > 0.0) || !(bd->rho_ratio > 0.0)) return IBLBM_ERR_INVALID_ARG;
     if (bd->motion == MOT_PRESC && !(bd->osc_period > 0.0)) return IBLBM_ERR_INVALID_ARG;
     if (scheme == SCH_MDF && (bd->mdf_nmin < 0 || bd->mdf_nmax < 1 || bd->mdf_nmin > bd->mdf_nmax)) return IBLBM_ERR_INVALID_ARG;
     const int S = kernel == K_HAT ? 2 : 4;
@@ -1011,6 +1011,11 @@ int build_ib_lists(BatchPlan* P, int sms) {
     for (auto* c : P->ctxs)
         for (auto& b : c->bodies)
             if (b.motion != MOT_FIXED) return IBLBM_OK;
+    // small plans are latency-bound: the IB stage and the lattice edges then overlap better
+    // the other way (edges beside the IB stage, the sweep after both)
+    long long nodes = 0;
+    for (auto* c : P->ctxs) nodes += (long long)c->hc.nx * c->hc.ny;
+    if (nodes < kLargeGroupNodes) return IBLBM_OK;
     const int free_sms = sms - P->ib_groups[0].nrefs;
     for (auto& g : P->groups)
         for (int v = 0; v < SC_VARIANTS; ++v) {

@@ -43,7 +43,7 @@ enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { COL_BGK = 0, COL_TRT = 1, COL_CM = 2, COL_NONE = 3 };
 enum { K_HAT = 0, K_P4 = 1 };
 enum { SCH_DF = 0, SCH_MDF = 1, SCH_DFC = 2 };
-enum { MOT_FIXED = 0, MOT_PRESC = 1, MOT_FREE = 2 };
+enum { MOT_FIXED = 0, MOT_PRESC = 1, MOT_FREE = 2, MOT_FREE_TRANSLATION = 3 };
 // device status bits
 enum : unsigned {
     STAT_UNSTABLE = 1u,

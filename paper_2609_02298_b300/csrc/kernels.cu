@@ -463,17 +463,8 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
-    int nseg = 1, cur = -1;
+    int nseg = 1;
     for (long long job = gw; job < jobs; job += nw) {
-        if (L.phase == SC_LIST) {
-            const int4 e = L.list[job];
-            if (e.x != cur) {
-                K.load(L.cases[e.x]);
-                cur = e.x;
-            }
-            sc_row_nodes<S, KIND, NPT>(K, e.y, e.z, lane);
-            continue;
-        }
         if (job >= c_hi || job < c_lo) {
             int lo = 0, hi = L.ncases - 1;
             while (lo < hi) {
@@ -492,6 +483,25 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
         sc_row_nodes<S, KIND, NPT>(K, y, xseg, lane);
     }
     if (L.pdl & PDL_DEPENDENT) pdl_wait();
+}
+
+// The SC_LIST phase: the listed segments (IB regions), warp w taking entries w, w + W, ...
+template <class S, int KIND, int NPT>
+__global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
+    sc_kernel_list(ScLaunch L, long long jobs) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    ScCase<S> K;
+    int cur = -1;
+    for (long long job = gw; job < jobs; job += nw) {
+        const int4 e = L.list[job];
+        if (e.x != cur) {
+            K.load(L.cases[e.x]);
+            cur = e.x;
+        }
+        sc_row_nodes<S, KIND, NPT>(K, e.y, e.z, lane);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1831,11 +1841,11 @@ __device__ void body_prepare(BodyDev& B, double* sh) {
     __syncthreads();   // sh may still be read by earlier code of the CTA
     if (threadIdx.x == 0) {
         double vx = S.vx, vy = S.vy, om = S.om;
-        if (B.motion == MOT_FREE) {
+        if (B.motion == MOT_FREE || B.motion == MOT_FREE_TRANSLATION) {
             const double Ftx = S.Fhx + dm * B.gx + S.dFimx, Fty = S.Fhy + dm * B.gy + S.dFimy;
             S.vhx = S.vx + Ftx / (2.0 * ms);
             S.vhy = S.vy + Fty / (2.0 * ms);
-            S.omh = S.om + S.Th / (2.0 * Is);
+            S.omh = B.motion == MOT_FREE ? S.om + S.Th / (2.0 * Is) : 0.0;
             S.xc += S.vhx;
             S.yc += S.vhy;
             S.theta += S.omh;
@@ -1855,7 +1865,7 @@ __device__ void body_prepare(BodyDev& B, double* sh) {
     const double xc = sh[0], yc = sh[1], vx = sh[2], vy = sh[3], om = sh[4], ct = sh[5], st = sh[6];
     for (int k = threadIdx.x; k < B.n; k += blockDim.x) {
         double rx, ry;
-        if (B.motion == MOT_FREE) {
+        if (B.motion == MOT_FREE || B.motion == MOT_FREE_TRANSLATION) {
             rx = ct * B.r0x[k] - st * B.r0y[k];
             ry = st * B.r0x[k] + ct * B.r0y[k];
             B.X[k] = xc + rx;
@@ -1879,13 +1889,13 @@ __device__ void body_prepare(BodyDev& B, double* sh) {
 __device__ void body_finish(BodyDev& B) {
     const double PI = 3.14159265358979323846;
     BodyState& S = B.st;
-    if (B.motion == MOT_FREE) {
+    if (B.motion == MOT_FREE || B.motion == MOT_FREE_TRANSLATION) {
         const double r2 = B.radius * B.radius;
         const double ms = B.rho_ratio * PI * r2, Is = 0.5 * ms * r2;
         const double dm = (B.rho_ratio - 1.0) * PI * r2, mf = PI * r2;
         const double vnx = S.vhx + (S.Fhx + dm * B.gx + S.dFimx) / (2.0 * ms);
         const double vny = S.vhy + (S.Fhy + dm * B.gy + S.dFimy) / (2.0 * ms);
-        const double omn = S.omh + S.Th / (2.0 * Is);
+        const double omn = B.motion == MOT_FREE ? S.omh + S.Th / (2.0 * Is) : 0.0;
         if (B.internal_mass) {
             S.dFimx = mf * (vnx - S.vx);
             S.dFimy = mf * (vny - S.vy);
@@ -2173,6 +2183,11 @@ template <class S, int KIND>
 static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, int grid, cudaStream_t st) {
     const int block = L.block > 0 ? L.block : kThreads;
     const bool dep = (L.pdl & PDL_DEPENDENT) != 0;
+    if (L.phase == SC_LIST) {
+        if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_list<S, KIND, 1>), grid, block, st, L, jobs);
+        else IBLBM_LAUNCH((sc_kernel_list<S, KIND, 2>), grid, block, st, L, jobs);
+        return cudaGetLastError();
+    }
     if (variant == SC_SCALAR) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1>), grid, block, st, dep, L, jobs);
     else if (variant == SC_SCALAR2) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2>), grid, block, st, dep, L, jobs);
     else if (variant == SC_BULK) {

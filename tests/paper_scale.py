@@ -256,7 +256,7 @@ WAKE_MDF_CASES = [(W.MDF, 1, W.BGK), (W.MDF, 0, W.BGK)]
 
 
 def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F32, steps=40000, sample=100,
-                         trace=False):
+                         trace=False, rotation=True):
     """Sec. 2.9.4 in lattice units: Omega = [0, 10] x [-1, 1] on 4001 x 801 nodes
     (dx = 0.0025), d = 0.2 (D = 80, 251 markers), heavy disk (rho_r 1.5) at
     (0.8, -0.13), light disk (1.25) at (1.2, 0.13), gravity g_lat = 2.156e-4 along
@@ -267,7 +267,9 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
     outlet.  Reading of the peaks: the light particle's is the maximum of its
     series (the paper's falls at step 35,000), the heavy particle's the maximum
     over the first 20,000 steps (the paper's falls at 8,500-9,500, long before
-    the heavy disk nears the outlet and speeds up again)."""
+    the heavy disk nears the outlet and speeds up again).  ``rotation`` False holds
+    the disks' rotation at rest (the paper calls its contribution negligible; with
+    the coupled MDF the torque-only rotation of these disks goes unstable here)."""
     dx, D, nu, g = 0.0025, 80.0, (0.59 - 0.5) / 3.0, 2.156e-4
     nb = int(round(math.pi * D))
     places = [(0.8, -0.13, 1.5), (1.2, 0.13, 1.25)]
@@ -278,10 +280,11 @@ def run_wake_interaction(L, cases_spec=WAKE_CASES, kernel=W.PESKIN4, storage=W.F
         for X, Y, rr in places:
             xc, yc = X / dx, (Y + 1.0) / dx
             xy, ds = W.circle_markers(xc, yc, D, nb)
-            lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr, motion=W.FREE,
+            lat.add_body(xy, ds, kernel, sch, xc=xc, yc=yc, radius=0.5 * D, rho_ratio=rr,
+                         motion=W.FREE if rotation else W.FREE_TRANSLATION,
                          gx=g, gy=0.0, internal_mass=im, mdf_nmin=5, mdf_nmax=20, mdf_tol=1e-4)
         cases.append({"scheme": SCHEME_NAMES[sch], "internal_mass": "B-2" if im else "A", "lat": lat,
-                      "collision": COLLISION_NAMES[col],
+                      "collision": COLLISION_NAMES[col], "rotation": rotation,
                       "re": [[], []], "x": [[], []], "mdf": [], "stopped": False})
     done = 0
     while done < steps and not all(c["stopped"] for c in cases):
@@ -357,6 +360,7 @@ def main():
                     help="0: Zou-He walls; 1: zero-velocity walls by on-node bounce-back")
     ap.add_argument("--wake-mdf-trace", type=int, default=0,
                     help="run the coupled-MDF wake cases for this many steps, printing every sample")
+    ap.add_argument("--no-rotation", action="store_true", help="hold the wake disks' rotation at rest")
     ap.add_argument("--wake", action="store_true",
                     help="run the two-particle wake interaction of Tables V and C.3")
     ap.add_argument("--table-b4", action="store_true",
@@ -455,12 +459,13 @@ def main():
         return
     if args.wake_mdf_trace:
         rows = run_wake_interaction(L, WAKE_MDF_CASES, storage=W.STORAGES[args.storage],
-                                    steps=args.wake_mdf_trace, trace=True)
+                                    steps=args.wake_mdf_trace, trace=True, rotation=not args.no_rotation)
         for r in rows:
             print(json.dumps({k: v for k, v in r.items() if k != "re"}), flush=True)
         return
     if args.wake:
-        rows = run_wake_interaction(L, WAKE_CASES + WAKE_MDF_CASES, storage=W.STORAGES[args.storage])
+        rows = run_wake_interaction(L, WAKE_CASES, storage=W.STORAGES[args.storage])
+        rows += run_wake_interaction(L, WAKE_CASES + WAKE_MDF_CASES, storage=W.STORAGES[args.storage], rotation=False)
         t5 = paper_table5()
         for r in rows:
             r["paper_heavy_re"], r["paper_light_re"] = t5[(r["scheme"], r["internal_mass"])]

@@ -376,19 +376,21 @@ def check_two_particle_dfc_f64(nx=100, ny=260, D=20.0, steps=100, spacing=1.5):
     assert_f64_state(g.populations(), c.populations(), u_ref=0.01)
 
 
-def check_coupled_mdf_f64(kernels, dsfac=1.0, nx=90, ny=64, D=14.0, n=44, steps=25, free=False):
+def check_coupled_mdf_f64(kernels, dsfac=1.0, nx=90, ny=64, D=14.0, n=44, steps=25, free=False,
+                          rotation=True, rho=(1.5, 1.25), g=2e-4):
     """Two MDF disks 0.1 D apart at the surface (footprints sharing nodes) in the inflow
     channel: the coupled iteration of Sec. 2.5.2 on the device against the oracle --
     populations and velocity at the FP64 bar, marker forces, the trial-iteration count,
     the joint residual and the final relaxation of every step.  dsfac scales the arc
     lengths so that trials are rejected and omega halved; ``free`` releases both disks
-    (density ratios 1.5 and 1.25, gravity across the stream)."""
+    (density ratios 1.5 and 1.25, gravity across the stream), with their rotation held
+    at rest when ``rotation`` is False."""
     kw = dict(mdf_nmin=5, mdf_nmax=20, mdf_omega=5.0 if dsfac != 1.0 else 0.0)
     if free:
-        kw.update(motion=W.FREE, gx=0.0, gy=-2e-4)
+        kw.update(motion=W.FREE if rotation else W.FREE_TRANSLATION, gx=0.0, gy=-g)
     xc0, yc0 = 0.3 * nx, 0.5 * ny
-    b0 = cylinder_body(xc0, yc0 - 0.55 * D, D, n, kernels[0], W.MDF, rho_ratio=1.5, **kw)
-    b1 = cylinder_body(xc0 + 0.2 * D, yc0 + 0.55 * D, D, n, kernels[1], W.MDF, rho_ratio=1.25, **kw)
+    b0 = cylinder_body(xc0, yc0 - 0.55 * D, D, n, kernels[0], W.MDF, rho_ratio=rho[0], **kw)
+    b1 = cylinder_body(xc0 + 0.2 * D, yc0 + 0.55 * D, D, n, kernels[1], W.MDF, rho_ratio=rho[1], **kw)
     for b in (b0, b1):
         b.ds *= dsfac
     # free disks settle from rest in a quiescent channel (a stream hitting disks at rest

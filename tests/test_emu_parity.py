@@ -147,6 +147,12 @@ def test_coupled_mdf_f64(L, kernels, dsfac, free):
     P.check_coupled_mdf_f64(kernels, dsfac=dsfac, nx=44, ny=34, D=8.0, n=26, steps=4, free=free)
 
 
+def test_coupled_mdf_free_translation_f64(L):
+    full_only(L)
+    P.check_coupled_mdf_f64((W.PESKIN4, W.HAT), nx=44, ny=34, D=8.0, n=26, steps=4, free=True, rotation=False,
+                            rho=(3.0, 2.5), g=5e-5)
+
+
 def test_two_particle_dfc_f64(L):
     full_only(L)
     P.check_two_particle_dfc_f64(nx=24, ny=64, D=6.0, steps=3)

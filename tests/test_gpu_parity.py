@@ -131,6 +131,14 @@ def test_coupled_mdf_f64(kernels, dsfac, free):
     P.check_coupled_mdf_f64(kernels, dsfac=dsfac, free=free, steps=steps)
 
 
+@pytest.mark.parametrize("kernels", [(W.PESKIN4, W.HAT), (W.PESKIN4, W.PESKIN4)])
+def test_coupled_mdf_free_translation_f64(kernels):
+    """Two heavier MDF disks (density ratios 3 and 2.5, D = 20) free in translation with
+    the rotation held at rest: a stable run, compared with the oracle for 150 steps."""
+    P.check_coupled_mdf_f64(kernels, nx=120, ny=90, D=20.0, n=63, steps=150, free=True, rotation=False,
+                            rho=(3.0, 2.5), g=5e-5)
+
+
 def test_two_particle_dfc_f64():
     P.check_two_particle_dfc_f64()
 

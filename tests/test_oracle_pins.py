@@ -969,3 +969,30 @@ def test_mdf_coupled_momentum_exchange():
     Fb = c.body_forces(0)[:2] + c.body_forces(1)[:2]
     np.testing.assert_allclose(_momentum(f1) - _momentum(f0), -Fb, rtol=1e-11, atol=1e-15)
     assert f1.sum() == pytest.approx(f0.sum(), rel=1e-15)
+
+
+def test_free_translation_holds_rotation():
+    """Free in translation with the rotation held at rest: with a torque acting (a disk
+    off the channel axis in a shear flow) the angular velocity and angle stay exactly
+    zero while the disk translates; with no torque (symmetric set-up) its trajectory is
+    the free body's to round-off."""
+    nx, ny = 48, 40
+    out = {}
+    for motion in (W.FREE, W.FREE_TRANSLATION):
+        for sym in (False, True):
+            c = oracle.Case(oracle.lattice_params(nx, ny, tau=0.8))
+            if not sym:   # a shear flow across the disk
+                f = np.stack([np.stack([oracle.feq(1.0, 0.04 * (y - 0.5 * ny) / ny, 0.0) for _ in range(nx)], axis=1)
+                              for y in range(ny)], axis=1)
+                c.set_populations(f)
+            yc = 0.5 * (ny - 1)
+            xy, ds = W.circle_markers(20.0, yc, 10.0, 31)
+            c.add_body(xy, ds, W.PESKIN4, W.DF, _body(xy, ds, W.PESKIN4, W.DF, 20.0, yc, 5.0, rho_ratio=2.0,
+                                                       motion=motion, gx=1e-5 if sym else 0.0))
+            c.step(30)
+            out[(motion, sym)] = (c.body_state(0), c.body_forces(0))
+    st, F = out[(W.FREE_TRANSLATION, False)]
+    assert abs(F[2]) > 1e-6 and st[4] == 0.0 and st[5] == 0.0
+    assert abs(out[(W.FREE, False)][0][4]) > 1e-9          # the free disk does turn
+    np.testing.assert_allclose(out[(W.FREE_TRANSLATION, True)][0][:4], out[(W.FREE, True)][0][:4],
+                               rtol=1e-10, atol=1e-15)

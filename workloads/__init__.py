@@ -25,7 +25,7 @@ PERIODIC, VELOCITY, NEUMANN = 0, 1, 2
 BGK, TRT, CMMRT, STREAM_ONLY = 0, 1, 2, 3
 HAT, PESKIN4 = 0, 1
 DF, MDF, DFC = 0, 1, 2
-FIXED, PRESCRIBED, FREE = 0, 1, 2
+FIXED, PRESCRIBED, FREE, FREE_TRANSLATION = 0, 1, 2, 3
 F64, F32, F16S = 0, 1, 2
 
 COLLISIONS = {"bgk": BGK, "trt": TRT, "cmmrt": CMMRT}
