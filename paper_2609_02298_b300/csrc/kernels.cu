@@ -920,6 +920,79 @@ __device__ __forceinline__ int block_max_i(int v, int* sh) {
     return r;
 }
 
+// Block-wide minimum of five ints: warp butterflies, then one warp over the 16 warp
+// results (two barriers instead of one per tree level).  sh holds 96 ints.
+__device__ __forceinline__ void block_min5(int (&v)[5], int* sh) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] = min(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sh[q * 16 + w] = v[q];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            int u = lane < kIbThreads / 32 ? sh[q * 16 + lane] : INT_MAX;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u = min(u, __shfl_xor_sync(0xffffffffu, u, o));
+            if (lane == 0) sh[80 + q] = u;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = sh[80 + q];
+}
+
+// Block-wide exclusive scan of two ints (warp scans, then one warp over the warp totals);
+// returns the totals.  sh holds 96 ints.
+__device__ __forceinline__ void block_exscan2(int& a, int& b, int& tot_a, int& tot_b, int* sh) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ua;
+            ib += ub;
+        }
+    }
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 31) {
+        sh[w] = ia;
+        sh[16 + w] = ib;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int xa = lane < kIbThreads / 32 ? sh[lane] : 0, xb = lane < kIbThreads / 32 ? sh[16 + lane] : 0;
+        int sa = xa, sb = xb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ua = __shfl_up_sync(0xffffffffu, sa, o), ub = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) {
+                sa += ua;
+                sb += ub;
+            }
+        }
+        if (lane < kIbThreads / 32) {
+            sh[32 + lane] = sa - xa;
+            sh[48 + lane] = sb - xb;
+        }
+        if (lane == kIbThreads / 32 - 1) {
+            sh[64] = sa;
+            sh[65] = sb;
+        }
+    }
+    __syncthreads();
+    a = sh[32 + w] + ia - a;
+    b = sh[48 + w] + ib - b;
+    tot_a = sh[64];
+    tot_b = sh[65];
+}
+
 // Footprint of a body: stencil origins and weights, bounding box, box-local
 // node -> slot map and a node -> marker CSR whose lists are sorted by marker
 // index (so every spread sums in ascending marker order, like Eq. 8 written out).
@@ -946,9 +1019,20 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         }
         mnx = min(mnx, i0); mny = min(mny, j0); mxx = max(mxx, i0); mxy = max(mxy, j0);
     }
-    const int e = block_max_i(err, shi);
-    const int bx0 = block_min_i(mnx, shi), by0 = block_min_i(mny, shi);
-    const int bx1 = block_max_i(mxx, shi) + Sx, by1 = block_max_i(mxy, shi) + Sx;
+    int red[5] = {-err, mnx, mny, mxx == INT_MIN ? INT_MAX : -mxx, mxy == INT_MIN ? INT_MAX : -mxy};
+    block_min5(red, shi);
+    const int e = -red[0];
+    const int bx0 = red[1], by0 = red[2];
+    if (e) {   // (the box below is meaningless then)
+        if (tid == 0) {
+            B.nfp = 0;
+            B.status |= STAT_MARKER_OUT;
+            atomicOr(const_cast<unsigned*>(&C.status), STAT_MARKER_OUT);
+        }
+        __syncthreads();
+        return false;
+    }
+    const int bx1 = -red[3] + Sx, by1 = -red[4] + Sx;
     const int bw = bx1 - bx0, bh = by1 - by0;
     if (e || (long long)bw * bh > B.box_cap) {
         if (tid == 0) {
@@ -977,23 +1061,8 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         nz += c > 0;
         cnt += c;
     }
-    int* sa = shi;
-    int* sb = shi + kIbThreads + 1;
-    sa[tid] = nz;
-    sb[tid] = cnt;
-    __syncthreads();
-    if (tid == 0) {
-        int a = 0, b = 0;
-        for (int t = 0; t < kIbThreads; ++t) {
-            const int ta = sa[t], tb = sb[t];
-            sa[t] = a; sb[t] = b;
-            a += ta; b += tb;
-        }
-        sa[kIbThreads] = a;
-        sb[kIbThreads] = b;
-    }
-    __syncthreads();
-    int slot = sa[tid], off = sb[tid];
+    int slot = nz, off = cnt, tot_nz = 0, tot_cnt = 0;
+    block_exscan2(slot, off, tot_nz, tot_cnt, shi);
     for (int q = beg; q < end; ++q) {
         const int c = B.node_map[q];
         if (c > 0) {
@@ -1006,9 +1075,9 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
             B.node_map[q] = -1;
         }
     }
-    const int nfp = sa[kIbThreads];
+    const int nfp = tot_nz;
     if (tid == 0) {
-        B.csr_off[nfp] = sb[kIbThreads];
+        B.csr_off[nfp] = tot_cnt;
         B.bx0 = bx0; B.by0 = by0; B.bw = bw; B.bh = bh; B.nfp = nfp;
     }
     for (int q = tid; q < nfp; q += kIbThreads) B.fill[q] = 0;
