@@ -525,6 +525,7 @@ int iblbm_move_body(iblbm_ctx* c, int id, const double* xy, const double uvw[3])
         b.st.om = uvw[2];
         b.ud_given = 0;
     }
+    b.ud_current = 0;   // U_d recomputed from the new state
     cudaMemcpy(&c->dbodies[id], &b, sizeof(BodyDev), cudaMemcpyHostToDevice);
     if (xy)
         for (int o = 0; o < (int)c->bodies.size(); ++o) {
@@ -551,8 +552,9 @@ int iblbm_set_marker_velocity(iblbm_ctx* c, int id, const double* ud) {
         cudaMemcpy(b.Udx, U.data(), 8 * (size_t)n, cudaMemcpyHostToDevice);
         cudaMemcpy(b.Udy, V.data(), 8 * (size_t)n, cudaMemcpyHostToDevice);
     }
-    const int flag = ud ? 1 : 0;
+    const int flag = ud ? 1 : 0, zero = 0;
     cudaMemcpy(&c->dbodies[id].ud_given, &flag, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(&c->dbodies[id].ud_current, &zero, sizeof(int), cudaMemcpyHostToDevice);
     return check(cudaGetLastError());
 }
 
@@ -746,6 +748,7 @@ int iblbm_restore(iblbm_ctx* c, const void* host, size_t n) {
         p += 24 * (size_t)B.hist_cap;
         B.cache_valid = 0;
         B.lam_valid = 0;
+        B.ud_current = 0;
         B.status = 0;
         B.t0 = h.steps - B.st.nstep;   // step at which the body joined the checkpointed run
         cudaMemcpyAsync(&c->dbodies[b], &B, sizeof(BodyDev), cudaMemcpyHostToDevice, w);

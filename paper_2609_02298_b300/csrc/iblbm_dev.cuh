@@ -102,6 +102,8 @@ struct BodyDev {
     // footprint: bounding box, box-local node -> slot map, node CSR over markers
     int bx0, by0, bw, bh, box_cap, nfp, nent, cache_valid, lam_valid;
     int ud_given;                 // FIXED: U_d set per marker by the caller, not v + omega x r
+    int ud_current;               // FIXED: U_d already holds v + omega x r (set on the device, cleared by
+                                  // every host write of the body)
     int* node_map;                // [box_cap]
     int* fp_node;                 // [nent] slot -> box-local node
     int* csr_off;                 // [nent + 1]

@@ -1904,6 +1904,8 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
 __device__ void body_prepare(BodyDev& B, double* sh) {
     const double PI = 3.14159265358979323846;
     BodyState& S = B.st;
+    // a fixed body whose desired velocities are already in place: nothing moves
+    if (B.motion == MOT_FIXED && (B.ud_given || B.ud_current)) return;
     const double r2 = B.radius * B.radius;
     const double ms = B.rho_ratio * PI * r2, Is = 0.5 * ms * r2;
     const double dm = (B.rho_ratio - 1.0) * PI * r2;
@@ -1927,7 +1929,9 @@ __device__ void body_prepare(BodyDev& B, double* sh) {
             vx = S.vx; vy = 0.0; om = 0.0;
         }
         sh[0] = S.xc; sh[1] = S.yc; sh[2] = vx; sh[3] = vy; sh[4] = om;
-        sh[5] = cos(S.theta); sh[6] = sin(S.theta);
+        const bool turns = B.motion == MOT_FREE || B.motion == MOT_FREE_TRANSLATION;
+        sh[5] = turns ? cos(S.theta) : 1.0;
+        sh[6] = turns ? sin(S.theta) : 0.0;
         if (B.motion != MOT_FIXED) B.cache_valid = 0;
     }
     __syncthreads();
@@ -1953,6 +1957,7 @@ __device__ void body_prepare(BodyDev& B, double* sh) {
         B.Udy[k] = vy + om * rx;
     }
     __syncthreads();
+    if (threadIdx.x == 0 && B.motion == MOT_FIXED) B.ud_current = 1;
 }
 
 __device__ void body_finish(BodyDev& B) {
