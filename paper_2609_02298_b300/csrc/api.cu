@@ -872,10 +872,12 @@ struct EdgeGroup {
 struct ListGroup {
     int storage = 0;
     int collision = 0;
+    int group = 0;                             // index into BatchPlan::groups
     CaseDev** dcases = nullptr;                // the group's lattices (list indices into it)
-    int4* dlist = nullptr;
-    long long n = 0;
-    int grid = 0;
+    // per scalar variant (its segment width): the segments, their count and the grid
+    int4* dlist[SC_VARIANTS] = {};
+    long long n[SC_VARIANTS] = {};
+    int grid[SC_VARIANTS] = {};
 };
 
 struct BatchPlan {
@@ -989,9 +991,11 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     }
     if (overlap)
         for (auto& lg : P->list_groups) {
-            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dlist, (int)SC_LIST, 0};
-            if ((e = launch_stream_collide(lg.storage, lg.collision, SC_SCALAR2, sl, lg.n, lg.grid, st)) !=
-                cudaSuccess)
+            // the same variant (segment width) as the group's sweep, so that every node sees
+            // the same per-segment force decision as in the whole-lattice order
+            const int v = chosen_variant(P->groups[lg.group]);
+            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dlist[v], (int)SC_LIST, 0};
+            if ((e = launch_stream_collide(lg.storage, lg.collision, v, sl, lg.n[v], lg.grid[v], st)) != cudaSuccess)
                 return e;
         }
     if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // join before the step counters advance
@@ -1000,8 +1004,8 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
 }
 
 // IB-region segment lists of an overlap plan: footprints are built at the bodies'
-// (fixed) markers, the boxes read back and every segment of the list launch (the
-// two-per-lane scalar variant) in the kIbAlign-aligned regions listed once per lattice.  Leaves overlap_ok false when a body is not fixed
+// (fixed) markers, the boxes read back and every segment of the kIbAlign-aligned regions
+// listed once per lattice, for each scalar variant's segment width.  Leaves overlap_ok false when a body is not fixed
 // or has no footprint.
 // At most this many IB CTAs (bodies) for the overlap: each holds a whole SM that the
 // sweep beside it gives up (so all the sweep's CTAs run at once and its static job
@@ -1034,36 +1038,42 @@ int build_ib_lists(BatchPlan* P, int sms) {
     }
     int rc = check(cudaStreamSynchronize(P->st));
     if (rc) return rc;
-    for (auto& grp : P->groups) {
-        std::vector<int4> list;
-        int ci = 0;
-        for (auto* c : P->ctxs) {
-            if (c->hc.storage != grp.storage || c->hc.collision != grp.collision) continue;
-            std::set<std::pair<int, int>> segs;
-            for (int b = 0; b < (int)c->bodies.size(); ++b) {
-                BodyDev B;
-                if (cudaMemcpy(&B, &c->dbodies[b], sizeof(BodyDev), cudaMemcpyDeviceToHost) != cudaSuccess)
-                    return check(cudaGetLastError());
-                if (B.nfp <= 0) return IBLBM_OK;
-                const int seg = sc_segment(grp.storage, SC_SCALAR2);   // the list launch's segment
-                for (int y = B.by0; y < B.by0 + B.bh; ++y)
-                    for (int x = 0; x < c->hc.nx; x += seg)
-                        if (in_ib_region(y, x, B.bx0, B.by0, B.bw, B.bh)) segs.insert({y, x});
-            }
-            for (auto& sg : segs) list.push_back(make_int4(ci, sg.first, sg.second, 0));
-            ++ci;
-        }
-        if (list.empty()) continue;
+    for (size_t gi = 0; gi < P->groups.size(); ++gi) {
+        const auto& grp = P->groups[gi];
         ListGroup lg;
         lg.storage = grp.storage;
         lg.collision = grp.collision;
+        lg.group = (int)gi;
         lg.dcases = grp.dcases;
-        lg.n = (long long)list.size();
-        lg.grid = (int)std::max<long long>(1, std::min<long long>((lg.n + 15) / 16, 4LL * sms));
-        lg.dlist = static_cast<int4*>(plan_alloc(P, sizeof(int4) * list.size()));
-        if (!lg.dlist) return IBLBM_ERR_OOM;
-        cudaMemcpyAsync(lg.dlist, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, P->st);
-        P->list_groups.push_back(lg);
+        bool any = false;
+        for (int v : {(int)SC_SCALAR, (int)SC_SCALAR2}) {
+            std::vector<int4> list;
+            const int seg = sc_segment(grp.storage, v);
+            int ci = 0;
+            for (auto* c : P->ctxs) {
+                if (c->hc.storage != grp.storage || c->hc.collision != grp.collision) continue;
+                std::set<std::pair<int, int>> segs;
+                for (int b = 0; b < (int)c->bodies.size(); ++b) {
+                    BodyDev B;
+                    if (cudaMemcpy(&B, &c->dbodies[b], sizeof(BodyDev), cudaMemcpyDeviceToHost) != cudaSuccess)
+                        return check(cudaGetLastError());
+                    if (B.nfp <= 0) return IBLBM_OK;
+                    for (int y = B.by0; y < B.by0 + B.bh; ++y)
+                        for (int x = 0; x < c->hc.nx; x += seg)
+                            if (in_ib_region(y, x, B.bx0, B.by0, B.bw, B.bh)) segs.insert({y, x});
+                }
+                for (auto& sg : segs) list.push_back(make_int4(ci, sg.first, sg.second, 0));
+                ++ci;
+            }
+            if (list.empty()) continue;
+            any = true;
+            lg.n[v] = (long long)list.size();
+            lg.grid[v] = (int)std::max<long long>(1, std::min<long long>((lg.n[v] + 15) / 16, 4LL * sms));
+            lg.dlist[v] = static_cast<int4*>(plan_alloc(P, sizeof(int4) * list.size()));
+            if (!lg.dlist[v]) return IBLBM_ERR_OOM;
+            cudaMemcpyAsync(lg.dlist[v], list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, P->st);
+        }
+        if (any) P->list_groups.push_back(lg);
     }
     rc = check(cudaStreamSynchronize(P->st));
     if (rc) return rc;

@@ -323,10 +323,7 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     S* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
-    // IB patch lookup and the force terms for the whole kIbAlign block holding the segment
-    // (uniform over the segment, and the same however a row is segmented)
-    const int xb = xseg / kIbAlign * kIbAlign;
-    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xb, xb + kIbAlign);
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 32 * NPT);
     const bool forced = ib || K.has_force;
     // pull offset of population i relative to the node: i plane - e_iy pitch - e_ix
     int koff[9];
@@ -373,8 +370,7 @@ __device__ __forceinline__ void sc_row_pair(const ScCase<__half>& K, int y, int 
     __half* __restrict__ dst = K.dst;
     const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
     if (y == 0 || y == ny - 1) return;
-    const int xb = xseg / kIbAlign * kIbAlign;   // as in sc_row_scalar
-    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xb, xb + kIbAlign);
+    const bool ib = K.nbodies > 0 && row_has_ib(C, y, xseg, xseg + 64 * NP);
     const bool forced = ib || K.has_force;
     const int row = y * pitch;
     bool unstable = false;
@@ -453,11 +449,13 @@ __device__ __forceinline__ void sc_row_nodes(const ScCase<S>& K, int y, int xseg
     else sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
 }
 
-template <class S, int KIND, int NPT>
+// SKIP: the launch beside the IB stage (segments in IB regions left out, programmatic
+// dependent launch); the whole-lattice launch is compiled without any of it.
+template <class S, int KIND, int NPT, bool SKIP>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     constexpr int kSegW = ScSeg<S, NPT>::value;
-    if (L.pdl & PDL_TRIGGER) pdl_trigger();
+    if (SKIP && (L.pdl & PDL_TRIGGER)) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -479,10 +477,10 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
         const int local = (int)(job - c_lo);   // < ny * nseg
         const int y = local / nseg;
         const int xseg = (local - y * nseg) * kSegW;
-        if (L.phase == SC_SKIP_IB && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
+        if (SKIP && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
         sc_row_nodes<S, KIND, NPT>(K, y, xseg, lane);
     }
-    if (L.pdl & PDL_DEPENDENT) pdl_wait();
+    if (SKIP && (L.pdl & PDL_DEPENDENT)) pdl_wait();
 }
 
 // The SC_LIST phase: the listed segments (IB regions), warp w taking entries w, w + W, ...
@@ -2262,8 +2260,13 @@ static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, i
         else IBLBM_LAUNCH((sc_kernel_list<S, KIND, 2>), grid, block, st, L, jobs);
         return cudaGetLastError();
     }
-    if (variant == SC_SCALAR) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1>), grid, block, st, dep, L, jobs);
-    else if (variant == SC_SCALAR2) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2>), grid, block, st, dep, L, jobs);
+    if (L.phase == SC_SKIP_IB) {
+        if (variant == SC_SCALAR) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1, true>), grid, block, st, dep, L, jobs);
+        else IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2, true>), grid, block, st, dep, L, jobs);
+        return cudaGetLastError();
+    }
+    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1, false>), grid, block, st, L, jobs);
+    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2, false>), grid, block, st, L, jobs);
     else if (variant == SC_BULK) {
         static const cudaError_t attr =
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
@@ -2300,9 +2303,9 @@ template <class S, int KIND>
 static int sc_occ_k(int variant) {
     int nb = 1;
     if (variant == SC_SCALAR)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1, false>, kThreads, 0);
     else if (variant == SC_SCALAR2)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2, false>, kThreads, 0);
     else if (variant == SC_BULK) {
         const void* fn = reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>);
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);

@@ -159,6 +159,10 @@ def test_graph_replay_equals_timed_launches():
     P.check_graph_equals_direct()
 
 
+def test_overlap_order_equals_serial_order():
+    P.check_overlap_equals_serial()
+
+
 def test_marker_out_of_domain_is_reported():
     P.check_marker_out_of_domain(L)
 
