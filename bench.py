@@ -91,7 +91,8 @@ def launches_per_step(specs, L=None) -> int:
     and -- when at most eight bodies, all fixed, of one storage type and the tuned sweeps
     are the one- or two-node-per-lane kernels, so the IB stage overlaps the sweep -- one
     launch per group with bodies for the IB-region segments; then one lattice-edge launch
-    per storage type and the step-counter launch."""
+    per storage type and the step-counter launch (folded into the edge launch in that
+    order when there is one storage type)."""
     storages = {s.storage for s in specs}
     with_bodies = {s.storage for s in specs if s.bodies}
     groups = {(s.storage, s.collision) for s in specs}
@@ -102,6 +103,8 @@ def launches_per_step(specs, L=None) -> int:
     large = sum(s.nodes for s in specs) >= (1 << 20)
     if len(with_bodies) == 1 and 0 < nbodies <= 8 and fixed and phased and large:
         n += len({(s.storage, s.collision) for s in specs if s.bodies})
+        if len(storages) == 1:
+            n -= 1   # the edge launch advances the step counters itself
     return n
 
 

@@ -905,6 +905,7 @@ struct BatchPlan {
     // A lattice with several DFC bodies, one of them moving: W_total of Eq. 17 reads every
     // DFC body's markers, so all bodies move in a launch of their own before the IB stage.
     bool prepare_first = false;
+    unsigned* ddone = nullptr;                 // finished-CTA count of the step-ending edge launch
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_edges = nullptr;
     ~BatchPlan() {
@@ -925,9 +926,15 @@ void* plan_alloc(BatchPlan* P, size_t b) {
     return p;
 }
 
-cudaError_t launch_edge_groups(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer, int noib) {
+cudaError_t launch_edge_groups(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer, int noib, bool ends_step = false) {
     for (auto& g : P->edge_groups) {
-        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block, noib, 0};
+        EdgeLaunch el{g.dcases, g.dchunks, g.nchunks, g.block, noib, 0, nullptr, 0, 0, nullptr};
+        if (ends_step) {   // (one edge group): begins beside the launch before it, ends the step
+            el.pdl = PDL_DEPENDENT;
+            el.count_cases = P->dcases_all;
+            el.ncount = (int)P->ctxs.size();
+            el.done = P->ddone;
+        }
         const cudaError_t e = timed_launch(timer, STAGE_EDGE, st, [&] { return launch_edges(g.storage, el, st); });
         if (e != cudaSuccess) return e;
     }
@@ -989,17 +996,23 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
              })) != cudaSuccess)
             return e;
     }
+    // with one edge group the edge launch of the overlap order runs beside the IB-region
+    // launches and advances the step counters itself
+    const bool edges_end = overlap && P->edge_groups.size() == 1 && P->ddone;
     if (overlap)
-        for (auto& lg : P->list_groups) {
+        for (size_t k = 0; k < P->list_groups.size(); ++k) {
+            const auto& lg = P->list_groups[k];
             // the same variant (segment width) as the group's sweep, so that every node sees
             // the same per-segment force decision as in the whole-lattice order
             const int v = chosen_variant(P->groups[lg.group]);
-            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dlist[v], (int)SC_LIST, 0};
+            const bool last = k + 1 == P->list_groups.size();
+            ScLaunch sl{lg.dcases, nullptr, 0, 0, lg.dlist[v], (int)SC_LIST, (edges_end && last) ? (int)PDL_TRIGGER : 0};
             if ((e = launch_stream_collide(lg.storage, lg.collision, v, sl, lg.n[v], lg.grid[v], st)) != cudaSuccess)
                 return e;
         }
     if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // join before the step counters advance
-    else if ((e = launch_edge_groups(P, st, timer, 0)) != cudaSuccess) return e;
+    else if ((e = launch_edge_groups(P, st, timer, 0, edges_end)) != cudaSuccess) return e;
+    if (edges_end) return cudaSuccess;
     return timed_launch(timer, STAGE_COUNTER, st, [&] { return launch_counters(P->dcases_all, (int)P->ctxs.size(), st); });
 }
 
@@ -1193,6 +1206,9 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             P->groups.push_back(g);
         }
     }
+    P->ddone = static_cast<unsigned*>(plan_alloc(P, sizeof(unsigned)));
+    if (!P->ddone) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+    cudaMemsetAsync(P->ddone, 0, sizeof(unsigned), P->st);
     P->nrefs_all = (int)all_refs.size();
     P->drefs_all = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, all_refs.size())));
     P->dcases_all = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * all_cases.size()));

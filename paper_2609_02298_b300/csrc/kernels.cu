@@ -487,6 +487,7 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
 template <class S, int KIND, int NPT>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_list(ScLaunch L, long long jobs) {
+    if (L.pdl & PDL_TRIGGER) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -537,26 +538,41 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     const CaseDev& C = sc;
     const int nx = K.nx, ny = K.ny;
     const int e = ch.first + (int)threadIdx.x;
-    if (e >= ch.end) return;
-    int x, y;
-    if (e < nx) {
-        x = e; y = 0;
-    } else if (ny > 1 && e < 2 * nx) {
-        x = e - nx; y = ny - 1;
-    } else {
-        const int r = e - (ny > 1 ? 2 * nx : nx);
-        if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
-        else { y = 1 + r; x = 0; }
-    }
-    R s[9];
-    post_stream_node<S, R>(C, K.src, x, y, s);
-    R Fx = K.gfx, Fy = K.gfy;
-    if (K.nbodies > 0 && !L.noib) add_ib<R>(C, x, y, s, Fx, Fy);
-    const R rho = collide<R, -1>(K.P, s, Fx, Fy);
-    if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
-    S* d = K.dst + ((long long)y * K.pitch + x);
+    if (e < ch.end) {
+        int x, y;
+        if (e < nx) {
+            x = e; y = 0;
+        } else if (ny > 1 && e < 2 * nx) {
+            x = e - nx; y = ny - 1;
+        } else {
+            const int r = e - (ny > 1 ? 2 * nx : nx);
+            if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
+            else { y = 1 + r; x = 0; }
+        }
+        R s[9];
+        post_stream_node<S, R>(C, K.src, x, y, s);
+        R Fx = K.gfx, Fy = K.gfy;
+        if (K.nbodies > 0 && !L.noib) add_ib<R>(C, x, y, s, Fx, Fy);
+        const R rho = collide<R, -1>(K.P, s, Fx, Fy);
+        if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
+        S* d = K.dst + ((long long)y * K.pitch + x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+        for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+    }
+    if (L.pdl & PDL_DEPENDENT) pdl_wait();   // the launch before this one has finished too
+    if (L.count_cases) {
+        // the last CTA to finish ends the step: every read of the step counters is done
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(L.done, 1u);
+            if (prev == gridDim.x - 1u) {
+                __threadfence();
+                for (int c = 0; c < L.ncount; ++c) L.count_cases[c]->step += 1ull;
+                L.done[0] = 0u;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2352,10 +2368,11 @@ bool sc_variant_ok(int variant, const void* f0, const void* f1) {
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st) {
     if (L.nchunks <= 0) return cudaSuccess;
     const int block = L.block > 0 ? L.block : kThreads;
+    const bool dep = (L.pdl & PDL_DEPENDENT) != 0;
     switch (storage) {
-    case ST_F64: IBLBM_LAUNCH(edge_kernel<double>, L.nchunks, block, st, L); break;
-    case ST_F32: IBLBM_LAUNCH(edge_kernel<float>, L.nchunks, block, st, L); break;
-    default: IBLBM_LAUNCH(edge_kernel<__half>, L.nchunks, block, st, L); break;
+    case ST_F64: IBLBM_LAUNCH_PDL(edge_kernel<double>, L.nchunks, block, st, dep, L); break;
+    case ST_F32: IBLBM_LAUNCH_PDL(edge_kernel<float>, L.nchunks, block, st, dep, L); break;
+    default: IBLBM_LAUNCH_PDL(edge_kernel<__half>, L.nchunks, block, st, dep, L); break;
     }
     return cudaGetLastError();
 }

@@ -77,7 +77,13 @@ struct EdgeLaunch {
     int nchunks;
     int block;   // threads per CTA: the chunk size, a multiple of 32 up to kThreads
     int noib;    // 1: no edge node lies in a body footprint (no IB patch lookup)
+    int pdl;     // PDL_DEPENDENT: may start while the previous launch runs, waits for it at the end
+    // When set, the edge launch ends the step: its last CTA (done[0] counts finished CTAs and
+    // is reset) advances the step counter of every case in count_cases.
+    CaseDev** count_cases;
+    int ncount;
     int pad_;
+    unsigned* done;
 };
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
