@@ -36,15 +36,16 @@ METRIC = "MLUPS & % of HBM peak per IB-LBM step; batched cases/s with p50/p99 la
 UNIT = "MLUPS"
 BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # DRAM bytes (read + write) per node of one FP32 stream-collide launch, by (variant,
-# operator), and per lattice of the edge launch, from ncu section captures of the
-# 12-lattice case (scaled by nodes).  A sweep whose kernels have no entry here (or changed
-# since) reports traffic null.
-SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): 564.13e6 / 8388608, (2, W.TRT): 563.61e6 / 8388608,
-                             (2, W.CMMRT): 564.38e6 / 8388608}
-# The edge launch gained the zero-velocity wall-closure branch after its capture: no figure
-# until it is captured again (the sweep's traffic is then reported null).
-EDGE_DRAM_BYTES_PER_LATTICE = None
+# operator), and per lattice of the edge launch: ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum of two steps of the 12-lattice case (4 lattices per stream-collide
+# launch, 12 per edge launch), averaged and divided by nodes or lattices.  A sweep whose
+# kernels have no entry here (or changed since) reports traffic null.
+SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): (560650752 + 558946560) / 2 / 8388608,
+                             (2, W.TRT): (559732992 + 560361728) / 2 / 8388608,
+                             (2, W.CMMRT): (560482048 + 559604736) / 2 / 8388608}
+EDGE_DRAM_BYTES_PER_LATTICE = (29597696 + 29859072) / 2 / 12
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
+STORAGE_LABEL = {W.F64: "f64 shifted", W.F32: "f32 shifted", W.F16S: "f16 shifted"}
 
 
 def matrix_specs(storage=W.F32, res=(100.0, 200.0), nx=2048, ny=1024):
@@ -443,7 +444,8 @@ def workload_config(specs, world=1):
     return {"workload": ("fixed-cylinder matrix %dx%d, D=%g, %d markers: Re {100,200} x "
                          "{DF, MDF(5), DFC} x {hat, P4} x {BGK, TRT, CM-MRT}" %
                          (nx, ny, specs[0].bodies[0].radius * 2, len(specs[0].bodies[0].xy))),
-            "lattices": len(specs), "nodes_per_step": nodes, "storage": "f32 shifted",
+            "lattices": len(specs), "nodes_per_step": nodes,
+            "storage": STORAGE_LABEL[specs[0].storage],
             "l2": "populations %.1f GB (A/B buffers) > 126 MB L2, no flush"
                   % (BYTES_PER_LU[specs[0].storage] * nodes / 1e9),
             "parallelism": "replicas" if world > 1 else "single"}

@@ -856,6 +856,7 @@ struct IbGroup {
     int storage = 0;
     BodyRef* drefs = nullptr;
     int nrefs = 0;
+    int cluster = 1;                           // CTAs per body (ib_cluster_size)
 };
 // Lattice-edge nodes of all lattices of one storage type (one launch per step).
 struct EdgeGroup {
@@ -905,7 +906,13 @@ struct BatchPlan {
     // A lattice with several DFC bodies, one of them moving: W_total of Eq. 17 reads every
     // DFC body's markers, so all bodies move in a launch of their own before the IB stage.
     bool prepare_first = false;
-    unsigned* ddone = nullptr;                 // finished-CTA count of the step-ending edge launch
+    unsigned* ddone = nullptr;                 // finished-CTA count of the step-ending launch
+    // Overlap order with one storage type: each group's sweep takes its IB-region segments
+    // after the IB stage, and the last one the lattice edges (32-node chunks) and the end of
+    // the step, so that a step is the IB launch and one launch per group.
+    bool fused_tail = false;
+    EdgeChunk* dechunks32 = nullptr;
+    int nechunks32 = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_edges = nullptr;
     ~BatchPlan() {
@@ -981,21 +988,45 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     for (size_t k = 0; k < P->ib_groups.size(); ++k) {
         const auto& g = P->ib_groups[k];
         const bool last = k + 1 == P->ib_groups.size();
-        IbLaunch il{g.drefs, g.nrefs, 0, (overlap && last) ? (int)PDL_TRIGGER : 0, P->prepare_first ? 1 : 0};
+        IbLaunch il{g.drefs, g.nrefs, 0, (overlap && last) ? (int)PDL_TRIGGER : 0, P->prepare_first ? 1 : 0,
+                    g.cluster};
         if ((e = timed_launch(timer, STAGE_IB, st, [&] { return launch_ib(g.storage, il, st); })) != cudaSuccess)
             return e;
     }
     const bool dependent = overlap && !P->ib_groups.empty();
-    for (auto& g : P->groups) {
+    const bool fused = dependent && P->fused_tail;
+    for (size_t gi = 0; gi < P->groups.size(); ++gi) {
+        const auto& g = P->groups[gi];
         const int v = chosen_variant(g);
         ScLaunch sl{g.dcases, g.djob[v], g.ncases, g.block[v], nullptr, overlap ? (int)SC_SKIP_IB : (int)SC_ALL,
                     dependent ? (int)(PDL_TRIGGER | PDL_DEPENDENT) : 0};
-        const int grid = overlap ? g.grid_overlap[v] : g.grid[v];
+        int grid = overlap ? g.grid_overlap[v] : g.grid[v];
+        if (fused) {
+            for (const auto& lg : P->list_groups)
+                if (lg.group == (int)gi) {
+                    sl.list = lg.dlist[v];
+                    sl.nlist = lg.n[v];
+                }
+            if (gi + 1 == P->groups.size()) {
+                sl.echunks = P->dechunks32;
+                sl.ecases = P->edge_groups[0].dcases;
+                sl.nechunks = P->nechunks32;
+                sl.count_cases = P->dcases_all;
+                sl.ncount = (int)P->ctxs.size();
+                sl.done = P->ddone;
+            }
+            // tail CTAs: one segment or edge chunk per warp
+            const long long tail_jobs = sl.nlist + sl.nechunks;
+            const int wpc = (g.block[v] > 0 ? g.block[v] : kThreads) / 32;
+            sl.tail_ctas = tail_jobs > 0 ? (int)std::max<long long>(1, (tail_jobs + wpc - 1) / wpc) : 0;
+            grid += sl.tail_ctas;
+        }
         if ((e = timed_launch(timer, STAGE_SWEEP, st, [&] {
                  return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], grid, st);
              })) != cudaSuccess)
             return e;
     }
+    if (fused) return cudaSuccess;
     // with one edge group the edge launch of the overlap order runs beside the IB-region
     // launches and advances the step counters itself
     const bool edges_end = overlap && P->edge_groups.size() == 1 && P->ddone;
@@ -1024,6 +1055,7 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
 // sweep beside it gives up (so all the sweep's CTAs run at once and its static job
 // split stays balanced); beyond that the SMs given up cost more than the overlap saves.
 constexpr int kOverlapMaxBodies = 8;
+constexpr int kOverlapIbSms = 8;
 
 int build_ib_lists(BatchPlan* P, int sms) {
     P->overlap_ok = false;
@@ -1036,7 +1068,10 @@ int build_ib_lists(BatchPlan* P, int sms) {
     long long nodes = 0;
     for (auto* c : P->ctxs) nodes += (long long)c->hc.nx * c->hc.ny;
     if (nodes < kLargeGroupNodes) return IBLBM_OK;
-    const int free_sms = sms - P->ib_groups[0].nrefs;
+    // the IB launch holds one SM per CTA (nrefs clusters of `cluster` CTAs), SMs the sweep
+    // beside it gives up: at most kOverlapIbSms of them
+    P->ib_groups[0].cluster = ib_cluster_size(P->ib_groups[0].storage, P->ib_groups[0].nrefs, kOverlapIbSms);
+    const int free_sms = sms - P->ib_groups[0].nrefs * std::max(1, P->ib_groups[0].cluster);
     for (auto& g : P->groups)
         for (int v = 0; v < SC_VARIANTS; ++v) {
             const long long cap = (long long)free_sms * sc_blocks_per_sm(g.storage, g.collision, v);
@@ -1088,6 +1123,26 @@ int build_ib_lists(BatchPlan* P, int sms) {
         }
         if (any) P->list_groups.push_back(lg);
     }
+    // one storage type: the lattice edges in 32-node chunks (one warp each), in the order of
+    // the edge group's cases, for the tail of the last sweep launch
+    if (P->edge_groups.size() == 1 && P->ddone) {
+        std::vector<EdgeChunk> chunks;
+        int ci = 0;
+        for (auto* c : P->ctxs) {
+            if (c->hc.storage != P->edge_groups[0].storage) continue;
+            const int ne = (int)lattice_edge_nodes(c->hc.nx, c->hc.ny);
+            for (int f = 0; f < ne; f += 32) chunks.push_back(EdgeChunk{ci, f, std::min(ne, f + 32), 0});
+            ++ci;
+        }
+        if (!chunks.empty()) {
+            P->dechunks32 = static_cast<EdgeChunk*>(plan_alloc(P, sizeof(EdgeChunk) * chunks.size()));
+            if (!P->dechunks32) return IBLBM_ERR_OOM;
+            cudaMemcpyAsync(P->dechunks32, chunks.data(), sizeof(EdgeChunk) * chunks.size(), cudaMemcpyHostToDevice,
+                            P->st);
+            P->nechunks32 = (int)chunks.size();
+            P->fused_tail = true;
+        }
+    }
     rc = check(cudaStreamSynchronize(P->st));
     if (rc) return rc;
     P->overlap_ok = true;
@@ -1124,6 +1179,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
             IbGroup ig;
             ig.storage = st;
             ig.nrefs = (int)refs.size();
+            ig.cluster = ib_cluster_size(st, ig.nrefs, sms / 2);
             ig.drefs = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * refs.size()));
             if (!ig.drefs) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
             cudaMemcpyAsync(ig.drefs, refs.data(), sizeof(BodyRef) * refs.size(), cudaMemcpyHostToDevice, P->st);

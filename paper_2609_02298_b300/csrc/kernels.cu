@@ -70,6 +70,36 @@ __device__ __forceinline__ void pdl_wait() {
 #endif
 }
 
+// L1 prefetch hint of the line holding a (a hint: it brings data early, changes nothing).
+__device__ __forceinline__ void prefetch_l1(const void* a) {
+#ifndef IBLBM_EMULATE
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+#else
+    (void)a;
+#endif
+}
+
+// Thread-block clusters (sm_90 and later): rank of this CTA in its cluster, and a barrier
+// of every thread of the cluster with release / acquire semantics at cluster scope (writes
+// before it, global memory included, are visible to the cluster's threads after it).  The
+// host emulation runs one CTA per cluster.
+__device__ __forceinline__ unsigned cluster_rank() {
+#ifndef IBLBM_EMULATE
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+#else
+    return 0;
+#endif
+}
+__device__ __forceinline__ void cluster_sync_all() {
+#ifndef IBLBM_EMULATE
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+#else
+    __syncthreads();
+#endif
+}
+
 // True when the row segment [xseg, xseg + w) of row y lies in the IB region of a body
 // of the case (w divides kIbAlign, xseg a multiple of w).
 __device__ __forceinline__ bool seg_in_ib(const CaseDev& C, int y, int xseg) {
@@ -449,6 +479,125 @@ __device__ __forceinline__ void sc_row_nodes(const ScCase<S>& K, int y, int xseg
     else sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
 }
 
+// Lattice-edge node e of a case (rows 0 and ny-1, columns 0 and nx-1): pull with wrap and
+// domain conditions (post_stream_node), IB patch, collision with the case's own operator,
+// store.  C is the case record (possibly a shared-memory copy), gc the case in global
+// memory (status flags).  Edge node e: e < nx -> (e, 0); e < 2nx -> (e - nx, ny - 1) when
+// ny > 1; then columns 0 and nx-1 of rows 1..ny-2, alternating.
+template <class S>
+__device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, int e, bool noib, const CaseDev* gc) {
+    using R = typename Traits<S>::R;
+    const int nx = K.nx, ny = K.ny;
+    int x, y;
+    if (e < nx) {
+        x = e; y = 0;
+    } else if (ny > 1 && e < 2 * nx) {
+        x = e - nx; y = ny - 1;
+    } else {
+        const int r = e - (ny > 1 ? 2 * nx : nx);
+        if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
+        else { y = 1 + r; x = 0; }
+    }
+    R s[9];
+    post_stream_node<S, R>(C, K.src, x, y, s);
+    R Fx = K.gfx, Fy = K.gfy;
+    if (K.nbodies > 0 && !noib) add_ib<R>(C, x, y, s, Fx, Fy);
+    const R rho = collide<R, -1>(K.P, s, Fx, Fy);
+    if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
+    S* d = K.dst + ((long long)y * K.pitch + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+}
+
+// Last CTA of a launch to finish ends the step: advances the step counter of every case
+// (every read of the counters in the step is done by then); done[0] counts finished CTAs
+// and is reset for the next step.
+__device__ __forceinline__ void end_step_if_last(unsigned* done, CaseDev** cases, int ncases) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1u) {
+            __threadfence();
+            for (int c = 0; c < ncases; ++c) cases[c]->step += 1ull;
+            done[0] = 0u;
+        }
+    }
+}
+
+// Work of the tail CTAs of a SC_SKIP_IB launch (warp w of nw): once the IB stage has
+// ended, the listed IB-region segments, then the lattice-edge chunks, one job per warp in
+// turn.
+template <class S, int KIND, int NPT>
+__device__ __forceinline__ void sc_tail(const ScLaunch& L, int w, int nw, int lane) {
+    ScCase<S> K;
+    const CaseDev* cur = nullptr;
+    const long long njobs = L.nlist + L.nechunks;
+    // Before the wait, what the first job reads that the IB stage does not write: its case
+    // record and, into L1, the lines its pulls and (IB-region segments) its footprint-map
+    // lookups will touch, so that after the wait only the patches are fetched from L2.
+    if (w < njobs) {
+        int y, x0, x1;
+        if (w < L.nlist) {
+            const int4 e = L.list[w];
+            cur = L.cases[e.x];
+            K.load(cur);
+            y = e.y;
+            x0 = e.z;
+            x1 = e.z + ScSeg<S, NPT>::value;
+        } else {
+            const EdgeChunk ch = L.echunks[w - L.nlist];
+            cur = L.ecases[ch.c];
+            K.load(cur);
+            // rows 0 and ny-1 are contiguous runs; the columns take one node per lane
+            const int e = min(ch.first + lane, ch.end - 1);
+            if (e < K.nx) { y = 0; x0 = ch.first; x1 = min(ch.end, K.nx); }
+            else if (K.ny > 1 && e < 2 * K.nx) { y = K.ny - 1; x0 = ch.first - K.nx; x1 = min(ch.end, 2 * K.nx) - K.nx; }
+            else { const int r = e - 2 * K.nx; y = 1 + (r >> 1); x0 = (r & 1) ? K.nx - 1 : 0; x1 = x0 + 1; }
+        }
+        const char* base = reinterpret_cast<const char*>(K.src);
+        const int nb = (int)sizeof(S);
+        const int xa = max(0, x0 - 1), xb = min(K.nx - 1, x1);   // pulled columns (clamped)
+        const int lines = ((xb - xa + 1) * nb + 127) / 128 + 1;
+        // a run of a row: the lanes share its lines; a column node: each lane its own
+        const bool run = x1 - x0 > 1;
+        for (int t = run ? lane : 0; t < 9 * 3 * lines; t += run ? 32 : 1) {
+            const int i = t / (3 * lines), r = (t / lines) % 3, l = t % lines;
+            const int yy = min(max(y - 1 + r, 0), K.ny - 1);
+            const int xx = min(xa + l * (128 / nb), xb);
+            prefetch_l1(base + ((long long)i * K.plane + (long long)yy * K.pitch + xx) * nb);
+        }
+        if (w < L.nlist)
+            for (int b = 0; b < K.nbodies; ++b) {
+                const BodyDev& B = K.C->bodies[b];
+                const int ly = y - B.by0, la = max(x0 - B.bx0, 0), lb = min(x1 - B.bx0, B.bw);
+                if (B.nfp <= 0 || ly < 0 || ly >= B.bh || la >= lb) continue;
+                for (int l = la + lane * 32; l < lb; l += 32 * 32) prefetch_l1(B.node_map + ly * B.bw + l);
+            }
+    }
+    if (L.pdl & PDL_DEPENDENT) pdl_wait();   // the IB stage has ended, its patches are visible
+    for (long long j = w; j < njobs; j += nw) {
+        if (j < L.nlist) {
+            const int4 e = L.list[j];
+            const CaseDev* c = L.cases[e.x];
+            if (c != cur) {
+                K.load(c);
+                cur = c;
+            }
+            sc_row_nodes<S, KIND, NPT>(K, e.y, e.z, lane);
+        } else {
+            const EdgeChunk ch = L.echunks[j - L.nlist];
+            const CaseDev* c = L.ecases[ch.c];
+            if (c != cur) {
+                K.load(c);
+                cur = c;
+            }
+            const int e = ch.first + lane;
+            if (e < ch.end) edge_node<S>(*c, K, e, false, c);
+        }
+    }
+}
+
 // SKIP: the launch beside the IB stage (segments in IB regions left out, programmatic
 // dependent launch); the whole-lattice launch is compiled without any of it.
 template <class S, int KIND, int NPT, bool SKIP>
@@ -457,8 +606,17 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
     constexpr int kSegW = ScSeg<S, NPT>::value;
     if (SKIP && (L.pdl & PDL_TRIGGER)) pdl_trigger();
     const int lane = threadIdx.x & 31;
+    // with tail CTAs (SKIP only) the segments outside the IB regions are split over the
+    // other CTAs
+    const int nblk = SKIP ? (int)gridDim.x - L.tail_ctas : (int)gridDim.x;
+    const int wpc = (int)blockDim.x >> 5;
+    if (SKIP && (int)blockIdx.x >= nblk) {
+        sc_tail<S, KIND, NPT>(L, ((int)blockIdx.x - nblk) * wpc + ((int)threadIdx.x >> 5), L.tail_ctas * wpc, lane);
+        if (L.done) end_step_if_last(L.done, L.count_cases, L.ncount);
+        return;
+    }
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nw = (long long)nblk * wpc;
     ScCase<S> K;
     long long c_lo = 0, c_hi = 0;
     int nseg = 1;
@@ -480,7 +638,8 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
         if (SKIP && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
         sc_row_nodes<S, KIND, NPT>(K, y, xseg, lane);
     }
-    if (SKIP && (L.pdl & PDL_DEPENDENT)) pdl_wait();
+    if (SKIP && L.tail_ctas == 0 && (L.pdl & PDL_DEPENDENT)) pdl_wait();
+    if (SKIP && L.done) end_step_if_last(L.done, L.count_cases, L.ncount);
 }
 
 // The SC_LIST phase: the listed segments (IB regions), warp w taking entries w, w + W, ...
@@ -509,9 +668,9 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
 // case (chunk table built on the host): pull with wrap and domain conditions
 // (post_stream_node), IB patch, collision with the case's own operator, store.
 // Runs after the stream-collide launches of the step and is the only writer of
-// these nodes' results (a variant that also wrote them is overwritten).
-// Edge node e of a case: e < nx -> (e, 0); e < 2nx -> (e - nx, ny - 1) when
-// ny > 1; then columns 0 and nx-1 of rows 1..ny-2, alternating.
+// these nodes' results (a variant that also wrote them is overwritten); in the
+// overlap order with one storage type the last stream-collide launch does this work
+// itself (edge_node in its tail).
 __host__ __device__ inline long long edge_count(int nx, int ny) {
     const long long rows = (long long)nx * (ny > 1 ? 2 : 1);
     const long long cols = ny > 2 ? (long long)(ny - 2) * (nx > 1 ? 2 : 1) : 0;
@@ -520,7 +679,6 @@ __host__ __device__ inline long long edge_count(int nx, int ny) {
 
 template <class S>
 __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
-    using R = typename Traits<S>::R;
     // one CTA per 256 edge nodes of one case; the case record is staged in shared
     // memory so the boundary logic reads it without global round trips
     __shared__ __align__(16) CaseDev sc;
@@ -535,44 +693,10 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
     __syncthreads();
     ScCase<S> K;
     K.load(&sc);
-    const CaseDev& C = sc;
-    const int nx = K.nx, ny = K.ny;
     const int e = ch.first + (int)threadIdx.x;
-    if (e < ch.end) {
-        int x, y;
-        if (e < nx) {
-            x = e; y = 0;
-        } else if (ny > 1 && e < 2 * nx) {
-            x = e - nx; y = ny - 1;
-        } else {
-            const int r = e - (ny > 1 ? 2 * nx : nx);
-            if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
-            else { y = 1 + r; x = 0; }
-        }
-        R s[9];
-        post_stream_node<S, R>(C, K.src, x, y, s);
-        R Fx = K.gfx, Fy = K.gfy;
-        if (K.nbodies > 0 && !L.noib) add_ib<R>(C, x, y, s, Fx, Fy);
-        const R rho = collide<R, -1>(K.P, s, Fx, Fy);
-        if (bad_density(rho)) atomicOr(const_cast<unsigned*>(&gc->status), STAT_UNSTABLE);
-        S* d = K.dst + ((long long)y * K.pitch + x);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
-    }
+    if (e < ch.end) edge_node<S>(sc, K, e, L.noib != 0, gc);
     if (L.pdl & PDL_DEPENDENT) pdl_wait();   // the launch before this one has finished too
-    if (L.count_cases) {
-        // the last CTA to finish ends the step: every read of the step counters is done
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(L.done, 1u);
-            if (prev == gridDim.x - 1u) {
-                __threadfence();
-                for (int c = 0; c < L.ncount; ++c) L.count_cases[c]->step += 1ull;
-                L.done[0] = 0u;
-            }
-        }
-    }
+    if (L.count_cases) end_step_if_last(L.done, L.count_cases, L.ncount);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1148,13 +1272,85 @@ template <class R> struct IbSmem {
                                  (kMdfEntryCap + kMdfNodeCap + 1) * 4;
 };
 
-// Parts of the per-body IB stage: all of it; footprint and gather only (the coupled MDF
-// runs between); spread and force sums of marker forces already set.
-enum { IB_WHOLE = 0, IB_GATHER = 1, IB_SPREAD = 2 };
+// Parts of the per-body IB stage, as bits: set-up (footprint, omega_MDF, DFC lambda_k),
+// gather of the post-streaming state at the footprint nodes, marker forces + spread + body
+// sums, and marker forces preset (the coupled MDF sets them between a gather and a spread).
+enum { IBP_SETUP = 1, IBP_GATHER = 2, IBP_FORCES = 4, IBP_PRESET = 8 };
+enum {
+    IB_WHOLE = IBP_SETUP | IBP_GATHER | IBP_FORCES,
+    IB_SETUP = IBP_SETUP,
+    IB_GATHER = IBP_SETUP | IBP_GATHER,
+    IB_FORCES = IBP_FORCES,
+    IB_SPREAD = IBP_FORCES | IBP_PRESET
+};
 
-// Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin).
+// Gather of the post-streaming state at the footprint nodes of body B (thread t of nt):
+// rho and u (DF, MDF; u twice, the MDF iterate starts from it) or the nine shifted
+// populations (DFC) per node into B.fpdata.  A node's values do not depend on which
+// thread computes them.
+template <class S>
+__device__ void ib_gather(const CaseDev& C, const BodyDev& B, int t, int nt) {
+    using R = typename Traits<S>::R;
+    const int bx0 = B.bx0, by0 = B.by0, bw = B.bw, nfp = B.nfp, scheme = B.scheme;
+    R* fp = static_cast<R*>(B.fpdata);
+    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+    // GB footprint nodes per thread at a time: their pulls are issued together
+    // (interior nodes pull directly; nodes on a lattice edge take the domain conditions)
+    constexpr int GB = sizeof(R) == 8 ? 2 : 4;
+    const int cnx = C.nx, cny = C.ny, cpitch = C.pitch;
+    const long long cplane = C.plane;
+    for (int q0 = t; q0 < nfp; q0 += GB * nt) {
+        int gx[GB], gy[GB];
+        bool live[GB], inner[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const int q = q0 + u * nt;
+            live[u] = q < nfp;
+            const int node = live[u] ? B.fp_node[q] : 0;
+            gx[u] = bx0 + node % bw;
+            gy[u] = by0 + node / bw;
+            inner[u] = live[u] && gx[u] >= 1 && gx[u] <= cnx - 2 && gy[u] >= 1 && gy[u] <= cny - 2;
+        }
+        R sb[GB][9];
+#pragma unroll
+        for (int u = 0; u < GB; ++u)
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                sb[u][i] = inner[u] ? ld1(src + i * cplane + (long long)(gy[u] - ey(i)) * cpitch + (gx[u] - ex(i)))
+                                    : R(0);
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            if (!live[u]) continue;
+            if (!inner[u]) post_stream_node<S, R>(C, src, gx[u], gy[u], sb[u]);
+            const R* s = sb[u];
+            R* o = fp + (size_t)(q0 + u * nt) * 9;
+            if (scheme == SCH_DFC) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) o[i] = s[i];
+            } else {
+                R drho = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    drho += s[i];
+                    jx += R(ex(i)) * s[i];
+                    jy += R(ey(i)) * s[i];
+                }
+                const R rho = R(1) + drho;
+                o[0] = rho;
+                o[1] = jx / rho;
+                o[2] = jy / rho;
+                o[3] = o[1];
+                o[4] = o[2];
+            }
+        }
+    }
+}
+
+// Per-body IB stage (Sec. 2.4-2.7) for a stencil width SX (2 hat, 4 Peskin), the parts in
+// `part`.  Returns false when nothing more is to be done for the body in this launch (its
+// footprint could not be built, or a set-up-only launch).
 template <class S, int SX>
-__device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
+__device__ __forceinline__ bool ib_run(const IbLaunch& L, const BodyRef& ref, int* shi, double* shd,
                                        typename Traits<S>::R* sU, typename Traits<S>::R* sF,
                                        typename Traits<S>::R* sEw, int* sEk, typename Traits<S>::R* sQc,
                                        int* sQo, int part = IB_WHOLE) {
@@ -1164,8 +1360,8 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
     BodyDev& B = *ref.b;
     const int tid = threadIdx.x;
     const int n = B.n, scheme = B.scheme;
-    if (part != IB_SPREAD && !B.cache_valid) {
-        if (!build_footprint<R>(C, B, shi)) return;
+    if ((part & IBP_SETUP) && !B.cache_valid) {
+        if (!build_footprint<R>(C, B, shi)) return false;
         if (tid == 0) B.cache_valid = (B.motion == MOT_FIXED) ? 1 : 0;
     }
     __syncthreads();
@@ -1179,7 +1375,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
 
     // MDF relaxation 1/||A||_inf (Sec. 2.5.2): sum_m A_lm = ds sum_x D_l(x) W(x),
     // W(x) = sum_m D_m(x); computed once on the first step.
-    if (part != IB_SPREAD && scheme == SCH_MDF && !B.st.omega_valid) {
+    if ((part & IBP_SETUP) && scheme == SCH_MDF && !B.st.omega_valid) {
         for (int q = tid; q < nfp; q += kIbThreads) {
             R w = R(0);
             for (int o = B.csr_off[q]; o < B.csr_off[q + 1]; ++o) w += cw[o];
@@ -1203,10 +1399,10 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         }
         __syncthreads();
     }
-    if (L.mode == 1) return;
+    if (L.mode == 1) return false;
 
     // DFC lambda_k of Eq. 17; W_total sums the markers of every DFC body of the case.
-    if (scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
+    if ((part & IBP_SETUP) && scheme == SCH_DFC && !(B.lam_valid && C.dfc_all_fixed)) {
         for (int q = tid; q < nfp; q += kIbThreads) {
             const int node = B.fp_node[q];
             const int x = bx0 + node % bw, y = B.by0 + node / bw;
@@ -1240,62 +1436,9 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         if (tid == 0) B.lam_valid = 1;
     }
 
-    if (part != IB_SPREAD) {
-    // gather the post-streaming state at every footprint node
-    const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
-    // GB footprint nodes per thread at a time: their pulls are issued together
-    // (interior nodes pull directly; nodes on a lattice edge take the domain conditions)
-    constexpr int GB = sizeof(R) == 8 ? 2 : 4;
-    const int by0 = B.by0, cnx = C.nx, cny = C.ny, cpitch = C.pitch;
-    const long long cplane = C.plane;
-    for (int q0 = tid; q0 < nfp; q0 += GB * kIbThreads) {
-        int gx[GB], gy[GB];
-        bool live[GB], inner[GB];
-#pragma unroll
-        for (int u = 0; u < GB; ++u) {
-            const int q = q0 + u * kIbThreads;
-            live[u] = q < nfp;
-            const int node = live[u] ? B.fp_node[q] : 0;
-            gx[u] = bx0 + node % bw;
-            gy[u] = by0 + node / bw;
-            inner[u] = live[u] && gx[u] >= 1 && gx[u] <= cnx - 2 && gy[u] >= 1 && gy[u] <= cny - 2;
-        }
-        R sb[GB][9];
-#pragma unroll
-        for (int u = 0; u < GB; ++u)
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                sb[u][i] = inner[u] ? ld1(src + i * cplane + (long long)(gy[u] - ey(i)) * cpitch + (gx[u] - ex(i)))
-                                    : R(0);
-#pragma unroll
-        for (int u = 0; u < GB; ++u) {
-            if (!live[u]) continue;
-            if (!inner[u]) post_stream_node<S, R>(C, src, gx[u], gy[u], sb[u]);
-            const R* s = sb[u];
-            R* o = fp + (size_t)(q0 + u * kIbThreads) * 9;
-        if (scheme == SCH_DFC) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) o[i] = s[i];
-        } else {
-            R drho = R(0), jx = R(0), jy = R(0);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                drho += s[i];
-                jx += R(ex(i)) * s[i];
-                jy += R(ey(i)) * s[i];
-            }
-            const R rho = R(1) + drho;
-            o[0] = rho;
-            o[1] = jx / rho;
-            o[2] = jy / rho;
-            o[3] = o[1];
-            o[4] = o[2];
-        }
-        }
-    }
-    }
+    if (part & IBP_GATHER) ib_gather<S>(C, B, tid, kIbThreads);
     __syncthreads();
-    if (part == IB_GATHER) return;
+    if (!(part & IBP_FORCES)) return true;
 
     // force and torque on the body (Sec. 2.7), accumulated in FP64 by each thread as its
     // markers' forces are final (ascending k per thread), reduced at the end
@@ -1307,7 +1450,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         gys += gy;
         ts += rx * gy - ry * gx;
     };
-    if (part == IB_SPREAD) {
+    if (part & IBP_PRESET) {
         // marker forces already final (coupled MDF): mk[16k + 0..1] and B.Fx, B.Fy
         for (int k = tid; k < n; k += kIbThreads) body_force(k, -B.Fx[k] * B.ds, -B.Fy[k] * B.ds);
     } else if (scheme == SCH_DF) {
@@ -1626,6 +1769,7 @@ __device__ __forceinline__ void ib_run(const IbLaunch& L, const BodyRef& ref, in
         B.hist[3 * h + 2] = Th;
         B.st.hist_n = B.st.hist_n + 1;
     }
+    return true;
 }
 
 __device__ void body_prepare(BodyDev& B, double* sh);
@@ -1861,7 +2005,11 @@ __device__ void mdf_coupled(const CaseDev& C, int* shi, double* shd) {
 template <class S>
 __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     if (L.pdl & PDL_TRIGGER) pdl_trigger();
-    const BodyRef ref = L.refs[blockIdx.x];
+    // L.cluster CTAs per body (a thread-block cluster): rank 0 runs the body's IB stage,
+    // the others share the gather of the footprint nodes with it
+    const int G = L.cluster > 1 ? L.cluster : 1;
+    const int rank = G > 1 ? (int)cluster_rank() : 0;
+    const BodyRef ref = L.refs[blockIdx.x / G];
     using R = typename Traits<S>::R;
     static_assert(kIbThreads == 512, "IbSmem sizes sF for 512 markers");
     __shared__ int shi[2 * kIbThreads + 4];
@@ -1874,9 +2022,10 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     int* sEk = reinterpret_cast<int*>(sQc + kMdfNodeCap);
     int* sQo = sEk + kMdfEntryCap;
     const CaseDev& C = *ref.c;
+    const int SX = ref.b->S;
     if (L.mode == 0 && C.n_mdf >= 2 && ref.b->scheme == SCH_MDF) {
         // coupled MDF: the CTA of the first MDF body steps all of them
-        if (ref.index != C.mdf_lead) return;
+        if (ref.index != C.mdf_lead || rank != 0) return;
         if (!L.prepared)
             for (int b = 0; b < C.nbodies; ++b)
                 if (C.bodies[b].scheme == SCH_MDF) body_prepare(C.bodies[b], shd);
@@ -1899,13 +2048,33 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
         }
         return;
     }
-    if (L.mode == 0 && !L.prepared) body_prepare(*ref.b, shd);
-    if (ref.b->S == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
-    else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
-    if (L.mode == 0) {
-        __syncthreads();
-        if (threadIdx.x == 0) body_finish(*ref.b);
+    if (L.mode != 0) {   // set-up only: footprint and omega_MDF at the initial markers
+        if (rank != 0) return;
+        if (SX == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
+        else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
+        return;
     }
+    // body motion and set-up (rank 0), gather (every rank), forces, spread, sums and the
+    // body update (rank 0).  The ranks' gathered values reach rank 0 through global memory,
+    // ordered by the cluster barrier (release / acquire at cluster scope).
+    bool ok = true;
+    if (rank == 0) {
+        if (!L.prepared) body_prepare(*ref.b, shd);
+        ok = SX == 2 ? ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_SETUP)
+                     : ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_SETUP);
+    }
+    if (G > 1) cluster_sync_all();
+    // (a body whose footprint could not be built has nfp = 0: nothing to gather)
+    if (ok) ib_gather<S>(C, *ref.b, rank * kIbThreads + (int)threadIdx.x, G * kIbThreads);
+    if (G > 1) cluster_sync_all();
+    else __syncthreads();
+    if (rank != 0) return;
+    if (ok) {
+        if (SX == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_FORCES);
+        else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_FORCES);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) body_finish(*ref.b);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2385,8 +2554,71 @@ static cudaError_t launch_ib_s(const IbLaunch& L, cudaStream_t st) {
     static const cudaError_t attr = cudaFuncSetAttribute(reinterpret_cast<const void*>(&ib_kernel<S>),
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (attr != cudaSuccess) return attr;
+#ifndef IBLBM_EMULATE
+    if (L.cluster > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(L.nrefs * L.cluster);
+        cfg.blockDim = dim3(kIbThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = L.cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, ib_kernel<S>, L);
+        return cudaGetLastError();
+    }
+#endif
     IBLBM_LAUNCH_SMEM(ib_kernel<S>, L.nrefs, kIbThreads, smem, st, L);
     return cudaGetLastError();
+}
+
+template <class S>
+static int ib_cluster_size_s(int nrefs, int sm_budget) {
+#ifdef IBLBM_EMULATE
+    (void)nrefs; (void)sm_budget;
+    return 1;
+#else
+    constexpr int smem = IbSmem<typename Traits<S>::R>::bytes;
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&ib_kernel<S>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    for (int g = 8; g >= 2; g /= 2) {
+        if ((long long)nrefs * g > sm_budget) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nrefs * g);
+        cfg.blockDim = dim3(kIbThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = g;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, ib_kernel<S>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nc >= nrefs) return g;
+    }
+    return 1;
+#endif
+}
+
+int ib_cluster_size(int storage, int nrefs, int sm_budget) {
+    if (nrefs <= 0) return 1;
+    switch (storage) {
+    case ST_F64: return ib_cluster_size_s<double>(nrefs, sm_budget);
+    case ST_F32: return ib_cluster_size_s<float>(nrefs, sm_budget);
+    default: return ib_cluster_size_s<__half>(nrefs, sm_budget);
+    }
 }
 
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st) {

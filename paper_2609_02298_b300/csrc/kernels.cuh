@@ -28,14 +28,35 @@ constexpr int kIbAlign = 128;
 // the previous one ends and waits for it (griddepcontrol.wait) before it exits.
 enum { PDL_TRIGGER = 1, PDL_DEPENDENT = 2 };
 
+// Lattice-edge nodes: chunk k covers edge nodes [first, end) of case c (at most
+// L.block of them); launched after the stream-collide launches of the step.
+struct EdgeChunk {
+    int c, first, end, pad_;
+};
+
 struct ScLaunch {
     CaseDev** cases;
     long long* job_off;
     int ncases;
     int block;   // threads per CTA for the scalar variants (0: kThreads)
-    const int4* list;   // SC_LIST: segment (x = index into cases, y = row, z = first node)
+    const int4* list;   // IB-region segments (x = index into cases, y = row, z = first node)
     int phase;          // SC_ALL, SC_SKIP_IB or SC_LIST
     int pdl;            // PDL_* flags
+    // SC_SKIP_IB with tail_ctas > 0: the last tail_ctas CTAs of the grid (dispatched last,
+    // onto the SMs the IB stage gives back) sweep no segment outside the IB regions; they
+    // wait for the IB stage to end (griddepcontrol.wait), then sweep the nlist listed
+    // IB-region segments and -- in the last launch of a step -- the lattice-edge nodes
+    // (echunks: 32-node chunks of ecases), one warp per segment or chunk.  The last CTA to
+    // finish (done[0] counts finished CTAs and is reset) advances the step counter of every
+    // case in count_cases.
+    int tail_ctas;
+    long long nlist;
+    const EdgeChunk* echunks;
+    CaseDev** ecases;
+    int nechunks;
+    int ncount;
+    CaseDev** count_cases;
+    unsigned* done;
 };
 
 struct IbLaunch {
@@ -46,6 +67,8 @@ struct IbLaunch {
     int pdl;        // PDL_* flags (PDL_TRIGGER only)
     int prepared;   // 1: body motion of the step already done by launch_prepare (another
                     // body's IB CTA reads these markers: DFC W_total over several bodies)
+    int cluster;    // CTAs per body (a thread-block cluster, 1-8; 0 or 1: one CTA); the
+                    // others share the body's footprint gather with the first
 };
 
 // host-side launchers (kernels.cu)
@@ -66,11 +89,6 @@ __host__ __device__ inline bool in_ib_region(int y, int xseg, int bx0, int by0, 
 }
 int sc_segment(int storage, int variant);
 bool sc_variant_ok(int variant, const void* f0, const void* f1);   // alignment a variant needs
-// Lattice-edge nodes: chunk k covers edge nodes [first, end) of case c (at most
-// L.block of them); launched after the stream-collide launches of the step.
-struct EdgeChunk {
-    int c, first, end, pad_;
-};
 struct EdgeLaunch {
     CaseDev** cases;
     EdgeChunk* chunks;
@@ -88,6 +106,9 @@ struct EdgeLaunch {
 cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
+// CTAs per body for an IB launch over nrefs bodies of this storage type: the largest of
+// 8, 4, 2 whose clusters all fit on the GPU at once within sm_budget SMs, else 1
+int ib_cluster_size(int storage, int nrefs, int sm_budget);
 // body motion of the step (first half of Eq. 23, markers, U_d) for every body, one CTA
 // each, before an IB launch with IbLaunch.prepared = 1
 cudaError_t launch_prepare(BodyRef* refs, int nrefs, cudaStream_t st);
