@@ -87,26 +87,43 @@ def sweep_traffic(L, specs):
 
 
 def launches_per_step(specs, L=None) -> int:
-    """Kernel launches of one batched step: one IB launch per storage type with bodies
-    (body motion folded in), one stream-collide launch per (storage, collision) group,
-    and -- when at most eight bodies, all fixed, of one storage type and the tuned sweeps
-    are the one- or two-node-per-lane kernels, so the IB stage overlaps the sweep -- one
-    launch per group with bodies for the IB-region segments; then one lattice-edge launch
-    per storage type and the step-counter launch (folded into the edge launch in that
-    order when there is one storage type)."""
+    """Kernel launches of one batched step, following the library's launch orders: one IB
+    launch per storage type with bodies (body motion folded in; one more before it when a
+    lattice holds several DFC bodies and one of them moves) and one stream-collide launch
+    per (storage, collision) group.  With one storage type the last stream-collide launch
+    also takes the lattice edges and the step end in its tail CTAs (its variant has them:
+    the one- or two-node-per-lane kernels) -- unless no body can reach a lattice edge, when
+    the edges run beside the IB stage in a launch of their own.  When at most eight bodies,
+    all fixed, of one storage type sit on at least 2^20 nodes, the IB stage runs beside the
+    sweep and each group's sweep also takes its IB-region segments.  Otherwise add a
+    lattice-edge launch per storage type and the step-counter launch (and, in the overlap
+    order, an IB-region launch per group with bodies)."""
     storages = {s.storage for s in specs}
     with_bodies = {s.storage for s in specs if s.bodies}
-    groups = {(s.storage, s.collision) for s in specs}
-    n = len(with_bodies) + len(groups) + len(storages) + 1
-    fixed = all(b.motion == W.FIXED for s in specs for b in s.bodies)
-    phased = L is None or all(L.kernel_variant(st, col)[0] in (1, 2) for st, col in groups)
-    nbodies = sum(len(s.bodies) for s in specs)
+    groups = sorted({(s.storage, s.collision) for s in specs})
+    bodies = [(s, b) for s in specs for b in s.bodies]
+    fixed = all(b.motion == W.FIXED for _, b in bodies)
+    variant = {g: (L.kernel_variant(*g)[0] if L is not None else 2) for g in groups}
+    phased = all(v in (1, 2) for v in variant.values())
     large = sum(s.nodes for s in specs) >= (1 << 20)
-    if len(with_bodies) == 1 and 0 < nbodies <= 8 and fixed and phased and large:
-        n += len({(s.storage, s.collision) for s in specs if s.bodies})
+    prepare = any(sum(1 for b in s.bodies if b.scheme == W.DFC) >= 2 and
+                  any(b.motion != W.FIXED for b in s.bodies) for s in specs)
+    n = len(with_bodies) + len(groups) + (1 if prepare else 0)
+    if len(with_bodies) == 1 and 0 < len(bodies) <= 8 and fixed and phased and large:
         if len(storages) == 1:
-            n -= 1   # the edge launch advances the step counters itself
-    return n
+            return n
+        return n + len({(s.storage, s.collision) for s in specs if s.bodies}) + len(storages) + 1
+
+    def clear(s, b):
+        xy = np.asarray(b.xy, dtype=float).reshape(-1, 2)
+        m = float(np.max(np.hypot(xy[:, 0] - b.xc, xy[:, 1] - b.yc))) + 4.0 if len(xy) else 4.0
+        return (b.motion == W.FIXED and b.xc - m > 1.0 and b.yc - m > 1.0 and b.xc + m < s.nx - 2.0
+                and b.yc + m < s.ny - 2.0)
+
+    early = all(clear(s, b) for s, b in bodies) and all(v != 0 for v in variant.values())
+    if len(storages) == 1 and variant[groups[-1]] in (1, 2):
+        return n + (1 if early else 0)
+    return n + len(storages) + 1
 
 
 def shard(items, rank: int, world: int):

@@ -291,6 +291,12 @@ int iblbm_set_kernel_variant(int storage, int collision, int variant);
  * lowered leaves the lattice's populations undefined.  Syncs the device.
  * Errors: CUDA. */
 int iblbm_test_set_consumer_poll_limit(long polls);
+/* Test hook: enable != 0 (the default) lets the IB stage of a fixed DF or DFC body with a
+ * cached footprint take its fast path (static data in registers and shared memory, the
+ * gathered state in shared memory); 0 sends every body through the general path.  Both
+ * compute the same values in the same order, so the results are bitwise equal; tests
+ * check that.  Process-wide.  Syncs the device.  Errors: CUDA. */
+int iblbm_test_set_ib_fast(int enable);
 int iblbm_kernel_variant(int storage, int collision, int* variant, double* ms);
 
 /* ---- serving loop ---------------------------------------------------------------------- */

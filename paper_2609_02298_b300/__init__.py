@@ -91,6 +91,7 @@ SIGNATURES = [
     ("iblbm_set_kernel_variant", _i, [_i, _i, _i]),
     ("iblbm_kernel_variant", _i, [_i, _i, _pi, _pd]),
     ("iblbm_test_set_consumer_poll_limit", _i, [C.c_long]),
+    ("iblbm_test_set_ib_fast", _i, [_i]),
     ("iblbm_server_create", _i, [_sz, _i, _vp, _P(_vp)]),
     ("iblbm_server_destroy", None, [_vp]),
     ("iblbm_server_submit", _i, [_vp, _P(LatticeDesc), _i, _d, _P(BodyDesc), _pd, _i, _d, _i, _i, _i,
@@ -428,6 +429,11 @@ KERNEL_VARIANTS = 4   # IBLBM_KERNEL_VARIANTS
 def test_set_consumer_poll_limit(polls: int) -> None:
     """Test hook: polls after which the bulk sweep's consumers give up (negative: default)."""
     _check(load_library().iblbm_test_set_consumer_poll_limit(int(polls)), "iblbm_test_set_consumer_poll_limit")
+
+
+def test_set_ib_fast(enable: bool) -> None:
+    """Test hook: False sends every IB stage through the general path (default True)."""
+    _check(load_library().iblbm_test_set_ib_fast(1 if enable else 0), "iblbm_test_set_ib_fast")
 
 
 def kernel_variant(storage: int, collision: int):

@@ -907,9 +907,10 @@ struct BatchPlan {
     // DFC body's markers, so all bodies move in a launch of their own before the IB stage.
     bool prepare_first = false;
     unsigned* ddone = nullptr;                 // finished-CTA count of the step-ending launch
-    // Overlap order with one storage type: each group's sweep takes its IB-region segments
-    // after the IB stage, and the last one the lattice edges (32-node chunks) and the end of
-    // the step, so that a step is the IB launch and one launch per group.
+    // One storage type: the last sweep launch of a step takes the lattice edges (32-node
+    // chunks) and the end of the step in its tail CTAs; in the overlap order each group's
+    // sweep also takes its IB-region segments after the IB stage.  A step is then the IB
+    // launch and one launch per group.
     bool fused_tail = false;
     EdgeChunk* dechunks32 = nullptr;
     int nechunks32 = 0;
@@ -995,6 +996,10 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     }
     const bool dependent = overlap && !P->ib_groups.empty();
     const bool fused = dependent && P->fused_tail;
+    // launch-by-launch order: the last sweep launch ends the step (edges unless they ran
+    // beside the IB stage, step counters) when its variant has the tail form
+    const bool serial_tail = !overlap && !timer && P->fused_tail && !P->groups.empty() &&
+                             sc_variant_phased(chosen_variant(P->groups.back()));
     for (size_t gi = 0; gi < P->groups.size(); ++gi) {
         const auto& g = P->groups[gi];
         const int v = chosen_variant(g);
@@ -1021,12 +1026,27 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
             sl.tail_ctas = tail_jobs > 0 ? (int)std::max<long long>(1, (tail_jobs + wpc - 1) / wpc) : 0;
             grid += sl.tail_ctas;
         }
+        if (serial_tail && gi + 1 == P->groups.size()) {
+            if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // the edges precede the step end
+            sl.phase = SC_ALL_TAIL;
+            if (!early) {
+                sl.echunks = P->dechunks32;
+                sl.ecases = P->edge_groups[0].dcases;
+                sl.nechunks = P->nechunks32;
+            }
+            sl.count_cases = P->dcases_all;
+            sl.ncount = (int)P->ctxs.size();
+            sl.done = P->ddone;
+            const int wpc = (g.block[v] > 0 ? g.block[v] : kThreads) / 32;
+            sl.tail_ctas = sl.nechunks > 0 ? (int)std::max<long long>(1, (sl.nechunks + wpc - 1) / wpc) : 0;
+            grid += sl.tail_ctas;
+        }
         if ((e = timed_launch(timer, STAGE_SWEEP, st, [&] {
                  return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], grid, st);
              })) != cudaSuccess)
             return e;
     }
-    if (fused) return cudaSuccess;
+    if (fused || serial_tail) return cudaSuccess;
     // with one edge group the edge launch of the overlap order runs beside the IB-region
     // launches and advances the step counters itself
     const bool edges_end = overlap && P->edge_groups.size() == 1 && P->ddone;
@@ -1055,7 +1075,7 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
 // sweep beside it gives up (so all the sweep's CTAs run at once and its static job
 // split stays balanced); beyond that the SMs given up cost more than the overlap saves.
 constexpr int kOverlapMaxBodies = 8;
-constexpr int kOverlapIbSms = 8;
+constexpr int kOverlapIbSms = 16;
 
 int build_ib_lists(BatchPlan* P, int sms) {
     P->overlap_ok = false;
@@ -1122,26 +1142,6 @@ int build_ib_lists(BatchPlan* P, int sms) {
             cudaMemcpyAsync(lg.dlist[v], list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, P->st);
         }
         if (any) P->list_groups.push_back(lg);
-    }
-    // one storage type: the lattice edges in 32-node chunks (one warp each), in the order of
-    // the edge group's cases, for the tail of the last sweep launch
-    if (P->edge_groups.size() == 1 && P->ddone) {
-        std::vector<EdgeChunk> chunks;
-        int ci = 0;
-        for (auto* c : P->ctxs) {
-            if (c->hc.storage != P->edge_groups[0].storage) continue;
-            const int ne = (int)lattice_edge_nodes(c->hc.nx, c->hc.ny);
-            for (int f = 0; f < ne; f += 32) chunks.push_back(EdgeChunk{ci, f, std::min(ne, f + 32), 0});
-            ++ci;
-        }
-        if (!chunks.empty()) {
-            P->dechunks32 = static_cast<EdgeChunk*>(plan_alloc(P, sizeof(EdgeChunk) * chunks.size()));
-            if (!P->dechunks32) return IBLBM_ERR_OOM;
-            cudaMemcpyAsync(P->dechunks32, chunks.data(), sizeof(EdgeChunk) * chunks.size(), cudaMemcpyHostToDevice,
-                            P->st);
-            P->nechunks32 = (int)chunks.size();
-            P->fused_tail = true;
-        }
     }
     rc = check(cudaStreamSynchronize(P->st));
     if (rc) return rc;
@@ -1265,6 +1265,26 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
     P->ddone = static_cast<unsigned*>(plan_alloc(P, sizeof(unsigned)));
     if (!P->ddone) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
     cudaMemsetAsync(P->ddone, 0, sizeof(unsigned), P->st);
+    // one storage type: the lattice edges in 32-node chunks (one warp each), in the order of
+    // the edge group's cases, for the tail of the last sweep launch
+    if (P->edge_groups.size() == 1 && P->ddone) {
+        std::vector<EdgeChunk> chunks;
+        int ci = 0;
+        for (auto* c : P->ctxs) {
+            if (c->hc.storage != P->edge_groups[0].storage) continue;
+            const int ne = (int)lattice_edge_nodes(c->hc.nx, c->hc.ny);
+            for (int f = 0; f < ne; f += 32) chunks.push_back(EdgeChunk{ci, f, std::min(ne, f + 32), 0});
+            ++ci;
+        }
+        if (!chunks.empty()) {
+            P->dechunks32 = static_cast<EdgeChunk*>(plan_alloc(P, sizeof(EdgeChunk) * chunks.size()));
+            if (!P->dechunks32) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
+            cudaMemcpyAsync(P->dechunks32, chunks.data(), sizeof(EdgeChunk) * chunks.size(), cudaMemcpyHostToDevice,
+                            P->st);
+            P->nechunks32 = (int)chunks.size();
+            P->fused_tail = true;
+        }
+    }
     P->nrefs_all = (int)all_refs.size();
     P->drefs_all = static_cast<BodyRef*>(plan_alloc(P, sizeof(BodyRef) * std::max<size_t>(1, all_refs.size())));
     P->dcases_all = static_cast<CaseDev**>(plan_alloc(P, sizeof(CaseDev*) * all_cases.size()));
@@ -1389,6 +1409,14 @@ extern "C" int iblbm_set_kernel_variant(int storage, int collision, int variant)
 
 extern "C" int iblbm_test_set_consumer_poll_limit(long polls) {
     if (cudaDeviceSynchronize() != cudaSuccess || set_consumer_poll_limit(polls) != cudaSuccess) {
+        cudaGetLastError();
+        return IBLBM_ERR_CUDA;
+    }
+    return IBLBM_OK;
+}
+
+extern "C" int iblbm_test_set_ib_fast(int enable) {
+    if (cudaDeviceSynchronize() != cudaSuccess || set_ib_fast(enable) != cudaSuccess) {
         cudaGetLastError();
         return IBLBM_ERR_CUDA;
     }

@@ -156,6 +156,32 @@ __device__ __forceinline__ float ld1_sweep(const float* p) {
 #endif
 }
 
+// The same loads with an L2 evict-first hint, for the sweep that runs beside the IB
+// stage: the streamed planes then give way in L2 before the IB stage's code and data.
+__device__ __forceinline__ double ld1_sweep_ef(const double* p) {
+#ifdef IBLBM_EMULATE
+    return *p;
+#else
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+#endif
+}
+__device__ __forceinline__ float ld1_sweep_ef(const float* p) {
+#ifdef IBLBM_EMULATE
+    return *p;
+#else
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    float v;
+    asm("ld.global.nc.L2::cache_hint.L2::256B.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+#endif
+}
+__device__ __forceinline__ float ld1_sweep_ef(const __half* p) { return ld1_sweep(p); }
+
 // FP16 storage, two adjacent nodes per 32-bit word (the pair sweep): read-only load
 // with the same 256-byte L2 fetch as the FP32 sweep, the unpacking to FP32, and the
 // store of two correctly rounded values.
@@ -189,6 +215,28 @@ __device__ __forceinline__ void st1(__half* p, float v) { *p = __float2half_rn(v
 __device__ __forceinline__ void st1_sweep(double* p, double v) { st1(p, v); }
 __device__ __forceinline__ void st1_sweep(__half* p, float v) { st1(p, v); }
 __device__ __forceinline__ void st1_sweep(float* p, float v) { *p = v; }
+// Store with an L2 evict-last hint: the IB-region populations written at the end of a
+// step are the ones the next step's IB stage gathers first, while the sweep beside it
+// streams the rest of the lattice through L2.
+__device__ __forceinline__ void st1_keep(double* p, double v) {
+#ifdef IBLBM_EMULATE
+    *p = v;
+#else
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+#endif
+}
+__device__ __forceinline__ void st1_keep(float* p, float v) {
+#ifdef IBLBM_EMULATE
+    *p = v;
+#else
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+#endif
+}
+__device__ __forceinline__ void st1_keep(__half* p, float v) { st1(p, v); }
 // One correctly rounded conversion from double (no double rounding through float).
 __device__ __forceinline__ void st1_from_double(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st1_from_double(float* p, double v) { *p = (float)v; }

@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(kThreads, (ScMinBlocks<S, KIND>::value)) sc_ke
 // B300: a boundary branch inside the sweep costs a third of the HBM rate).
 // 32-bit element offsets with per-population constants; the Guo term only on rows
 // that carry a force.
-template <class S, int KIND, int NPT>
+// KEEP: the stores carry an L2 evict-last hint (IB-region segments, st1_keep); EVF: the
+// loads an L2 evict-first hint (the sweep beside the IB stage, ld1_sweep_ef).
+template <class S, int KIND, int NPT, bool KEEP = false, bool EVF = false>
 __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xseg, int lane) {
     using R = typename Traits<S>::R;
     const CaseDev& C = *K.C;
@@ -368,7 +370,10 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
             R s[9];
             const int a = row + x;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) s[i] = ld1_sweep(src + (a + koff[i]));
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (EVF) s[i] = ld1_sweep_ef(src + (a + koff[i]));
+                else s[i] = ld1_sweep(src + (a + koff[i]));
+            }
             R rho;
             if (forced) {
                 R Fx = K.gfx, Fy = K.gfy;
@@ -379,7 +384,10 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
             }
             unstable |= bad_density(rho);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) st1_sweep(dst + (a + i * plane), s[i]);
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (KEEP) st1_keep(dst + (a + i * plane), s[i]);
+                else st1_sweep(dst + (a + i * plane), s[i]);
+            }
         }
     }
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
@@ -473,10 +481,10 @@ template <int KIND, int NPT> struct ScScalarMinBlocks<double, KIND, NPT> { stati
 // for FP16 storage (sc_row_pair).
 template <class S, int NPT> struct ScSeg { static constexpr int value = 32 * NPT; };
 template <int NPT> struct ScSeg<__half, NPT> { static constexpr int value = 64 * NPT; };
-template <class S, int KIND, int NPT>
+template <class S, int KIND, int NPT, bool KEEP = false, bool EVF = false>
 __device__ __forceinline__ void sc_row_nodes(const ScCase<S>& K, int y, int xseg, int lane) {
     if constexpr (std::is_same<S, __half>::value) sc_row_pair<KIND, NPT>(K, y, xseg, lane);
-    else sc_row_scalar<S, KIND, NPT>(K, y, xseg, lane);
+    else sc_row_scalar<S, KIND, NPT, KEEP, EVF>(K, y, xseg, lane);
 }
 
 // Lattice-edge node e of a case (rows 0 and ny-1, columns 0 and nx-1): pull with wrap and
@@ -584,7 +592,7 @@ __device__ __forceinline__ void sc_tail(const ScLaunch& L, int w, int nw, int la
                 K.load(c);
                 cur = c;
             }
-            sc_row_nodes<S, KIND, NPT>(K, e.y, e.z, lane);
+            sc_row_nodes<S, KIND, NPT, true>(K, e.y, e.z, lane);
         } else {
             const EdgeChunk ch = L.echunks[j - L.nlist];
             const CaseDev* c = L.ecases[ch.c];
@@ -598,19 +606,20 @@ __device__ __forceinline__ void sc_tail(const ScLaunch& L, int w, int nw, int la
     }
 }
 
-// SKIP: the launch beside the IB stage (segments in IB regions left out, programmatic
-// dependent launch); the whole-lattice launch is compiled without any of it.
-template <class S, int KIND, int NPT, bool SKIP>
+// MODE (SC_MODE_*): SKIP, the launch beside the IB stage (segments in IB regions left out,
+// programmatic dependent launch) with tail CTAs; TAIL, every segment plus tail CTAs for the
+// lattice edges and the step end; the plain whole-lattice launch is compiled without either.
+template <class S, int KIND, int NPT, int MODE>
 __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::value))
     sc_kernel_scalar(ScLaunch L, long long jobs) {
     constexpr int kSegW = ScSeg<S, NPT>::value;
+    constexpr bool SKIP = MODE == SC_MODE_SKIP, TAIL = MODE != SC_MODE_PLAIN;
     if (SKIP && (L.pdl & PDL_TRIGGER)) pdl_trigger();
     const int lane = threadIdx.x & 31;
-    // with tail CTAs (SKIP only) the segments outside the IB regions are split over the
-    // other CTAs
-    const int nblk = SKIP ? (int)gridDim.x - L.tail_ctas : (int)gridDim.x;
+    // with tail CTAs the segments of the first phase are split over the other CTAs
+    const int nblk = TAIL ? (int)gridDim.x - L.tail_ctas : (int)gridDim.x;
     const int wpc = (int)blockDim.x >> 5;
-    if (SKIP && (int)blockIdx.x >= nblk) {
+    if (TAIL && (int)blockIdx.x >= nblk) {
         sc_tail<S, KIND, NPT>(L, ((int)blockIdx.x - nblk) * wpc + ((int)threadIdx.x >> 5), L.tail_ctas * wpc, lane);
         if (L.done) end_step_if_last(L.done, L.count_cases, L.ncount);
         return;
@@ -636,10 +645,10 @@ __global__ void __launch_bounds__(kThreads, (ScScalarMinBlocks<S, KIND, NPT>::va
         const int y = local / nseg;
         const int xseg = (local - y * nseg) * kSegW;
         if (SKIP && K.nbodies > 0 && seg_in_ib(*K.C, y, xseg)) continue;
-        sc_row_nodes<S, KIND, NPT>(K, y, xseg, lane);
+        sc_row_nodes<S, KIND, NPT, false, SKIP>(K, y, xseg, lane);
     }
     if (SKIP && L.tail_ctas == 0 && (L.pdl & PDL_DEPENDENT)) pdl_wait();
-    if (SKIP && L.done) end_step_if_last(L.done, L.count_cases, L.ncount);
+    if (TAIL && L.done) end_step_if_last(L.done, L.count_cases, L.ncount);
 }
 
 // The SC_LIST phase: the listed segments (IB regions), warp w taking entries w, w + W, ...
@@ -1007,24 +1016,30 @@ __device__ __forceinline__ double block_max_sqrt(double e2, double* sh) {
 // Three FP64 sums in a fixed order: every thread parks its partials in shared memory
 // and one warp adds them (lane l takes slots l, l + 32, ...), then a butterfly; few
 // FP64 instructions, since FP64 arithmetic is scarce on B300.  sh holds 3 kIbThreads.
+// The adding warp's part: lane l sums slots l, l + 32, ... of each array, then a butterfly
+// (every lane ends with the totals).
+__device__ __forceinline__ void warp_sum3(const double* sh, int lane, double& x, double& y, double& z) {
+    x = 0.0; y = 0.0; z = 0.0;
+    for (int i = lane; i < kIbThreads; i += 32) {
+        x += sh[i];
+        y += sh[kIbThreads + i];
+        z += sh[2 * kIbThreads + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+}
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     __syncthreads();
     sh[t] = a; sh[kIbThreads + t] = b; sh[2 * kIbThreads + t] = c;
     __syncthreads();
     if (w == 0) {
-        double x = 0.0, y = 0.0, z = 0.0;
-        for (int i = lane; i < kIbThreads; i += 32) {
-            x += sh[i];
-            y += sh[kIbThreads + i];
-            z += sh[2 * kIbThreads + i];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-            z += __shfl_xor_sync(0xffffffffu, z, o);
-        }
+        double x, y, z;
+        warp_sum3(sh, lane, x, y, z);
         __syncwarp();
         if (lane == 0) { sh[0] = x; sh[1] = y; sh[2] = z; }
     }
@@ -1267,9 +1282,12 @@ constexpr int kMdfNodeCap = 2048; // footprint nodes whose MDF iterate fits in s
 constexpr int kMdfEntryCap = 4096; // node->marker entries staged in shared memory for MDF
 // Dynamic shared memory of ib_kernel: sU (2 per node), sF (2 per marker), sEw (per
 // entry), then sEk (per entry, int).
+// The fixed-body fast path (ib_fast) uses up to kFastSmem bytes of the same region.
+constexpr int kFastSmem = 160 * 1024;
 template <class R> struct IbSmem {
-    static constexpr int bytes = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap + kMdfNodeCap) * (int)sizeof(R) +
-                                 (kMdfEntryCap + kMdfNodeCap + 1) * 4;
+    static constexpr int mdf = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap + kMdfNodeCap) * (int)sizeof(R) +
+                               (kMdfEntryCap + kMdfNodeCap + 1) * 4;
+    static constexpr int bytes = mdf > kFastSmem ? mdf : kFastSmem;
 };
 
 // Parts of the per-body IB stage, as bits: set-up (footprint, omega_MDF, DFC lambda_k),
@@ -1751,9 +1769,15 @@ __device__ __forceinline__ bool ib_run(const IbLaunch& L, const BodyRef& ref, in
                     }
             }
         }
+        // (a DF or MDF patch is read as the force only: p[0], p[1])
         R* o = patch + (size_t)q * 9;
+        if (scheme == SCH_DFC) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o[i] = p[i];
+            for (int i = 0; i < 9; ++i) o[i] = p[i];
+        } else {
+            o[0] = p[0];
+            o[1] = p[1];
+        }
     }
 
     // body force and torque: fixed-order reduction of the per-thread sums
@@ -2002,6 +2026,344 @@ __device__ void mdf_coupled(const CaseDev& C, int* shi, double* shd) {
 
 // One CTA per body.  Mode 0 (a step): body motion (body_prepare), the IB stage, then the
 // end-of-step body update (body_finish); mode 1: footprint and omega_MDF only.
+// ------------------------------------------------------------------------------------------
+// IB stage of a fixed DF or DFC body with a cached footprint (the fast path).  The body's
+// static data -- each footprint slot's node, each marker's stencil, weights, desired
+// velocity and position, the node->marker lists -- is fetched in one batch of independent
+// loads, into registers (per marker, per gathered slot) and shared memory (the lists);
+// the gathered state goes straight into rank 0's shared memory (distributed shared memory
+// of the cluster) and the marker forces stay there, so the stage waits on about four
+// global round trips instead of a dozen.  That matters while the sweep beside it keeps
+// the memory system saturated.  Every value is computed by the same expressions in the
+// same order as in ib_gather / ib_run, so the results are bit for bit those of the
+// general path.
+__device__ int g_ib_fast_enabled = 1;   // test knob: 0 forces the general path
+
+// Shared-memory layout of the fast path: gathered state (NV R per slot), marker forces
+// (NM R per marker), list offsets, marker index and weight per list entry.
+template <class R> struct FastLayout {
+    int nv, nm, goff, moff, ooff, eoff, woff, bytes;
+    __device__ FastLayout(int scheme, int nfp, int n, int ne) {
+        nv = scheme == SCH_DFC ? 9 : 3;
+        nm = scheme == SCH_DFC ? 9 : 2;
+        goff = 0;
+        moff = goff + ((nfp * nv * (int)sizeof(R) + 15) & ~15);
+        ooff = moff + ((n * nm * (int)sizeof(R) + 15) & ~15);
+        eoff = ooff + (((nfp + 1) * 4 + 15) & ~15);
+        woff = eoff + ((ne * 4 + 15) & ~15);
+        bytes = woff + ne * (int)sizeof(R);
+    }
+};
+
+template <class S>
+__device__ __forceinline__ bool ib_fast_ok(const CaseDev& C, const BodyDev& B) {
+    using R = typename Traits<S>::R;
+    if (!g_ib_fast_enabled || B.motion != MOT_FIXED || !B.cache_valid || B.nfp <= 0 || B.n > kIbThreads) return false;
+    if (B.scheme == SCH_DFC) {
+        if (!(B.lam_valid && C.dfc_all_fixed)) return false;
+    } else if (B.scheme != SCH_DF) {
+        return false;
+    }
+    const FastLayout<R> F(B.scheme, B.nfp, B.n, B.n * B.S * B.S);
+    return F.bytes <= kFastSmem;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+#ifndef IBLBM_EMULATE
+    return (unsigned)__cvta_generic_to_shared(p);
+#else
+    (void)p;
+    return 0u;
+#endif
+}
+__device__ __forceinline__ unsigned cluster_map0(unsigned a) {
+#ifndef IBLBM_EMULATE
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(r) : "r"(a));
+    return r;
+#else
+    return a;
+#endif
+}
+__device__ __forceinline__ void st_cluster(unsigned a, float v) {
+#ifndef IBLBM_EMULATE
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+#endif
+}
+__device__ __forceinline__ void st_cluster(unsigned a, double v) {
+#ifndef IBLBM_EMULATE
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+#endif
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+#ifndef IBLBM_EMULATE
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void cluster_wait() {
+#ifndef IBLBM_EMULATE
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+#endif
+}
+
+template <class S, int SX>
+__device__ void ib_fast(const IbLaunch& L, const BodyRef& ref, int rank, int G, double* shd, unsigned char* dsm) {
+    using R = typename Traits<S>::R;
+    constexpr int SS = SX * SX;
+    constexpr int GB = sizeof(R) == 8 ? 2 : 4;   // slots per thread whose pulls go out together
+    const CaseDev& C = *ref.c;
+    BodyDev& B = *ref.b;
+    const int tid = threadIdx.x, n = B.n, nfp = B.nfp, ne = n * SS, scheme = B.scheme;
+    const FastLayout<R> F(scheme, nfp, n, ne);
+    R* sG = reinterpret_cast<R*>(dsm + F.goff);
+    R* sM = reinterpret_cast<R*>(dsm + F.moff);
+    int* sO = reinterpret_cast<int*>(dsm + F.ooff);
+    int* sK = reinterpret_cast<int*>(dsm + F.eoff);
+    R* sW = reinterpret_cast<R*>(dsm + F.woff);
+    if (G > 1) cluster_arrive_relaxed();   // (every CTA of the cluster has started: DSMEM below)
+    // ---- one batch of independent loads: this thread's first slots' nodes, and on rank 0
+    // its marker's stencil and weights and its share of the node->marker lists
+    const int T = rank * kIbThreads + tid, NT = G * kIbThreads;
+    int node0[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) node0[u] = T + u * NT < nfp ? B.fp_node[T + u * NT] : 0;
+    const bool own = rank == 0 && tid < n;
+    int sl[SS];
+    R wx[4], wy[4];
+    // U_d, position and lambda_k of this thread's marker: loaded with the batch when the
+    // body motion of the step leaves U_d as it is (a fixed body's usual step), else after it
+    const bool ud_static = B.ud_given || B.ud_current;
+    double udxk = 0.0, udyk = 0.0, xk = 0.0, yk = 0.0, lamk = 0.0;
+    if (own) {
+        xk = B.X[tid];
+        yk = B.Y[tid];
+        if (scheme == SCH_DFC) lamk = B.lam[tid];
+        if (ud_static) {
+            udxk = B.Udx[tid];
+            udyk = B.Udy[tid];
+        }
+    }
+    if (own) {
+        const R* wts = static_cast<const R*>(B.wts);
+#pragma unroll
+        for (int r = 0; r < SS; ++r) sl[r] = B.mslot[tid * SS + r];
+#pragma unroll
+        for (int a = 0; a < SX; ++a) {
+            wx[a] = wts[tid * 8 + a];
+            wy[a] = wts[tid * 8 + 4 + a];
+        }
+    }
+    if (rank == 0) {
+        const R* cw = static_cast<const R*>(B.csr_w);
+        constexpr int EB = 8;   // list entries per thread whose loads go out together
+        for (int o0 = tid; o0 <= nfp; o0 += EB * kIbThreads) {
+            int v[EB];
+#pragma unroll
+            for (int u = 0; u < EB; ++u) v[u] = o0 + u * kIbThreads <= nfp ? B.csr_off[o0 + u * kIbThreads] : 0;
+#pragma unroll
+            for (int u = 0; u < EB; ++u)
+                if (o0 + u * kIbThreads <= nfp) sO[o0 + u * kIbThreads] = v[u];
+        }
+        for (int o0 = tid; o0 < ne; o0 += EB * kIbThreads) {
+            int e[EB];
+            R w[EB];
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+                const int o = o0 + u * kIbThreads;
+                e[u] = o < ne ? B.csr_ent[o] : 0;
+                w[u] = o < ne ? cw[o] : R(0);
+            }
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+                const int o = o0 + u * kIbThreads;
+                if (o < ne) {
+                    sK[o] = e[u] / SS;
+                    sW[o] = w[u];
+                }
+            }
+        }
+        if (!L.prepared) body_prepare(B, shd);   // a fixed body: U_d already current, or set now
+    }
+    // ---- gather (every rank): pulls of this thread's slots, rho and u (DF) or the nine
+    // shifted populations (DFC) into rank 0's shared memory
+    {
+        const S* src = static_cast<const S*>(C.f[(int)(C.step & 1ull)]);
+        const int bx0 = B.bx0, by0 = B.by0, bw = B.bw;
+        const int cnx = C.nx, cny = C.ny, cpitch = C.pitch;
+        const long long cplane = C.plane;
+        const unsigned g0 = G > 1 ? cluster_map0(smem_u32(sG)) : 0u;
+        if (G > 1) cluster_wait();
+        for (int q0 = T; q0 < nfp; q0 += GB * NT) {
+            int gx[GB], gy[GB];
+            bool live[GB], inner[GB];
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+                const int q = q0 + u * NT;
+                live[u] = q < nfp;
+                const int node = !live[u] ? 0 : (q0 == T ? node0[u] : B.fp_node[q]);
+                gx[u] = bx0 + node % bw;
+                gy[u] = by0 + node / bw;
+                inner[u] = live[u] && gx[u] >= 1 && gx[u] <= cnx - 2 && gy[u] >= 1 && gy[u] <= cny - 2;
+            }
+            R sb[GB][9];
+#pragma unroll
+            for (int u = 0; u < GB; ++u)
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    sb[u][i] = inner[u] ? ld1(src + i * cplane + (long long)(gy[u] - ey(i)) * cpitch + (gx[u] - ex(i)))
+                                        : R(0);
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+                if (!live[u]) continue;
+                if (!inner[u]) post_stream_node<S, R>(C, src, gx[u], gy[u], sb[u]);
+                const R* sv = sb[u];
+                const int q = q0 + u * NT;
+                R o[9];
+                int nvals;
+                if (scheme == SCH_DFC) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) o[i] = sv[i];
+                    nvals = 9;
+                } else {
+                    R drho = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        drho += sv[i];
+                        jx += R(ex(i)) * sv[i];
+                        jy += R(ey(i)) * sv[i];
+                    }
+                    const R rho = R(1) + drho;
+                    o[0] = rho;
+                    o[1] = jx / rho;
+                    o[2] = jy / rho;
+                    nvals = 3;
+                }
+                if (G > 1) {
+                    for (int j = 0; j < nvals; ++j) st_cluster(g0 + (unsigned)((q * F.nv + j) * (int)sizeof(R)), o[j]);
+                } else {
+                    for (int j = 0; j < nvals; ++j) sG[q * F.nv + j] = o[j];
+                }
+            }
+        }
+    }
+    if (G > 1) cluster_sync_all();   // the ranks' gathered values are in rank 0's shared memory
+    else __syncthreads();
+    if (rank != 0) return;
+    // ---- marker forces (one marker per thread), FP64 body sums per thread
+    const R ds = R(B.ds);
+    double gxs = 0.0, gys = 0.0, ts = 0.0;
+    if (own) {
+        const int k = tid;
+        R D[SS];
+#pragma unroll
+        for (int r = 0; r < SS; ++r) D[r] = wx[r % SX] * wy[r / SX];
+        if (!ud_static) {
+            udxk = B.Udx[k];
+            udyk = B.Udy[k];
+        }
+        const double bxc = B.st.xc, byc = B.st.yc;
+        const double rx = xk - bxc, ry = yk - byc;
+        R* mk = static_cast<R*>(B.mk);
+        double fbx, fby;
+        if (scheme == SCH_DF) {
+            R rk = R(0), Ux = R(0), Uy = R(0);
+#pragma unroll
+            for (int r = 0; r < SS; ++r) {
+                const R* g = sG + sl[r] * 3;
+                rk += g[0] * D[r];
+                Ux += g[1] * D[r];
+                Uy += g[2] * D[r];
+            }
+            const R Fx = R(2) * rk * (R(udxk) - Ux), Fy = R(2) * rk * (R(udyk) - Uy);
+            sM[2 * k] = Fx;
+            sM[2 * k + 1] = Fy;
+            mk[k * 16 + 0] = Fx;
+            mk[k * 16 + 1] = Fy;
+            B.Fx[k] = (double)Fx;
+            B.Fy[k] = (double)Fy;
+            fbx = -(double)Fx * B.ds;
+            fby = -(double)Fy * B.ds;
+        } else {
+            R st[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st[i] = R(0);
+#pragma unroll
+            for (int r = 0; r < SS; ++r) {
+                const R* g = sG + sl[r] * 9;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) st[i] += g[i] * D[r];
+            }
+            const R lam = R(lamk);
+            const R udx = R(udxk), udy = R(udyk);
+            R fsx = R(0), fsy = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R d = lam * (st[opp(i)] - st[i] + R(6) * wgt<R>(i) * (R(ex(i)) * udx + R(ey(i)) * udy));
+                sM[k * 9 + i] = d;
+                mk[k * 16 + 2 + i] = d;
+                fsx += R(ex(i)) * d;
+                fsy += R(ey(i)) * d;
+            }
+            mk[k * 16 + 0] = -ds * fsx;
+            mk[k * 16 + 1] = -ds * fsy;
+            B.Fx[k] = (double)(-ds * fsx);
+            B.Fy[k] = (double)(-ds * fsy);
+            fbx = (double)(-ds * fsx);
+            fby = (double)(-ds * fsy);
+        }
+        gxs += fbx;
+        gys += fby;
+        ts += rx * fby - ry * fbx;
+    }
+    // ---- body force and torque (the fixed-order reduction of block_sum3, by warp 0) beside
+    // the spread (Eq. 8 / Eq. 19; each slot's list in ascending marker order, warps 1-15)
+    shd[tid] = gxs;
+    shd[kIbThreads + tid] = gys;
+    shd[2 * kIbThreads + tid] = ts;
+    __syncthreads();   // (also publishes the marker forces)
+    if (tid < 32) {
+        double x, y, z;
+        warp_sum3(shd, tid, x, y, z);
+        if (tid == 0) {
+            B.st.Fhx = x;
+            B.st.Fhy = y;
+            B.st.Th = z;
+            const long long h = B.st.hist_n % B.hist_cap;
+            B.hist[3 * h + 0] = x;
+            B.hist[3 * h + 1] = y;
+            B.hist[3 * h + 2] = z;
+            B.st.hist_n = B.st.hist_n + 1;
+        }
+        return;
+    }
+    R* patch = static_cast<R*>(B.patch);
+    for (int q = tid - 32; q < nfp; q += kIbThreads - 32) {
+        R p[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p[i] = R(0);
+        const int o1 = sO[q + 1];
+        for (int o = sO[q]; o < o1; ++o) {
+            const int k = sK[o];
+            const R dd = sW[o];
+            if (scheme == SCH_DFC) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) p[i] += sM[k * 9 + i] * dd * ds;
+            } else {
+                p[0] += sM[2 * k] * dd * ds;
+                p[1] += sM[2 * k + 1] * dd * ds;
+            }
+        }
+        R* o = patch + (size_t)q * 9;
+        if (scheme == SCH_DFC) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[i] = p[i];
+        } else {
+            o[0] = p[0];
+            o[1] = p[1];
+        }
+    }
+}
+
 template <class S>
 __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
     if (L.pdl & PDL_TRIGGER) pdl_trigger();
@@ -2052,6 +2414,15 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
         if (rank != 0) return;
         if (SX == 2) ib_run<S, 2>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
         else ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo);
+        return;
+    }
+    if (ib_fast_ok<S>(C, *ref.b)) {   // (the same decision on every rank: static fields)
+        if (SX == 2) ib_fast<S, 2>(L, ref, rank, G, shd, dsm);
+        else ib_fast<S, 4>(L, ref, rank, G, shd, dsm);
+        if (rank == 0) {
+            __syncthreads();
+            if (threadIdx.x == 0) body_finish(*ref.b);
+        }
         return;
     }
     // body motion and set-up (rank 0), gather (every rank), forces, spread, sums and the
@@ -2446,12 +2817,19 @@ static cudaError_t sc_launch_k(int variant, const ScLaunch& L, long long jobs, i
         return cudaGetLastError();
     }
     if (L.phase == SC_SKIP_IB) {
-        if (variant == SC_SCALAR) IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1, true>), grid, block, st, dep, L, jobs);
-        else IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2, true>), grid, block, st, dep, L, jobs);
+        if (variant == SC_SCALAR)
+            IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 1, SC_MODE_SKIP>), grid, block, st, dep, L, jobs);
+        else IBLBM_LAUNCH_PDL((sc_kernel_scalar<S, KIND, 2, SC_MODE_SKIP>), grid, block, st, dep, L, jobs);
         return cudaGetLastError();
     }
-    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1, false>), grid, block, st, L, jobs);
-    else if (variant == SC_SCALAR2) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2, false>), grid, block, st, L, jobs);
+    if (L.phase == SC_ALL_TAIL) {
+        if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1, SC_MODE_TAIL>), grid, block, st, L, jobs);
+        else IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2, SC_MODE_TAIL>), grid, block, st, L, jobs);
+        return cudaGetLastError();
+    }
+    if (variant == SC_SCALAR) IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 1, SC_MODE_PLAIN>), grid, block, st, L, jobs);
+    else if (variant == SC_SCALAR2)
+        IBLBM_LAUNCH((sc_kernel_scalar<S, KIND, 2, SC_MODE_PLAIN>), grid, block, st, L, jobs);
     else if (variant == SC_BULK) {
         static const cudaError_t attr =
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>),
@@ -2488,9 +2866,9 @@ template <class S, int KIND>
 static int sc_occ_k(int variant) {
     int nb = 1;
     if (variant == SC_SCALAR)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 1, SC_MODE_PLAIN>, kThreads, 0);
     else if (variant == SC_SCALAR2)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sc_kernel_scalar<S, KIND, 2, SC_MODE_PLAIN>, kThreads, 0);
     else if (variant == SC_BULK) {
         const void* fn = reinterpret_cast<const void*>(&sc_kernel_bulk<S, KIND>);
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, BulkGeom<S>::SMEM);
@@ -2588,7 +2966,11 @@ static int ib_cluster_size_s(int nrefs, int sm_budget) {
         cudaGetLastError();
         return 1;
     }
-    for (int g = 8; g >= 2; g /= 2) {
+    // clusters of 16 CTAs are a non-portable size: allowed explicitly, used when they fit
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&ib_kernel<S>),
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int g = 16; g >= 2; g /= 2) {
         if ((long long)nrefs * g > sm_budget) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nrefs * g);
@@ -2681,6 +3063,14 @@ cudaError_t launch_macro(const CaseDev* hc, CaseDev* dc, double* rho, double* ux
     default: IBLBM_LAUNCH(macro_kernel<__half>, g, 256, st, dc, rho, ux, uy); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t set_ib_fast(int enable) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, (const void*)&g_ib_fast_enabled);
+    if (e != cudaSuccess) return e;
+    const int v = enable ? 1 : 0;
+    return cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice);
 }
 
 cudaError_t set_consumer_poll_limit(long polls) {

@@ -21,7 +21,11 @@ struct BodyRef {
 // regions as an explicit segment list (SC_LIST).  The IB region of a body is its
 // footprint box's rows, widened in x to multiples of kIbAlign nodes, so that every
 // segment of a scalar variant (32, 64 or 128 nodes) lies wholly inside or outside it.
-enum { SC_ALL = 0, SC_SKIP_IB = 1, SC_LIST = 2 };
+enum { SC_ALL = 0, SC_SKIP_IB = 1, SC_LIST = 2, SC_ALL_TAIL = 3 };
+// Compiled forms of the scalar sweep: every node of the first phase; the overlap order's
+// SC_SKIP_IB (IB regions left to the tail CTAs); SC_ALL_TAIL, every node plus tail CTAs
+// that take the lattice edges and the step end (the last launch of a launch-by-launch step).
+enum { SC_MODE_PLAIN = 0, SC_MODE_SKIP = 1, SC_MODE_TAIL = 2 };
 constexpr int kIbAlign = 128;
 // Programmatic dependent launch: PDL_TRIGGER, the kernel lets the next launch of its
 // stream begin as soon as all its CTAs run; PDL_DEPENDENT, the launch may begin before
@@ -67,7 +71,7 @@ struct IbLaunch {
     int pdl;        // PDL_* flags (PDL_TRIGGER only)
     int prepared;   // 1: body motion of the step already done by launch_prepare (another
                     // body's IB CTA reads these markers: DFC W_total over several bodies)
-    int cluster;    // CTAs per body (a thread-block cluster, 1-8; 0 or 1: one CTA); the
+    int cluster;    // CTAs per body (a thread-block cluster, 1-16; 0 or 1: one CTA); the
                     // others share the body's footprint gather with the first
 };
 
@@ -107,7 +111,7 @@ cudaError_t launch_edges(int storage, const EdgeLaunch& L, cudaStream_t st);
 long long lattice_edge_nodes(int nx, int ny);
 cudaError_t launch_ib(int storage, const IbLaunch& L, cudaStream_t st);
 // CTAs per body for an IB launch over nrefs bodies of this storage type: the largest of
-// 8, 4, 2 whose clusters all fit on the GPU at once within sm_budget SMs, else 1
+// 16, 8, 4, 2 whose clusters all fit on the GPU at once within sm_budget SMs, else 1
 int ib_cluster_size(int storage, int nrefs, int sm_budget);
 // body motion of the step (first half of Eq. 23, markers, U_d) for every body, one CTA
 // each, before an IB launch with IbLaunch.prepared = 1
@@ -125,5 +129,7 @@ int sc_blocks_per_sm(int storage, int collision, int variant);
 // Polls after which the bulk sweep's consumer warps give up waiting for a staged tile
 // (negative: the default bound).  Process-wide; for tests of the give-up path.
 cudaError_t set_consumer_poll_limit(long polls);
+// 0: every IB stage takes the general path (tests compare it with the fixed-body fast path)
+cudaError_t set_ib_fast(int enable);
 
 }  // namespace iblbm

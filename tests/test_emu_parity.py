@@ -179,6 +179,12 @@ def test_graph_replay_equals_timed_launches(L):
     P.check_graph_equals_direct(nx=40, ny=24, steps=3)
 
 
+@pytest.mark.parametrize("storage", [W.F64, W.F32])
+def test_ib_fast_path_equals_general_path(L, storage):
+    full_only(L)
+    P.check_ib_fast_equals_general(L, storage, nx=120, ny=60, steps=3)
+
+
 def test_marker_out_of_domain_is_reported(L):
     full_only(L)
     P.check_marker_out_of_domain(L, steps=60)

@@ -163,6 +163,11 @@ def test_overlap_order_equals_serial_order():
     P.check_overlap_equals_serial()
 
 
+@pytest.mark.parametrize("storage", [W.F64, W.F32, W.F16S])
+def test_ib_fast_path_equals_general_path(storage):
+    P.check_ib_fast_equals_general(L, storage)
+
+
 def test_marker_out_of_domain_is_reported():
     P.check_marker_out_of_domain(L)
 
