@@ -70,15 +70,6 @@ __device__ __forceinline__ void pdl_wait() {
 #endif
 }
 
-// L1 prefetch hint of the line holding a (a hint: it brings data early, changes nothing).
-__device__ __forceinline__ void prefetch_l1(const void* a) {
-#ifndef IBLBM_EMULATE
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-#else
-    (void)a;
-#endif
-}
-
 // Thread-block clusters (sm_90 and later): rank of this CTA in its cluster, and a barrier
 // of every thread of the cluster with release / acquire semantics at cluster scope (writes
 // before it, global memory included, are visible to the cluster's threads after it).  The
@@ -521,15 +512,17 @@ __device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, 
 // (every read of the counters in the step is done by then); done[0] counts finished CTAs
 // and is reset for the next step.
 __device__ __forceinline__ void end_step_if_last(unsigned* done, CaseDev** cases, int ncases) {
+    __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned prev = atomicAdd(done, 1u);
-        if (prev == gridDim.x - 1u) {
-            __threadfence();
-            for (int c = 0; c < ncases; ++c) cases[c]->step += 1ull;
-            done[0] = 0u;
-        }
+        last = atomicAdd(done, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (last) {   // (the whole CTA: one counter per thread)
+        __threadfence();
+        for (int c = threadIdx.x; c < ncases; c += blockDim.x) cases[c]->step += 1ull;
+        if (threadIdx.x == 0) done[0] = 0u;
     }
 }
 
@@ -541,47 +534,9 @@ __device__ __forceinline__ void sc_tail(const ScLaunch& L, int w, int nw, int la
     ScCase<S> K;
     const CaseDev* cur = nullptr;
     const long long njobs = L.nlist + L.nechunks;
-    // Before the wait, what the first job reads that the IB stage does not write: its case
-    // record and, into L1, the lines its pulls and (IB-region segments) its footprint-map
-    // lookups will touch, so that after the wait only the patches are fetched from L2.
-    if (w < njobs) {
-        int y, x0, x1;
-        if (w < L.nlist) {
-            const int4 e = L.list[w];
-            cur = L.cases[e.x];
-            K.load(cur);
-            y = e.y;
-            x0 = e.z;
-            x1 = e.z + ScSeg<S, NPT>::value;
-        } else {
-            const EdgeChunk ch = L.echunks[w - L.nlist];
-            cur = L.ecases[ch.c];
-            K.load(cur);
-            // rows 0 and ny-1 are contiguous runs; the columns take one node per lane
-            const int e = min(ch.first + lane, ch.end - 1);
-            if (e < K.nx) { y = 0; x0 = ch.first; x1 = min(ch.end, K.nx); }
-            else if (K.ny > 1 && e < 2 * K.nx) { y = K.ny - 1; x0 = ch.first - K.nx; x1 = min(ch.end, 2 * K.nx) - K.nx; }
-            else { const int r = e - 2 * K.nx; y = 1 + (r >> 1); x0 = (r & 1) ? K.nx - 1 : 0; x1 = x0 + 1; }
-        }
-        const char* base = reinterpret_cast<const char*>(K.src);
-        const int nb = (int)sizeof(S);
-        const int xa = max(0, x0 - 1), xb = min(K.nx - 1, x1);   // pulled columns (clamped)
-        const int lines = ((xb - xa + 1) * nb + 127) / 128 + 1;
-        // a run of a row: the lanes share its lines; a column node: each lane its own
-        const bool run = x1 - x0 > 1;
-        for (int t = run ? lane : 0; t < 9 * 3 * lines; t += run ? 32 : 1) {
-            const int i = t / (3 * lines), r = (t / lines) % 3, l = t % lines;
-            const int yy = min(max(y - 1 + r, 0), K.ny - 1);
-            const int xx = min(xa + l * (128 / nb), xb);
-            prefetch_l1(base + ((long long)i * K.plane + (long long)yy * K.pitch + xx) * nb);
-        }
-        if (w < L.nlist)
-            for (int b = 0; b < K.nbodies; ++b) {
-                const BodyDev& B = K.C->bodies[b];
-                const int ly = y - B.by0, la = max(x0 - B.bx0, 0), lb = min(x1 - B.bx0, B.bw);
-                if (B.nfp <= 0 || ly < 0 || ly >= B.bh || la >= lb) continue;
-                for (int l = la + lane * 32; l < lb; l += 32 * 32) prefetch_l1(B.node_map + ly * B.bw + l);
-            }
+    if (w < njobs) {   // the first job's case record before the wait (the IB stage leaves it)
+        cur = w < L.nlist ? L.cases[L.list[w].x] : L.ecases[L.echunks[w - L.nlist].c];
+        K.load(cur);
     }
     if (L.pdl & PDL_DEPENDENT) pdl_wait();   // the IB stage has ended, its patches are visible
     for (long long j = w; j < njobs; j += nw) {
