@@ -837,6 +837,7 @@ struct BatchGroup {
     bool ok[SC_VARIANTS] = {};                 // variant usable for every lattice of the group
     int size_class = 0;                        // 1: the group sweeps >= kLargeGroupNodes nodes
     int grid_overlap[SC_VARIANTS] = {};        // grid while the IB stage holds some SMs
+    int per_sm[SC_VARIANTS] = {};              // resident CTAs per SM at the group's block size
 };
 
 // Stream-collide variant per (storage, collision, size class), process-wide so
@@ -912,6 +913,7 @@ struct BatchPlan {
     // sweep also takes its IB-region segments after the IB stage.  A step is then the IB
     // launch and one launch per group.
     bool fused_tail = false;
+    int sms = 148;
     EdgeChunk* dechunks32 = nullptr;
     int nechunks32 = 0;
     cudaStream_t side = nullptr;
@@ -1039,7 +1041,10 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
             sl.done = P->ddone;
             const int wpc = (g.block[v] > 0 ? g.block[v] : kThreads) / 32;
             sl.tail_ctas = sl.nechunks > 0 ? (int)std::max<long long>(1, (sl.nechunks + wpc - 1) / wpc) : 0;
-            grid += sl.tail_ctas;
+            // the first phase leaves the tail CTAs' SMs free, so the edges run beside it
+            const int per_sm = std::max(1, g.per_sm[v]);
+            const int tail_sms = (sl.tail_ctas + per_sm - 1) / per_sm;
+            grid = std::min<long long>(grid, (long long)std::max(1, P->sms - tail_sms) * per_sm) + sl.tail_ctas;
         }
         if ((e = timed_launch(timer, STAGE_SWEEP, st, [&] {
                  return launch_stream_collide(g.storage, g.collision, v, sl, g.jobs[v], grid, st);
@@ -1167,6 +1172,7 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
     std::vector<CaseDev*> all_cases;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
+    P->sms = sms;
     for (int st = 0; st < 3; ++st) {
         std::vector<BodyRef> refs;
         for (int i = 0; i < n; ++i) {
@@ -1252,10 +1258,12 @@ BatchPlan* get_plan(iblbm_ctx** ctxs, int n, int* rc) {
                 if (!g.djob[v]) { *rc = IBLBM_ERR_OOM; delete P; return nullptr; }
                 cudaMemcpyAsync(g.djob[v], off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, P->st);
                 const long long cap = (long long)sms * sc_blocks_per_sm(st, col, v);
+                g.per_sm[v] = (int)(cap / sms);
                 g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 7) / 8, cap));
                 if ((v == SC_SCALAR || v == SC_SCALAR2) && (g.jobs[v] + 7) / 8 < sms) {
                     // too few jobs to give every SM a 256-thread CTA: spread 64-thread CTAs
                     g.block[v] = 64;
+                    g.per_sm[v] = (int)(4 * cap / sms);
                     g.grid[v] = (int)std::max<long long>(1, std::min<long long>((g.jobs[v] + 1) / 2, 4 * cap));
                 }
             }

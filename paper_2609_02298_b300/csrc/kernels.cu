@@ -384,6 +384,67 @@ __device__ __forceinline__ void sc_row_scalar(const ScCase<S>& K, int y, int xse
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
 }
 
+// The tail CTAs' form of sc_row_scalar (KEEP stores) in two parts: row_pre takes the pulls
+// and the segment's IB decision before the wait for the IB stage (they read nothing that
+// stage writes), row_post the patch, collision and stores after it.  The expressions are
+// those of sc_row_scalar, so the results are too.
+template <class S, int NPT> struct RowPre {
+    typename Traits<S>::R s[NPT][9];
+    bool ib;
+};
+template <class S, int NPT>
+__device__ __forceinline__ void row_pre(const ScCase<S>& K, int y, int xseg, int lane, RowPre<S, NPT>& P) {
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
+    P.ib = false;
+    if (y == 0 || y == ny - 1) return;
+    P.ib = K.nbodies > 0 && row_has_ib(*K.C, y, xseg, xseg + 32 * NPT);
+    int koff[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) koff[i] = i * plane - ey(i) * pitch - ex(i);
+    const int row = y * pitch;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int x = xseg + 32 * j + lane;
+        if (x >= 1 && x < nx - 1) {
+            const int a = row + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) P.s[j][i] = ld1_sweep(K.src + (a + koff[i]));
+        }
+    }
+}
+template <class S, int KIND, int NPT>
+__device__ __forceinline__ void row_post(const ScCase<S>& K, int y, int xseg, int lane, RowPre<S, NPT>& P) {
+    using R = typename Traits<S>::R;
+    const CaseDev& C = *K.C;
+    S* __restrict__ dst = K.dst;
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch, plane = (int)K.plane;
+    if (y == 0 || y == ny - 1) return;
+    const bool ib = P.ib;
+    const bool forced = ib || K.has_force;
+    const int row = y * pitch;
+    bool unstable = false;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int x = xseg + 32 * j + lane;
+        if (x >= 1 && x < nx - 1) {
+            R* s = P.s[j];
+            const int a = row + x;
+            R rho;
+            if (forced) {
+                R Fx = K.gfx, Fy = K.gfy;
+                if (ib) add_ib<R>(C, x, y, P.s[j], Fx, Fy);
+                rho = collide<R, KIND>(K.P, P.s[j], Fx, Fy);
+            } else {
+                rho = collide<R, KIND, false>(K.P, P.s[j], R(0), R(0));
+            }
+            unstable |= bad_density(rho);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st1_keep(dst + (a + i * plane), s[i]);
+        }
+    }
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(const_cast<unsigned*>(&C.status), STAT_UNSTABLE);
+}
+
 // FP16 storage, NP pairs of adjacent nodes per lane: a warp handles NP chunks of 64
 // nodes of a row, lane l the pair (x0, x0 + 1), x0 = xseg + 64 j + 2 l.  Each
 // population is one aligned 32-bit load of the source row's pair at x0 (two nodes, half
@@ -483,11 +544,12 @@ __device__ __forceinline__ void sc_row_nodes(const ScCase<S>& K, int y, int xseg
 // store.  C is the case record (possibly a shared-memory copy), gc the case in global
 // memory (status flags).  Edge node e: e < nx -> (e, 0); e < 2nx -> (e - nx, ny - 1) when
 // ny > 1; then columns 0 and nx-1 of rows 1..ny-2, alternating.
+// In two parts, so that the tail CTAs can pull before they wait for the IB stage.
 template <class S>
-__device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, int e, bool noib, const CaseDev* gc) {
+__device__ __forceinline__ void edge_pre(const CaseDev& C, const ScCase<S>& K, int e, int& x, int& y,
+                                         typename Traits<S>::R (&s)[9]) {
     using R = typename Traits<S>::R;
     const int nx = K.nx, ny = K.ny;
-    int x, y;
     if (e < nx) {
         x = e; y = 0;
     } else if (ny > 1 && e < 2 * nx) {
@@ -497,8 +559,12 @@ __device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, 
         if (nx > 1) { y = 1 + (r >> 1); x = (r & 1) ? nx - 1 : 0; }
         else { y = 1 + r; x = 0; }
     }
-    R s[9];
     post_stream_node<S, R>(C, K.src, x, y, s);
+}
+template <class S>
+__device__ __forceinline__ void edge_post(const CaseDev& C, const ScCase<S>& K, int x, int y, bool noib,
+                                          const CaseDev* gc, typename Traits<S>::R (&s)[9]) {
+    using R = typename Traits<S>::R;
     R Fx = K.gfx, Fy = K.gfy;
     if (K.nbodies > 0 && !noib) add_ib<R>(C, x, y, s, Fx, Fy);
     const R rho = collide<R, -1>(K.P, s, Fx, Fy);
@@ -506,6 +572,13 @@ __device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, 
     S* d = K.dst + ((long long)y * K.pitch + x);
 #pragma unroll
     for (int i = 0; i < 9; ++i) st1(d + i * K.plane, s[i]);
+}
+template <class S>
+__device__ __forceinline__ void edge_node(const CaseDev& C, const ScCase<S>& K, int e, bool noib, const CaseDev* gc) {
+    typename Traits<S>::R s[9];
+    int x, y;
+    edge_pre<S>(C, K, e, x, y, s);
+    edge_post<S>(C, K, x, y, noib, gc, s);
 }
 
 // Last CTA of a launch to finish ends the step: advances the step counter of every case
@@ -531,15 +604,42 @@ __device__ __forceinline__ void end_step_if_last(unsigned* done, CaseDev** cases
 // turn.
 template <class S, int KIND, int NPT>
 __device__ __forceinline__ void sc_tail(const ScLaunch& L, int w, int nw, int lane) {
+    using R = typename Traits<S>::R;
+    constexpr bool SPLIT = !std::is_same<S, __half>::value;   // (FP16 pairs: sc_row_pair)
     ScCase<S> K;
     const CaseDev* cur = nullptr;
     const long long njobs = L.nlist + L.nechunks;
-    if (w < njobs) {   // the first job's case record before the wait (the IB stage leaves it)
-        cur = w < L.nlist ? L.cases[L.list[w].x] : L.ecases[L.echunks[w - L.nlist].c];
-        K.load(cur);
+    // the first job's reads that the IB stage leaves alone (case record, pulls, the segment's
+    // IB decision) go out before the wait
+    RowPre<S, NPT> P;
+    R es[9];
+    int4 e0 = make_int4(0, 0, 0, 0);
+    int ex0 = 0, ey0 = 0;
+    bool live0 = false;
+    if (w < njobs) {
+        if (w < L.nlist) {
+            e0 = L.list[w];
+            cur = L.cases[e0.x];
+            K.load(cur);
+            if constexpr (SPLIT) row_pre<S, NPT>(K, e0.y, e0.z, lane, P);
+        } else {
+            const EdgeChunk ch = L.echunks[w - L.nlist];
+            cur = L.ecases[ch.c];
+            K.load(cur);
+            live0 = ch.first + lane < ch.end;
+            if (live0) edge_pre<S>(*cur, K, ch.first + lane, ex0, ey0, es);
+        }
     }
     if (L.pdl & PDL_DEPENDENT) pdl_wait();   // the IB stage has ended, its patches are visible
-    for (long long j = w; j < njobs; j += nw) {
+    if (w < njobs) {
+        if (w < L.nlist) {
+            if constexpr (SPLIT) row_post<S, KIND, NPT>(K, e0.y, e0.z, lane, P);
+            else sc_row_nodes<S, KIND, NPT, true>(K, e0.y, e0.z, lane);
+        } else if (live0) {
+            edge_post<S>(*cur, K, ex0, ey0, false, cur, es);
+        }
+    }
+    for (long long j = w + nw; j < njobs; j += nw) {
         if (j < L.nlist) {
             const int4 e = L.list[j];
             const CaseDev* c = L.cases[e.x];
