@@ -93,7 +93,8 @@ def launches_per_step(specs, L=None) -> int:
     per (storage, collision) group.  With one storage type the last stream-collide launch
     also takes the lattice edges and the step end in its tail CTAs (its variant has them:
     the one- or two-node-per-lane kernels) -- unless no body can reach a lattice edge, when
-    the edges run beside the IB stage in a launch of their own.  When at most eight bodies,
+    the edges run beside the IB stage in a launch of their own and a counter launch ends
+    the step.  When at most eight bodies,
     all fixed, of one storage type sit on at least 2^20 nodes, the IB stage runs beside the
     sweep and each group's sweep also takes its IB-region segments.  Otherwise add a
     lattice-edge launch per storage type and the step-counter launch (and, in the overlap
@@ -121,8 +122,8 @@ def launches_per_step(specs, L=None) -> int:
                 and b.yc + m < s.ny - 2.0)
 
     early = all(clear(s, b) for s, b in bodies) and all(v != 0 for v in variant.values())
-    if len(storages) == 1 and variant[groups[-1]] in (1, 2):
-        return n + (1 if early else 0)
+    if len(storages) == 1 and variant[groups[-1]] in (1, 2) and not early:
+        return n
     return n + len(storages) + 1
 
 

@@ -998,9 +998,10 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
     }
     const bool dependent = overlap && !P->ib_groups.empty();
     const bool fused = dependent && P->fused_tail;
-    // launch-by-launch order: the last sweep launch ends the step (edges unless they ran
-    // beside the IB stage, step counters) when its variant has the tail form
-    const bool serial_tail = !overlap && !timer && P->fused_tail && !P->groups.empty() &&
+    // launch-by-launch order: the last sweep launch takes the lattice edges and ends the step
+    // when its variant has the tail form and the edges did not run beside the IB stage (with
+    // nothing else for its tail, the plain form and the counter launch measured faster)
+    const bool serial_tail = !overlap && !early && !timer && P->fused_tail && !P->groups.empty() &&
                              sc_variant_phased(chosen_variant(P->groups.back()));
     for (size_t gi = 0; gi < P->groups.size(); ++gi) {
         const auto& g = P->groups[gi];
@@ -1029,13 +1030,10 @@ cudaError_t launch_batch_step(BatchPlan* P, cudaStream_t st, iblbm_ctx* timer) {
             grid += sl.tail_ctas;
         }
         if (serial_tail && gi + 1 == P->groups.size()) {
-            if (early) cudaStreamWaitEvent(st, P->ev_edges, 0);   // the edges precede the step end
             sl.phase = SC_ALL_TAIL;
-            if (!early) {
-                sl.echunks = P->dechunks32;
-                sl.ecases = P->edge_groups[0].dcases;
-                sl.nechunks = P->nechunks32;
-            }
+            sl.echunks = P->dechunks32;
+            sl.ecases = P->edge_groups[0].dcases;
+            sl.nechunks = P->nechunks32;
             sl.count_cases = P->dcases_all;
             sl.ncount = (int)P->ctxs.size();
             sl.done = P->ddone;
