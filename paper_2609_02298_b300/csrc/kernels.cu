@@ -2110,17 +2110,24 @@ template <class R> struct FastLayout {
     }
 };
 
+// A DF or DFC body whose footprint, stencils and lambda_k are current fits the fast path
+// (its shared-memory layout within kFastSmem, at most one marker per thread).
 template <class S>
-__device__ __forceinline__ bool ib_fast_ok(const CaseDev& C, const BodyDev& B) {
+__device__ __forceinline__ bool ib_fast_fits(const BodyDev& B) {
     using R = typename Traits<S>::R;
-    if (!g_ib_fast_enabled || B.motion != MOT_FIXED || !B.cache_valid || B.nfp <= 0 || B.n > kIbThreads) return false;
+    if (!g_ib_fast_enabled || B.nfp <= 0 || B.n > kIbThreads) return false;
     if (B.scheme == SCH_DFC) {
-        if (!(B.lam_valid && C.dfc_all_fixed)) return false;
+        if (!B.lam_valid) return false;
     } else if (B.scheme != SCH_DF) {
         return false;
     }
     const FastLayout<R> F(B.scheme, B.nfp, B.n, B.n * B.S * B.S);
     return F.bytes <= kFastSmem;
+}
+// ... and a fixed one with its footprint (and lambda_k) cached takes it without a set-up
+template <class S>
+__device__ __forceinline__ bool ib_fast_ok(const CaseDev& C, const BodyDev& B) {
+    return B.motion == MOT_FIXED && B.cache_valid && (B.scheme != SCH_DFC || C.dfc_all_fixed) && ib_fast_fits<S>(B);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -2162,7 +2169,8 @@ __device__ __forceinline__ void cluster_wait() {
 }
 
 template <class S, int SX>
-__device__ void ib_fast(const IbLaunch& L, const BodyRef& ref, int rank, int G, double* shd, unsigned char* dsm) {
+__device__ void ib_fast(const IbLaunch& L, const BodyRef& ref, int rank, int G, double* shd, unsigned char* dsm,
+                        bool prepare) {
     using R = typename Traits<S>::R;
     constexpr int SS = SX * SX;
     constexpr int GB = sizeof(R) == 8 ? 2 : 4;   // slots per thread whose pulls go out together
@@ -2237,7 +2245,7 @@ __device__ void ib_fast(const IbLaunch& L, const BodyRef& ref, int rank, int G, 
                 }
             }
         }
-        if (!L.prepared) body_prepare(B, shd);   // a fixed body: U_d already current, or set now
+        if (prepare && !L.prepared) body_prepare(B, shd);   // a fixed body: U_d current, or set now
     }
     // ---- gather (every rank): pulls of this thread's slots, rho and u (DF) or the nine
     // shifted populations (DFC) into rank 0's shared memory
@@ -2472,8 +2480,8 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
         return;
     }
     if (ib_fast_ok<S>(C, *ref.b)) {   // (the same decision on every rank: static fields)
-        if (SX == 2) ib_fast<S, 2>(L, ref, rank, G, shd, dsm);
-        else ib_fast<S, 4>(L, ref, rank, G, shd, dsm);
+        if (SX == 2) ib_fast<S, 2>(L, ref, rank, G, shd, dsm, true);
+        else ib_fast<S, 4>(L, ref, rank, G, shd, dsm, true);
         if (rank == 0) {
             __syncthreads();
             if (threadIdx.x == 0) body_finish(*ref.b);
@@ -2490,6 +2498,19 @@ __global__ void __launch_bounds__(kIbThreads, 1) ib_kernel(IbLaunch L) {
                      : ib_run<S, 4>(L, ref, shi, shd, sU, sF, sEw, sEk, sQc, sQo, IB_SETUP);
     }
     if (G > 1) cluster_sync_all();
+    else __syncthreads();
+    // a moving DF or DFC body with its footprint and lambda_k just rebuilt: the rest of the
+    // stage on the fast path (the same decision on every rank, from the fields set above;
+    // a footprint that could not be built has nfp = 0 and does not fit)
+    if (ib_fast_fits<S>(*ref.b)) {
+        if (SX == 2) ib_fast<S, 2>(L, ref, rank, G, shd, dsm, false);
+        else ib_fast<S, 4>(L, ref, rank, G, shd, dsm, false);
+        if (rank == 0) {
+            __syncthreads();
+            if (threadIdx.x == 0) body_finish(*ref.b);
+        }
+        return;
+    }
     // (a body whose footprint could not be built has nfp = 0: nothing to gather)
     if (ok) ib_gather<S>(C, *ref.b, rank * kIbThreads + (int)threadIdx.x, G * kIbThreads);
     if (G > 1) cluster_sync_all();

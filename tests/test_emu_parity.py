@@ -185,6 +185,11 @@ def test_ib_fast_path_equals_general_path(L, storage):
     P.check_ib_fast_equals_general(L, storage, nx=120, ny=60, steps=3)
 
 
+def test_ib_fast_path_equals_general_path_moving(L):
+    full_only(L)
+    P.check_ib_fast_equals_general_moving(L, W.F64, steps=2)
+
+
 def test_marker_out_of_domain_is_reported(L):
     full_only(L)
     P.check_marker_out_of_domain(L, steps=60)

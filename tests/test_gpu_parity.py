@@ -168,6 +168,11 @@ def test_ib_fast_path_equals_general_path(storage):
     P.check_ib_fast_equals_general(L, storage)
 
 
+@pytest.mark.parametrize("storage", [W.F64, W.F32])
+def test_ib_fast_path_equals_general_path_moving(storage):
+    P.check_ib_fast_equals_general_moving(L, storage)
+
+
 def test_marker_out_of_domain_is_reported():
     P.check_marker_out_of_domain(L)
 
