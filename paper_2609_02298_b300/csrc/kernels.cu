@@ -1204,8 +1204,104 @@ __device__ __forceinline__ void block_exscan2(int& a, int& b, int& tot_a, int& t
 // Footprint of a body: stencil origins and weights, bounding box, box-local
 // node -> slot map and a node -> marker CSR whose lists are sorted by marker
 // index (so every spread sums in ascending marker order, like Eq. 8 written out).
+// The node map, list fill counters, lists and stencil weights of a footprint rebuild in
+// shared memory (a moving body rebuilds it every step): the same slots, list order and
+// weights as the global-memory build below, written out once at the end.
+constexpr int kFastSmem = 160 * 1024;   // bytes of the IB CTA's dynamic shared memory the fast path may use
+constexpr int kFootSmemArea = 6144;   // box nodes
+constexpr int kFootSmemEnt = 8192;    // node->marker entries (markers x stencil nodes)
+// scratch layout (ints): map, fill, offsets (area + 1, padded to area + 4), entries, origins
+// (2 per marker), then 8 weights per marker; kIbThreads markers at most
+constexpr int kFootSmemInts = 3 * kFootSmemArea + 4 + kFootSmemEnt + 2 * kIbThreads;
+static_assert(kFootSmemInts % 2 == 0, "the weights start 8-byte aligned");
+static_assert(kFootSmemInts * 4 + 8 * kIbThreads * 8 <= kFastSmem, "footprint scratch fits the IB CTA's region");
 template <class R>
-__device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
+__device__ bool footprint_in_smem(BodyDev& B, int* shi, int* scratch, int bx0, int by0, int bw, int bh) {
+    const int tid = threadIdx.x, n = B.n, Sx = B.S, SS = Sx * Sx, ne = n * SS, area = bw * bh;
+    int* sMap = scratch;                           // [area] counts, then slot or -1
+    int* sFill = sMap + kFootSmemArea;             // [area] fill counters per slot
+    int* sOff = sFill + kFootSmemArea;             // [area + 1] list offsets per slot
+    int* sEnt = sOff + kFootSmemArea + 4;          // [ne] list entries
+    int* sIJ = sEnt + kFootSmemEnt;                // [2n] stencil origins
+    R* sW = reinterpret_cast<R*>(scratch + kFootSmemInts);   // [8n] weights
+    const R* wts = static_cast<const R*>(B.wts);
+    for (int q = tid; q < area; q += kIbThreads) sMap[q] = 0;
+    for (int k = tid; k < n; k += kIbThreads) {    // (this thread wrote them: no barrier needed)
+        sIJ[2 * k] = B.ij[2 * k];
+        sIJ[2 * k + 1] = B.ij[2 * k + 1];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) sW[k * 8 + a] = wts[k * 8 + a];
+    }
+    __syncthreads();
+    for (int en = tid; en < ne; en += kIbThreads) {
+        const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
+        atomicAdd(&sMap[(sIJ[2 * k + 1] + b - by0) * bw + (sIJ[2 * k] + a - bx0)], 1);
+    }
+    __syncthreads();
+    // chunked exclusive scans: slot index and list offset (as in the global build)
+    const int chunk = (area + kIbThreads - 1) / kIbThreads;
+    const int beg = min(area, tid * chunk), end = min(area, beg + chunk);
+    int nz = 0, cnt = 0;
+    for (int q = beg; q < end; ++q) {
+        const int c = sMap[q];
+        nz += c > 0;
+        cnt += c;
+    }
+    int slot = nz, off = cnt, tot_nz = 0, tot_cnt = 0;
+    block_exscan2(slot, off, tot_nz, tot_cnt, shi);
+    for (int q = beg; q < end; ++q) {
+        const int c = sMap[q];
+        if (c > 0) {
+            B.fp_node[slot] = q;
+            sOff[slot] = off;
+            sFill[slot] = 0;
+            sMap[q] = slot;
+            ++slot;
+            off += c;
+        } else {
+            sMap[q] = -1;
+        }
+    }
+    const int nfp = tot_nz;
+    if (tid == 0) {
+        sOff[nfp] = tot_cnt;
+        B.bx0 = bx0; B.by0 = by0; B.bw = bw; B.bh = bh; B.nfp = nfp;
+    }
+    __syncthreads();
+    for (int en = tid; en < ne; en += kIbThreads) {
+        const int k = en / SS, r = en % SS, b = r / Sx, a = r % Sx;
+        const int sl = sMap[(sIJ[2 * k + 1] + b - by0) * bw + (sIJ[2 * k] + a - bx0)];
+        B.mslot[en] = sl;
+        sEnt[sOff[sl] + atomicAdd(&sFill[sl], 1)] = en;
+    }
+    __syncthreads();
+    R* cw = static_cast<R*>(B.csr_w);
+    for (int q = tid; q < nfp; q += kIbThreads) {   // insertion sort of each short list
+        const int o0 = sOff[q], o1 = sOff[q + 1];
+        for (int i = o0 + 1; i < o1; ++i) {
+            const int v = sEnt[i];
+            int j = i - 1;
+            while (j >= o0 && sEnt[j] > v) {
+                sEnt[j + 1] = sEnt[j];
+                --j;
+            }
+            sEnt[j + 1] = v;
+        }
+        B.csr_off[q] = o0;
+        for (int o = o0; o < o1; ++o) {             // D(x - X_k) of each entry, kept with it
+            const int en = sEnt[o], k = en / SS, r = en % SS;
+            B.csr_ent[o] = en;
+            cw[o] = sW[k * 8 + (r % Sx)] * sW[k * 8 + 4 + (r / Sx)];
+        }
+    }
+    if (tid == 0) B.csr_off[nfp] = tot_cnt;
+    for (int q = tid; q < area; q += kIbThreads) B.node_map[q] = sMap[q];
+    __syncthreads();
+    return true;
+}
+
+template <class R>
+__device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi, int* scratch = nullptr) {
     const int tid = threadIdx.x, n = B.n, Sx = B.S, SS = Sx * Sx, kern = B.kernel;
     R* wts = static_cast<R*>(B.wts);
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, err = 0;
@@ -1252,6 +1348,8 @@ __device__ bool build_footprint(const CaseDev& C, BodyDev& B, int* shi) {
         return false;
     }
     const int area = bw * bh;
+    if (scratch && area <= kFootSmemArea && n * SS <= kFootSmemEnt && n <= kIbThreads)
+        return footprint_in_smem<R>(B, shi, scratch, bx0, by0, bw, bh);
     for (int q = tid; q < area; q += kIbThreads) B.node_map[q] = 0;
     __syncthreads();
     for (int en = tid; en < n * SS; en += kIbThreads) {
@@ -1337,8 +1435,8 @@ constexpr int kMdfNodeCap = 2048; // footprint nodes whose MDF iterate fits in s
 constexpr int kMdfEntryCap = 4096; // node->marker entries staged in shared memory for MDF
 // Dynamic shared memory of ib_kernel: sU (2 per node), sF (2 per marker), sEw (per
 // entry), then sEk (per entry, int).
-// The fixed-body fast path (ib_fast) uses up to kFastSmem bytes of the same region.
-constexpr int kFastSmem = 160 * 1024;
+// The fixed-body fast path (ib_fast) and the shared-memory footprint build use up to
+// kFastSmem bytes of the same region (kFastSmem is defined with the footprint build).
 template <class R> struct IbSmem {
     static constexpr int mdf = (2 * kMdfNodeCap + 2 * 512 + kMdfEntryCap + kMdfNodeCap) * (int)sizeof(R) +
                                (kMdfEntryCap + kMdfNodeCap + 1) * 4;
@@ -1434,7 +1532,7 @@ __device__ __forceinline__ bool ib_run(const IbLaunch& L, const BodyRef& ref, in
     const int tid = threadIdx.x;
     const int n = B.n, scheme = B.scheme;
     if ((part & IBP_SETUP) && !B.cache_valid) {
-        if (!build_footprint<R>(C, B, shi)) return false;
+        if (!build_footprint<R>(C, B, shi, reinterpret_cast<int*>(sU))) return false;
         if (tid == 0) B.cache_valid = (B.motion == MOT_FIXED) ? 1 : 0;
     }
     __syncthreads();
