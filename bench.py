@@ -40,10 +40,10 @@ BYTES_PER_LU = {W.F64: 144, W.F32: 72, W.F16S: 36}
 # dram__bytes_write.sum of two steps of the 12-lattice case (4 lattices per stream-collide
 # launch, 12 per edge launch), averaged and divided by nodes or lattices.  A sweep whose
 # kernels have no entry here (or changed since) reports traffic null.
-SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): (560650752 + 558946560) / 2 / 8388608,
-                             (2, W.TRT): (559732992 + 560361728) / 2 / 8388608,
-                             (2, W.CMMRT): (560482048 + 559604736) / 2 / 8388608}
-EDGE_DRAM_BYTES_PER_LATTICE = (29597696 + 29859072) / 2 / 12
+SWEEP_DRAM_BYTES_PER_NODE = {(2, W.BGK): (560977408 + 558729216) / 2 / 8388608,
+                             (2, W.TRT): (559787776 + 560373760) / 2 / 8388608,
+                             (2, W.CMMRT): (560088320 + 560034816) / 2 / 8388608}
+EDGE_DRAM_BYTES_PER_LATTICE = (29608192 + 29780736) / 2 / 12
 DTYPE = {W.F64: "f64", W.F32: "f32", W.F16S: "f32 compute / f16 storage"}
 STORAGE_LABEL = {W.F64: "f64 shifted", W.F32: "f32 shifted", W.F16S: "f16 shifted"}
 
