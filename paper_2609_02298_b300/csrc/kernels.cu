@@ -776,7 +776,9 @@ __global__ void __launch_bounds__(kThreads) edge_kernel(EdgeLaunch L) {
 // path (global pulls with the domain conditions), as in the other variants.
 template <class S> struct BulkCfg;
 template <> struct BulkCfg<float> { static constexpr int NPT = 2, NST = 6, MINB = 2; };
-template <> struct BulkCfg<__half> { static constexpr int NPT = 2, NST = 8, MINB = 2; };
+// FP16: four shallow pipelines per SM (a CTA's 56 registers and 38 KB of stages) measured 5 %
+// faster than two deep ones (8 stages, 96 registers): the sweep is short of warps, not of stages
+template <> struct BulkCfg<__half> { static constexpr int NPT = 2, NST = 4, MINB = 4; };
 template <> struct BulkCfg<double> { static constexpr int NPT = 1, NST = 6, MINB = 2; };
 constexpr int kBulkConsumers = kThreads;          // eight consumer warps
 constexpr int kBulkThreads = kThreads + 32;       // plus one producer warp
@@ -794,7 +796,7 @@ template <class S> struct BulkGeom {
     static constexpr int BAR = (HDR + 127) / 128 * 128;             // header, keeps stages aligned
     static constexpr int SMEM = BAR + NST * STAGE;
     static_assert((RS * (int)sizeof(S)) % 16 == 0, "staged rows must stay 16-byte aligned");
-    static_assert(SMEM <= 113 * 1024, "two CTAs per SM must fit");
+    static_assert(SMEM <= 226 * 1024 / BulkCfg<S>::MINB, "the CTAs per SM must fit");
 };
 #ifndef IBLBM_EMULATE
 constexpr long kBulkSpinLimit = 1L << 22;   // polls of an mbarrier before the kernel gives up
