@@ -136,7 +136,7 @@ def main():
     ap.add_argument("--oscillating", action="store_true")
     ap.add_argument("--sedimentation", action="store_true")
     ap.add_argument("--steps", type=int, default=0)
-    ap.add_argument("--out", default="gpurun_out/workload_runs.json")
+    ap.add_argument("--out", default="workload_runs.json")
     args = ap.parse_args()
     import paper_2609_02298_b300 as L
     L.use_torch_allocator()
